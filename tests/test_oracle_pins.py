@@ -1,0 +1,286 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a closed form,
+a brute-force sum, a library routine used as an independent check, an
+invariant, or a special case with a known answer.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+rng0 = np.random.default_rng(12345)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+# ------------------------------------------------------------------ kernel (Sec. 3)
+def test_kernel_is_z_derivative_of_inverse_distance():
+    """K = d/dz (1/r): compare with a central difference of 1/r (fixes sign and the 3/2 power)."""
+    pts = rng0.uniform(-2, 2, size=(50, 3))
+    pts[:, 2] = np.where(np.abs(pts[:, 2]) < 0.2, 0.5, pts[:, 2])
+    e = 1e-5
+    inv_r = lambda x, y, z: 1.0 / np.sqrt(x * x + y * y + z * z)
+    fd = (inv_r(pts[:, 0], pts[:, 1], pts[:, 2] + e) - inv_r(pts[:, 0], pts[:, 1], pts[:, 2] - e)) / (2 * e)
+    assert rel(O.kernel_K(pts[:, 0], pts[:, 1], pts[:, 2]), fd) < 1e-8
+
+
+def _rect_solid_angle(x1, x2, y1, y2, z):
+    """integral over [x1,x2]x[y1,y2] of |z| / (x^2+y^2+z^2)^(3/2) (closed form of the rectangle's solid angle)."""
+    z = abs(z)
+    F = lambda x, y: np.arctan(x * y / (z * np.sqrt(x * x + y * y + z * z)))
+    return F(x2, y2) - F(x1, y2) - F(x2, y1) + F(x1, y1)
+
+
+@pytest.mark.parametrize("dz", [-0.5, -0.3, 0.4])
+def test_kernel_hat_dc_bin_equals_rectangle_closed_form(dz):
+    """h^2 * DFT at k = 0 is the midpoint rule for the kernel's integral over the periodic box;
+    the integral has the closed form -sgn(z) * solid angle of the box's square."""
+    n, h = 256, 0.01
+    Kh = O.kernel_hat(n, h, [0.0], [-dz])[0, 0]           # z_i - z'_j = dz
+    # wrapped lags run from -n/2 to n/2 - 1: cells cover [-(n/2 + 1/2) h, (n/2 - 1/2) h]
+    lo, hi = -(n / 2 + 0.5) * h, (n / 2 - 0.5) * h
+    exact = -np.sign(dz) * _rect_solid_angle(lo, hi, lo, hi, dz)
+    assert abs(Kh[0, 0] - exact) <= 1e-4 * abs(exact)
+    # and the whole-plane value -2 pi sgn(z) is approached as the box grows
+    assert abs(Kh[0, 0] + 2 * np.pi * np.sign(dz)) < 2 * np.pi * abs(dz) / (n / 2 * h) * 1.5
+
+
+def test_kernel_hat_matches_continuum_transform():
+    """K~(w, z) = -2 pi sgn(z) exp(-|w||z|) (Fourier transform of d/dz 1/r with the e^{-i w x}
+    convention of Lemma 1's 1/(4 pi^2) Plancherel identity).  On a large box the discrete
+    transform h^2 DFT must agree to within the box-truncation error, which is bounded by the
+    kernel's L1 mass outside the inscribed disk, 2 pi |z| / half-width."""
+    n, h, dz = 512, 0.05, -0.5
+    Kh = O.kernel_hat(n, h, [0.0], [-dz])[0, 0]
+    k = np.fft.fftfreq(n, d=h) * 2 * np.pi
+    W = np.sqrt(k[None, :] ** 2 + k[:, None] ** 2)
+    exact = -2 * np.pi * np.sign(dz) * np.exp(-W * abs(dz))
+    bound = 2 * np.pi * abs(dz) / (n / 2 * h)
+    sel = W < 12.0
+    assert np.max(np.abs(Kh[sel] - exact[sel])) < bound
+    # away from k = 0 the truncation error oscillates away; the agreement is much tighter
+    mid = (W > 2.0) & (W < 12.0)
+    assert np.max(np.abs(Kh[mid] - exact[mid])) < 0.1 * bound
+    # a wrong decay law (e.g. exp(-|w||z|/2)) or a dropped 2 pi would fail these bounds
+    wrong = -2 * np.pi * np.sign(dz) * np.exp(-W * abs(dz) / 2)
+    assert np.max(np.abs(Kh[mid] - wrong[mid])) > 10 * (0.1 * bound)
+
+
+@pytest.mark.parametrize("n,pad", [(8, 1), (6, 1), (6, 2)])
+def test_kernel_hat_is_real_and_has_eightfold_symmetry(n, pad):
+    Kh = O.kernel_hat(n, 0.3, [0.0, 0.1], [0.5, 0.7], pad)
+    L = n * pad
+    for i in range(2):
+        for j in range(2):
+            K = Kh[i, j]
+            assert np.allclose(K, K.T, rtol=0, atol=1e-13 * np.abs(K).max())                 # kx <-> ky
+            idx = (-np.arange(L)) % L
+            assert np.allclose(K, K[idx][:, idx], rtol=0, atol=1e-13 * np.abs(K).max())      # k -> -k
+            assert np.allclose(K, K[:, idx], rtol=0, atol=1e-13 * np.abs(K).max())           # kx -> -kx
+
+
+# ------------------------------------------------------------------ DFT
+@pytest.mark.parametrize("shape", [(4, 4), (6, 6), (3, 5)])
+def test_dft2_equals_definition_double_sum(shape):
+    f = rng0.standard_normal(shape) + 1j * rng0.standard_normal(shape)
+    Ly, Lx = shape
+    F = np.zeros(shape, complex)
+    for ky in range(Ly):
+        for kx in range(Lx):
+            for y in range(Ly):
+                for x in range(Lx):
+                    F[ky, kx] += f[y, x] * np.exp(-2j * np.pi * (ky * y / Ly + kx * x / Lx))
+    assert rel(O.dft2(f), F) < 1e-13
+    assert rel(O.idft2(F), f) < 1e-13
+
+
+def test_dft2_agrees_with_library_fft_and_parseval():
+    f = rng0.standard_normal((3, 24, 24))
+    F = O.dft2(f)
+    assert rel(F, np.fft.fft2(f)) < 1e-13
+    # Parseval: sum |f|^2 = L^-2 sum |F|^2 (the discrete form of Lemma 1's Plancherel identity)
+    assert abs(np.sum(f ** 2) - np.sum(np.abs(F) ** 2) / 24 ** 2) < 1e-10 * np.sum(f ** 2)
+
+
+# ------------------------------------------------------------------ convolution theorem (Eq. (5))
+@pytest.mark.parametrize("n", [6, 8])
+def test_forward_dft_equals_direct_quadrature_periodic(n):
+    h, zy, zr, nu = 0.25, [0.0, 0.1], [0.5, 0.6, 0.8], [0.1, 0.1, 0.2]
+    zeta = rng0.standard_normal((2, 3, n, n))
+    Ud = O.forward_direct(zeta, n, h, zy, zr, nu)
+    Uf = O.forward_dft(zeta, n, h, zy, zr, nu)
+    assert rel(Uf, Ud) < 1e-12
+
+
+def test_pad2_gives_the_aperiodic_sum_over_R():
+    n, h, zy, zr, nu = 5, 0.3, [0.0], [0.5, 0.9], [0.2, 0.2]
+    zeta = rng0.standard_normal((2, n, n))
+    # brute force aperiodic sum, no wrapping at all
+    U = np.zeros((1, n, n))
+    for b in range(n):
+        for a in range(n):
+            for j in range(2):
+                for bb in range(n):
+                    for aa in range(n):
+                        U[0, b, a] += h * h * nu[j] * O.kernel_K((a - aa) * h, (b - bb) * h, zy[0] - zr[j]) * zeta[j, bb, aa]
+    assert rel(O.forward_direct(zeta, n, h, zy, zr, nu, pad=2), U) < 1e-13
+    assert rel(O.forward_dft(zeta, n, h, zy, zr, nu, pad=2), U) < 1e-12
+
+
+def _operator_matrix(n, h, zy, zr, nu, pad=1):
+    """The full discrete operator of Eq. (4) as a dense matrix, column by column from unit inputs."""
+    Mp = len(zr)
+    cols = []
+    for j in range(Mp):
+        for b in range(n):
+            for a in range(n):
+                e = np.zeros((Mp, n, n))
+                e[j, b, a] = 1.0
+                cols.append(O.forward_direct(e, n, h, zy, zr, nu, pad).ravel())
+    return np.array(cols).T
+
+
+# ------------------------------------------------------------------ Tikhonov (Sec. 5)
+def test_tikhonov_optimality_pinv_limit_and_dual_identity():
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((20, 3, 5))
+    u = rng.standard_normal((20, 3, 2)) + 1j * rng.standard_normal((20, 3, 2))
+    for a in [1e-3, 0.1, 3.0]:
+        x = O.tikhonov_qr(A, u, a)
+        g = np.swapaxes(A, 1, 2) @ (A @ x - u) + a * x              # gradient of the Tikhonov functional
+        assert np.max(np.abs(g)) < 1e-12 * max(1, np.max(np.abs(u)))
+        # dual form A^T (A A^T + a I)^{-1} u (a different formula for the same minimiser)
+        xd = np.swapaxes(A, 1, 2) @ np.linalg.solve(A @ np.swapaxes(A, 1, 2) + a * np.eye(3), u)
+        assert rel(x, xd) < 1e-11
+    x0 = O.tikhonov_qr(A, u, 1e-13)
+    assert rel(x0, np.linalg.pinv(A) @ u) < 1e-8                   # normal (minimum-norm) solution
+    # the residual grows and the norm shrinks with alpha
+    res = [np.linalg.norm(A @ O.tikhonov_qr(A, u, a) - u) for a in np.logspace(-6, 2, 12)]
+    nrm = [np.linalg.norm(O.tikhonov_qr(A, u, a)) for a in np.logspace(-6, 2, 12)]
+    assert np.all(np.diff(res) >= -1e-12) and np.all(np.diff(nrm) <= 1e-12)
+
+
+def test_algorithm1_equals_dense_tikhonov_of_full_operator():
+    """Per-frequency Tikhonov + inverse DFT (Algorithm 1, Lemma 1) equals Tikhonov on the whole
+    discretised operator of Eq. (4), assembled by brute force from the direct quadrature."""
+    n, h, zy, zr, nu = 4, 0.3, [0.0], [0.5, 0.7, 0.9], [0.2, 0.2, 0.2]
+    Aop = _operator_matrix(n, h, zy, zr, nu)
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal((1, 1, n, n))
+    A = O.A_matrices(n, h, zy, zr, nu)
+    s2 = O.alpha_scale(A)
+    for alpha in [1e-12, 1e-3, 0.5]:
+        out = O.invert(U, n, -0.6, h, zy, zr, nu, alpha=alpha, output="zeta")
+        stacked = np.vstack([Aop, np.sqrt(alpha * s2) * np.eye(Aop.shape[1])])
+        rhs = np.concatenate([U.ravel(), np.zeros(Aop.shape[1])])
+        z = np.linalg.lstsq(stacked, rhs, rcond=None)[0]
+        assert rel(out["zeta"].ravel(), z) < 1e-9
+    # the alpha -> 0 limit is the normal solution (Assumption U): the pseudo-inverse of the operator
+    out = O.invert(U, n, -0.6, h, zy, zr, nu, alpha=1e-14, output="zeta")
+    assert rel(out["zeta"].ravel(), np.linalg.pinv(Aop) @ U.ravel()) < 1e-6
+
+
+def test_frequency_residual_equals_spatial_residual():
+    """Parseval: the residual summed over frequencies / L^2 is the spatial residual ||A zeta - U||^2."""
+    n, h, zy, zr, nu = 6, 0.3, [0.0], [0.5, 0.8], [0.25, 0.25]
+    rng = np.random.default_rng(4)
+    U = rng.standard_normal((1, 1, n, n))
+    out = O.invert(U, n, -0.9, h, zy, zr, nu, alphas=[1e-4, 1e-2], delta=1.0, tau=1.1, output="zeta")
+    k = out["alpha_index"]
+    Ufit = O.forward_direct(out["zeta"], n, h, zy, zr, nu)
+    assert abs(out["res2"][k] - np.sum((Ufit - U) ** 2)) < 1e-10 * np.sum(U ** 2)
+
+
+def test_exact_recovery_tiny_well_conditioned():
+    """M = M' = 1, coarse grid, small |dz|: noise-free data are inverted essentially exactly."""
+    n, h, zy, zr, nu = 8, 0.25, [0.0], [0.1], [1.0]
+    A = O.A_matrices(n, h, zy, zr, nu)
+    cond = np.abs(A).max() / np.abs(A).min()
+    assert cond < 50
+    zt = np.random.default_rng(5).standard_normal((1, 1, n, n))
+    U = O.forward_direct(zt, n, h, zy, zr, nu)
+    out = O.invert(U, n, -1.0, h, zy, zr, nu, alpha=1e-14, output="zeta")
+    assert rel(out["zeta"], zt) < 1e-9
+
+
+def test_discrepancy_rule():
+    r2 = np.array([0.5, 1.0, 1.2, 4.0, 9.0])
+    assert O.choose_alpha_index(r2, 1.0, 1.1) == (2, 0)        # 1.2 <= 1.21 < 4
+    assert O.choose_alpha_index(r2, 0.1, 1.1) == (0, 1)        # nothing admissible: smallest, flagged
+    assert O.choose_alpha_index(r2, 10.0, 1.1) == (4, 2)       # everything admissible: largest, flagged
+
+
+def test_convergence_as_noise_vanishes():
+    """Theorem 1: with the discrepancy principle the error to the normal solution decreases as
+    delta -> 0.  The truth is built in range(A^T) per frequency, so it is its own normal solution."""
+    n, h, zy, zr, nu = 16, 0.125, [0.0], list(0.5 + 0.05 * np.arange(6)), [0.05] * 6
+    A = O.A_matrices(n, h, zy, zr, nu)
+    rng = np.random.default_rng(11)
+    w = O.dft2(rng.standard_normal((1, n, n)))                       # Hermitian weights
+    Zh = np.einsum("yxij,iyx->jyx", A, w)
+    zt = O.idft2(Zh).real[None]
+    U = O.forward_dft(zt, n, h, zy, zr, nu, A=A)
+    noise = rng.standard_normal(U.shape)
+    errs = []
+    for lev in [1e-1, 1e-2, 1e-3, 1e-4, 1e-5]:
+        d = lev * np.linalg.norm(U)
+        Un = U + d * noise / np.linalg.norm(noise)
+        out = O.invert(Un, n, -1.0, h, zy, zr, nu, alphas=np.logspace(-12, 0, 25), delta=d, tau=1.1,
+                       output="zeta", A=A)
+        errs.append(rel(out["zeta"], zt))
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1)), errs
+    assert errs[-1] < 0.05
+
+
+# ------------------------------------------------------------------ sources and V0 (Sec. 2, Sec. 6)
+def test_A0_A2_for_exponential_source_pulse():
+    g = json.load(open(os.path.join(GOLD, "paper_model_example.json")))
+    assert abs(O.A0_of(lambda t: np.exp(-t)) - g["A0_for_g"]) < 1e-10
+    assert abs(O.A2_of(lambda t: np.exp(-t)) - g["A2_for_g"]) < 1e-10
+
+
+def test_V0_solves_poisson_equation_for_point_sources():
+    """Delta V0 = A0 phi: V0 is harmonic away from the sources and the flux of grad V0 through a
+    sphere around one source is A0 (fixes the sign and the 1/(4 pi))."""
+    pts = np.array([[0.1, -0.2, -0.3], [0.5, 0.5, -0.4]])
+    A0 = 1.7
+    e = 1e-3
+    X, Y, Z = 0.3, 0.2, 0.6
+    lap = (O.V0(pts, X + e, Y, Z, A0) + O.V0(pts, X - e, Y, Z, A0) + O.V0(pts, X, Y + e, Z, A0)
+           + O.V0(pts, X, Y - e, Z, A0) + O.V0(pts, X, Y, Z + e, A0) + O.V0(pts, X, Y, Z - e, A0)
+           - 6 * O.V0(pts, X, Y, Z, A0)) / e ** 2
+    assert abs(lap) < 1e-4
+    # flux through a sphere of radius 0.05 around the first source (midpoint rule in angles)
+    r, c = 0.05, pts[0]
+    th = (np.arange(200) + 0.5) * np.pi / 200
+    ph = (np.arange(400) + 0.5) * 2 * np.pi / 400
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    nrm = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)])
+    x = c[:, None, None] + r * nrm
+    grad = np.stack([(O.V0(pts, x[0] + s[0] * e, x[1] + s[1] * e, x[2] + s[2] * e, A0)
+                      - O.V0(pts, x[0] - s[0] * e, x[1] - s[1] * e, x[2] - s[2] * e, A0)) / (2 * e)
+                     for s in np.eye(3)])
+    flux = np.sum(np.sum(grad * nrm, axis=0) * r * r * np.sin(T)) * (np.pi / 200) * (2 * np.pi / 400)
+    assert abs(flux - A0) < 1e-3 * A0
+
+
+def test_combination_recovers_shared_xi_exactly():
+    from paper_1703_01216_gb300.inputs import cross_sources
+    n, x0, h = 8, -1.0, 0.25
+    zr = [0.6, 0.8]
+    xi = np.random.default_rng(2).standard_normal((2, n, n))
+    S = cross_sources(3)
+    zeta = O.zeta_from_xi(xi, S, n, x0, h, zr)
+    assert rel(O.combine_sources(zeta, S, n, x0, h, zr), xi) < 1e-14
+    # single source: xi = zeta / V0 (Algorithm 1 step 4)
+    c = x0 + (np.arange(n) + 0.5) * h
+    v = O.V0(S[0], c[None, None, :], c[None, :, None], np.array(zr)[:, None, None])
+    assert rel(O.combine_sources(zeta[:1], S[:1], n, x0, h, zr), zeta[0] / v) < 1e-14
