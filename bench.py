@@ -1,0 +1,388 @@
+"""Benchmark: steady-state FFT-Tikhonov inversion (Algorithm 1) at 256^2 x 64 voxels.
+
+Workload: the 256 x 256 x 64 voxel slab R = [-1, 1]^2 x [0.5, 1] with one observation plane
+z = 0 (M = 1), 8 source parameters (5-point crosses on the planes z = -0.1 (q + 1)), 10
+Gaussian/ellipsoid inclusions, 1 % relative Gaussian noise, 64 log-spaced alphas in
+[1e-8, 1e-1] with the discrepancy principle, xi output.  Data are synthesised once on the
+device by the library's own forward operator (untimed).  A step is one fr3d_invert call:
+data FFT, alpha rule, per-frequency solve, inverse FFT and xi = zeta / V0 combination.
+
+Timing: W untimed warm-up steps, then K timed steps; every step is bracketed by CUDA events on
+the launching stream and preceded (outside the events) by a 256 MB write that flushes L2.
+value = voxels processed by all ranks / max over ranks of the summed step time.
+Multi-GPU (torchrun): every rank inverts its own independent instance (weak scaling, no
+collective on the data path).
+
+--impl reference runs the FP64 oracle (the paper's method written plainly, numpy) on the host
+cores instead: each step is a bounded sample of the same workload, scaled to voxels/s.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG_ID = 3
+WORKLOAD = "fft_tikhonov_invert_256x256x64_q8_a64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fr3d", choices=["fr3d", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1703_01216_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(stage: str):
+    """DRAM bytes per launch of ``stage`` from the committed ncu summary, if it was taken on the
+    current kernel sources (profiles/traffic.md lines: `stage | source hash | bytes per launch | ...`)."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash()
+    for line in open(p):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == stage and cells[1] == cur:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+def stage_bytes(stage: str, n: int, mp: int, q: int, nj: int) -> float:
+    """Algorithmic DRAM bytes of one launch: every input read once, every output written once."""
+    ps = (n // 2 + 1) * n                     # half-spectrum bins per plane
+    if stage == "row_c2r":                    # spectra of nj depths x q sources in, xi of nj depths out
+        return nj * q * ps * 8.0 + nj * n * n * 4.0
+    if stage == "col_solve":                  # data spectra + weights in, per-depth spectra out
+        return q * ps * 8.0 + nj * ps * 4.0 + nj * q * ps * 8.0
+    if stage == "row_r2c":
+        return q * n * n * 4.0 + q * ps * 8.0
+    if stage == "col_fwd":
+        return 2 * q * ps * 8.0
+    if stage == "alpha":
+        C = (n // 2 + 1) * (n // 2 + 2) // 2
+        return q * ps * 8.0 + C * 64 * 8.0
+    return 0.0
+
+
+# ---------------------------------------------------------------- CPU oracle (bounded sample)
+def oracle_sample(w, A, U, delta, budget_bins=96):
+    """Time the FP64 oracle on a bounded sample of one step and scale it to the whole step.
+
+    Sample: the data DFT (all Q planes, full), the Tikhonov QR solves and residuals for all 64
+    alphas on ``budget_bins`` of the n^2 frequencies (scaled by n^2 / budget_bins), and the inverse
+    DFT plus combination for one of the M' depths (scaled by M')."""
+    import oracle as O
+    n, Q, Mp = w.n, w.Q, w.Mp
+    rng = np.random.default_rng(0)
+    bins = np.sort(rng.choice(n * n, size=budget_bins, replace=False))
+    t0 = time.perf_counter()
+    Uh = O.dft2(U)
+    t1 = time.perf_counter()
+    O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=delta, tau=1.1, output="none",
+             bins=bins, A=A)
+    t2 = time.perf_counter()
+    # the invert above repeats the data DFT: remove it from the solve share
+    t_solve = max((t2 - t1) - (t1 - t0), 1e-9)
+    Zh = np.zeros((Q, 1, n, n), np.complex128)
+    Zh[:, 0] = Uh[:, 0]
+    t3 = time.perf_counter()
+    z = O.idft2(Zh).real
+    O.combine_sources(np.repeat(z, 1, axis=1), w.sources, n, w.x0, w.h, w.zr[:1])
+    t4 = time.perf_counter()
+    est = (t1 - t0) + t_solve * (n * n / budget_bins) + (t4 - t3) * Mp
+    wall = t4 - t0
+    return {"seconds_per_step_est": est, "sample_wall_s": wall,
+            "sample": f"data DFT of all {Q} planes; QR Tikhonov solves + residuals for all {w.alphas.size} alphas on "
+                      f"{budget_bins} of {n * n} frequencies (x{n * n / budget_bins:.0f}); inverse DFT + xi for 1 of "
+                      f"{Mp} depths (x{Mp})"}
+
+
+def cpu_cores():
+    v = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------- workload setup on the GPU
+def setup_gpu(w, dev):
+    import torch
+    from paper_1703_01216_gb300 import fr3d
+    H = fr3d.kernel_transform(w.n, w.x0, w.h, w.zr, w.zy, w.nu)
+    xi = torch.tensor(w.xi_true, dtype=torch.float32, device=dev)
+    zeta = torch.empty((w.Q, w.Mp, w.n, w.n), device=dev)
+    fr3d.zeta_from_xi(H, xi, w.sources, zeta)
+    U = torch.empty((w.Q, 1, w.n, w.n), device=dev)
+    fr3d.fwd_apply(H, zeta, w.Q, U)
+    nz = torch.tensor(w.noise, dtype=torch.float32, device=dev)
+    nz *= w.noise_level * U.norm() / nz.norm()
+    U += nz
+    delta = float(nz.norm())
+    del zeta
+    return H, U, delta
+
+
+def run_fr3d(args):
+    import torch
+    from paper_1703_01216_gb300 import fr3d
+    from paper_1703_01216_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    w = I.config_workload(CONFIG_ID, instance=rank)
+    n, Mp, Q = w.n, w.Mp, w.Q
+    voxels = n * n * Mp
+    t0 = time.perf_counter()
+    H, U, delta = setup_gpu(w, dev)
+    torch.cuda.synchronize()
+    t_cold = time.perf_counter() - t0
+    out = torch.empty((Mp, n, n), device=dev)
+    idx = torch.zeros(1, dtype=torch.int32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    opts = fr3d.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx, info=info)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+    st = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        fr3d.invert(H, U, Q, out, opts)
+    torch.cuda.synchronize()
+    fr3d.profile_enable(H, True)
+    stage_ms = {}
+    stage_launches = {}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.fill_(1.0)
+            ev[k][0].record(st)
+            fr3d.invert(H, U, Q, out, opts)
+            ev[k][1].record(st)
+            launches += fr3d.last_launch_count(H)
+            for name, ms in fr3d.profile_read(H):
+                stage_ms[name] = stage_ms.get(name, 0.0) + ms
+                stage_launches[name] = stage_launches.get(name, 0) + 1
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    fr3d.profile_enable(H, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = voxels * world * args.steps / total_s
+
+    # end to end through the host-buffer entry point (pinned host memory, copies inside the region)
+    U_host = U.cpu().pin_memory()
+    out_host = torch.empty((Mp, n, n), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        fr3d.invert_host(H, U_host, Q, out_host, opts)
+    e2e_steps = max(5, min(args.steps, 20))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e2e_total = 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        fr3d.invert_host(H, U_host, Q, out_host, opts)   # H2D copy, inversion, D2H copy, stream sync
+        e2e_total += time.perf_counter() - a
+    if dist:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    # reconstruction quality of the last step (not timed)
+    xi_true = torch.tensor(w.xi_true, device=dev)
+    rel_truth = float((out.double() - xi_true).norm() / xi_true.norm())
+
+    # roofline of the dominant kernel (largest summed time over the timed region)
+    dom = max(stage_ms, key=stage_ms.get)
+    per_launch_ms = stage_ms[dom] / stage_launches[dom]
+    nchunk = max(1, stage_launches.get("col_solve", 1) // args.steps)
+    nj = -(-Mp // nchunk)
+    algo = stage_bytes(dom, n, Mp, Q, nj)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = algo / (per_launch_ms * 1e-3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom),
+            "algorithmic_bytes_per_launch": algo, "ms_per_launch": round(per_launch_ms, 5),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"}
+
+    result = {
+        "metric": "voxels/s of FFT-Tikhonov inversion at 256^2x64 (plain discrepancy-principle method)",
+        "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FFT) + f64 (alpha rule)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m_prime": Mp, "m": 1, "q_sources": Q, "n_alpha": int(w.alphas.size),
+                   "voxels_per_instance": voxels, "instances_per_gpu": 1, "l2": "flushed (256 MB write) before every step",
+                   "parallelism": f"replicas x{world} (independent instances)"},
+        "gpu_launches": launches,
+        "e2e": {"value": voxels * world * e2e_steps / e2e_total, "unit": "voxels/s",
+                "h2d_bytes_per_step": int(U_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4)},
+        "roofline": roof,
+        "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
+        "cold_setup_s": round(t_cold, 3),
+        "alpha_index": int(idx.item()), "info": int(info.item()),
+        "rel_l2_vs_truth": round(rel_truth, 4),
+    }
+    clocks = clk.summary()
+    result["clocks"] = clocks
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu)
+        Uc = U.double().cpu().numpy()
+        s = oracle_sample(w, A, Uc, delta)
+        result["cpu_baseline"] = {"value": voxels / s["seconds_per_step_est"], "unit": "voxels/s",
+                                  "cores": cpu_cores(), "kind": "oracle", "sample": s["sample"],
+                                  "sample_wall_s": round(s["sample_wall_s"], 2)}
+    if rank == 0:
+        print(json.dumps(result))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, one bounded sample per step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1703_01216_gb300 import inputs as I
+    w = I.config_workload(CONFIG_ID)
+    n, Mp, Q = w.n, w.Mp, w.Q
+    A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu)
+    zeta = O.zeta_from_xi(w.xi_true, w.sources, n, w.x0, w.h, w.zr)
+    U = O.forward_dft(zeta, n, w.h, w.zy, w.zr, w.nu, A=A)
+    nz = w.noise * (w.noise_level * np.linalg.norm(U) / np.linalg.norm(w.noise))
+    U = U + nz
+    delta = float(np.linalg.norm(nz))
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(w, A, U, delta, budget_bins=16)
+    ests = []
+    sample = None
+    for _ in range(args.steps):
+        s = oracle_sample(w, A, U, delta, budget_bins=32)
+        ests.append(s["seconds_per_step_est"])
+        sample = s["sample"]
+    sec = float(np.mean(ests))
+    value = n * n * Mp / sec
+    print(json.dumps({
+        "impl": "reference", "metric": "voxels/s of FFT-Tikhonov inversion at 256^2x64 (plain discrepancy-principle method)",
+        "value": value, "unit": "voxels/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m_prime": Mp, "m": 1, "q_sources": Q, "n_alpha": int(w.alphas.size)},
+        "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fr3d(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * fr3d.h -- C ABI of the GB300 (sm_103a) FFT-Tikhonov inversion library.
+ *
+ * The library solves the linear first-kind Fredholm equation of Leonov &
+ * Bakushinsky (arXiv 1703.01216), Eq. (4):
+ *
+ *     integral over R of K(x - x', y - y', z - z') zeta(x', y', z') dx' dy' dz' = U(x, y, z),
+ *     (x, y, z) in Y,      K(x, y, z) = d/dz (1/r) = -z / (x^2 + y^2 + z^2)^(3/2),
+ *
+ * for the flat-layer geometry of Sec. 3 (R and Y horizontal slabs), with
+ * Algorithm 1 of Sec. 4 in the finite-dimensional form of Sec. 5:
+ *   step 1  2D DFT over (x, y) of the data and of the sampled kernel,
+ *   step 2  per horizontal frequency m, a Tikhonov solution of the small system
+ *           A^(m) zeta~^(m) = U~^(m) of Eq. (6), alpha by the discrepancy principle,
+ *   step 3  inverse 2D DFT per depth z'_j,
+ *   step 4  xi = zeta / V0, xi = 1/c0^2 - 1/c^2 (c = (1/c0^2 - xi)^(-1/2)).
+ *
+ * Conventions.  Horizontal grid: n x n voxel-centred points x_a = x0 + (a + 1/2) h
+ * (same in y); the box is periodic (pad = 1, the paper's discrete model of Sec. 5).
+ * Real volumes are row-major [plane][y][x] (x fastest).  The forward DFT is
+ * unnormalised, the inverse carries 1/n^2; the continuous transform is
+ * approximated by h^2 * DFT.  Depth grids: M' depths z'_j of R with quadrature
+ * weights nu_j, and M observation depths z_i of Y; every z_i - z'_j must be
+ * non-zero (R and Y are disjoint, Sec. 1).  The Tikhonov parameter is
+ * dimensionless: the regulariser is alpha * s^2 with s^2 = max_m ||A^(m)||_F^2.
+ *
+ * Memory.  Data pointers (volumes, alpha_idx, residuals, info) are DEVICE
+ * pointers owned by the caller unless stated otherwise; small parameter arrays
+ * (depths, alphas, source points) are HOST pointers read during the call.  The
+ * handle owns its device tables and a workspace that grows on the first call for
+ * a new shape (so make that first call outside any stream capture).  Calls are
+ * asynchronous on the given CUDA stream (NULL = legacy default stream); results
+ * are valid once the stream has synchronised.  One handle serves one stream at a
+ * time: concurrent calls on one handle share its workspace and race.
+ *
+ * Errors.  Every call returns an int status: FR3D_OK (0) or a negative
+ * FR3D_ERR_* code; argument and geometry checks happen on the host before any
+ * launch, so an error return means nothing was enqueued.  Conditions only the
+ * device can see (alpha rule outcome, non-finite data) are reported as
+ * FR3D_INFO_* bit flags in an optional device int.  No C++ exception crosses
+ * this interface.
+ */
+#ifndef FR3D_H
+#define FR3D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FR3D_OK 0
+#define FR3D_ERR_INVALID_ARG (-1)      /* NULL pointer, negative count, bad enum */
+#define FR3D_ERR_BAD_GEOMETRY (-2)     /* some z_i - z'_j == 0 (R and Y overlap), h <= 0 */
+#define FR3D_ERR_UNSUPPORTED_SIZE (-3) /* n not 2^a 3^b in [16, 512], nx != ny, too many alphas/sources */
+#define FR3D_ERR_OOM (-4)              /* device allocation failed */
+#define FR3D_ERR_CUDA (-5)             /* a CUDA runtime call failed */
+#define FR3D_ERR_TIMEOUT (-6)          /* a bounded device wait gave up */
+#define FR3D_ERR_NONFINITE_INPUT (-7)  /* reserved for synchronous checks */
+
+/* ---- device-side info bits (OR-ed into *info when an info pointer is given) ---- */
+#define FR3D_INFO_ALPHA_NONE_SATISFIES 1 /* no candidate met the bound: the smallest alpha was used */
+#define FR3D_INFO_ALPHA_ALL_SATISFY 2    /* every candidate met the bound: the largest alpha was used */
+#define FR3D_INFO_NONFINITE 4            /* the data spectrum held NaN/Inf */
+
+/* ---- enums ---- */
+#define FR3D_K_DZ_INV_R 0 /* K = d/dz (1/r), Eq. (4) (the equation the paper solves) */
+#define FR3D_PREC_FP32 0  /* FP32 FFTs, FP64 alpha rule; data and outputs are float */
+#define FR3D_PREC_FP64 1  /* FP64 throughout; data and outputs are double */
+#define FR3D_ALPHA_FIXED 0
+#define FR3D_ALPHA_DISCREPANCY 1
+#define FR3D_OUT_ZETA 0   /* output zeta_q per source parameter: [Q][M'][n][n] */
+#define FR3D_OUT_XI 1     /* output xi (Algorithm 1 step 4): [M'][n][n] */
+
+#define FR3D_MAX_ALPHAS 128
+#define FR3D_MAX_SOURCE_POINTS 256 /* total points over all source parameters q */
+
+/* Flat-layer geometry (Sec. 3: R = R^2 x [h, H], Y = R^2 x [h_Y, H_Y]; Sec. 5 grids). */
+typedef struct fr3d_geometry {
+  int nx, ny;              /* horizontal grid; nx == ny == n, n = 2^a 3^b with 16 <= n <= 512 */
+  double x0, y0, hx, hy;   /* voxel-centred grid x_a = x0 + (a + 1/2) hx; hx == hy > 0 */
+  int pad;                 /* box factor P; only 1 (periodic box of side n h) is supported */
+  int nzr;                 /* M' >= 1: depths of R */
+  const double* zr;        /* host [M'] depths z'_j */
+  const double* nu;        /* host [M'] quadrature weights nu_j (NULL: midpoint, |z'_1 - z'_0|, or 1 if M' = 1) */
+  int nzy;                 /* M >= 1: observation depths of Y */
+  const double* zy;        /* host [M] depths z_i; z_i != z'_j for all i, j */
+  int kernel_kind;         /* FR3D_K_DZ_INV_R */
+} fr3d_geometry;
+
+/* Point sources of the model example (Sec. 6): for source parameter q the field source is
+ * sum_l delta(x - x_{q,l}); V0_q(x) = -A0/(4 pi) sum_l 1/|x - x_{q,l}| (points outside R and Y). */
+typedef struct fr3d_sources {
+  int q;                   /* number of source parameters Q >= 1 */
+  int n_points;            /* points per source parameter L >= 1 (Q * L <= FR3D_MAX_SOURCE_POINTS) */
+  const double* xyz;       /* host [Q][L][3] */
+  double A0;               /* A0 = integral of g(t) dt, non-zero (Sec. 2, Assumption 5) */
+} fr3d_sources;
+
+typedef struct fr3d_handle fr3d_handle;
+
+typedef struct fr3d_invert_opts {
+  int alpha_mode;          /* FR3D_ALPHA_FIXED or FR3D_ALPHA_DISCREPANCY */
+  double alpha;            /* FIXED: alpha > 0 */
+  const double* alphas;    /* DISCREPANCY: host [n_alpha], strictly increasing, > 0 */
+  int n_alpha;             /* 1 .. FR3D_MAX_ALPHAS */
+  double delta;            /* DISCREPANCY: data error level, ||U - U_exact|| over all data (>= 0) */
+  double tau;              /* DISCREPANCY: threshold factor (e.g. 1.1); the largest alpha with
+                              residual <= tau * delta is chosen */
+  int output;              /* FR3D_OUT_ZETA or FR3D_OUT_XI */
+  int precision;           /* FR3D_PREC_FP32 or FR3D_PREC_FP64 */
+  const fr3d_sources* sources; /* required for FR3D_OUT_XI (sources->q == Q) */
+  int* alpha_idx;          /* device int[1] or NULL: index of the chosen alpha (0 for FIXED) */
+  double* residuals;       /* device double[n_alpha] or NULL: squared residuals ||A zeta_alpha - U||^2 */
+  int* info;               /* device int[1] or NULL: FR3D_INFO_* bits of this call (overwritten) */
+} fr3d_invert_opts;
+
+/* Step 1 for the kernel (Algorithm 1, Sec. 5): samples K at the periodic lags for every
+ * z_i - z'_j, transforms them in FP64 and builds the tables A^(m) = [nu_j K~(w^(m), z_i - z'_j)]
+ * of Eq. (6), ||A^(m)||_F^2 and s^2.  Allocates the handle (free with fr3d_handle_destroy).
+ * The geometry's host arrays are copied; they may be freed after the call returns. */
+int fr3d_kernel_transform(const fr3d_geometry* geom, fr3d_handle** out, void* stream);
+void fr3d_handle_destroy(fr3d_handle* h);
+
+/* Sizes and the alpha scale of a handle (any pointer may be NULL).  Synchronises the
+ * handle's creation stream on the first call. */
+int fr3d_handle_query(fr3d_handle* h, int* n, int* m, int* mp, double* s2);
+
+/* The discrete operator of Eq. (4) through Eq. (5)-(6): U_q = A zeta_q for q = 0..Q-1.
+ * zeta: device [Q][M'][n][n]; U: device [Q][M][n][n]; float or double per precision. */
+int fr3d_fwd_apply(fr3d_handle* h, const void* zeta, int Q, void* U, int precision, void* stream);
+
+/* zeta_q = xi * V0_q (Sec. 2, zeta = xi V0) for the point sources of Sec. 6.
+ * xi: device [M'][n][n]; zeta: device [Q][M'][n][n]; Q = sources->q. */
+int fr3d_zeta_from_xi(fr3d_handle* h, const void* xi, const fr3d_sources* sources, void* zeta,
+                      int precision, void* stream);
+
+/* Step 2's parameter choice alone: squared residuals r^2(alpha_k) = ||A zeta_alpha_k - U||^2
+ * (summed over all q and all data points) and the discrepancy choice (Sec. 4): the largest
+ * alpha_k with r <= tau * delta.  U: device [Q][M][n][n].  alpha_idx: device int[1];
+ * residuals: device double[n_alpha] or NULL; info: device int[1] or NULL. */
+int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const double* alphas, int n_alpha,
+                      double delta, double tau, int precision, int* alpha_idx, double* residuals,
+                      int* info, void* stream);
+
+/* Algorithm 1 steps 1-4.  U: device [Q][M][n][n]; out: device [Q][M'][n][n] (ZETA) or
+ * [M'][n][n] (XI).  The regularised normal solution of each frequency's system is the
+ * Tikhonov minimiser of ||A zeta - U||^2 + alpha s^2 ||zeta||^2. */
+int fr3d_invert(fr3d_handle* h, const void* U, int Q, const fr3d_invert_opts* opts, void* out,
+                void* stream);
+
+/* fr3d_invert with HOST buffers: copies U (host [Q][M][n][n]) to the device, inverts and copies
+ * the result back to out (host); returns after the stream has synchronised.  Pinned host memory
+ * gives asynchronous copies; pageable memory also works. */
+int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_invert_opts* opts,
+                     void* out_host, void* stream);
+
+/* Number of kernel launches the last call on this handle enqueued (cache rebuilds excluded). */
+int fr3d_last_launch_count(fr3d_handle* h);
+
+/* Stage tracing.  When enabled, fr3d_invert records a CUDA event on its stream before its first
+ * launch and after every launch.  fr3d_profile_read waits for the last event of the latest call
+ * and writes, per launch interval i < min(cap, count), its stage kind and its duration in ms;
+ * it returns the count.  Kinds: 0 data row pass, 1 data column pass, 2 alpha rule, 3 solve +
+ * inverse column pass, 4 inverse row pass (+ xi), 5 table rebuild, 6 forward contraction,
+ * 7 inverse column pass, 8 other. */
+int fr3d_profile_enable(fr3d_handle* h, int enable);
+int fr3d_profile_read(fr3d_handle* h, int* kinds, float* ms, int cap);
+
+const char* fr3d_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FR3D_H */

@@ -206,16 +206,15 @@ def tikhonov_qr(A: np.ndarray, Uh: np.ndarray, alpha_s2: float) -> np.ndarray:
     return x[..., :K] + 1j * x[..., K:]
 
 
-def residual_sq(A: np.ndarray, Zh: np.ndarray, Uh: np.ndarray) -> float:
+def residual_sq(A: np.ndarray, Zh: np.ndarray, Uh: np.ndarray, n_freq: int | None = None) -> float:
     """sum over frequencies and right-hand sides of |A^(m) zeta~ - U~|^2, divided by L^2.
 
     By Parseval this is the squared residual ||A zeta - U||^2 on the spatial grid
     (the data norm of the discrepancy principle).  A: [B, M, M'], Zh: [B, M', K],
-    Uh: [B, M, K]; B = L*L frequencies.
+    Uh: [B, M, K]; ``n_freq`` = L^2, the number of grid frequencies (default B).
     """
-    B = A.shape[0]
     r = A @ Zh - Uh
-    return float(np.sum(np.abs(r) ** 2) / B)
+    return float(np.sum(np.abs(r) ** 2) / (A.shape[0] if n_freq is None else n_freq))
 
 
 def choose_alpha_index(res2, delta: float, tau: float):
@@ -304,10 +303,11 @@ def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int =
     Step 3: inverse 2D DFT per depth z'_j (cropped to n x n when pad = 2).
     Step 4: xi = zeta / V0 (several q: pointwise least squares).
 
-    Returns a dict with ``zeta`` [Q, M', n, n], ``xi`` [M', n, n] (if sources are given),
-    ``alpha_index``, ``flag`` and ``res2`` (squared residual per candidate alpha).
-    ``bins`` (optional) restricts step 2 to a subset of flattened frequencies (used only
-    to time a bounded sample); the returned zeta is then meaningless.
+    Returns a dict with ``zeta`` [Q, M', n, n], ``xi`` [M', n, n] (if sources are given and
+    output == "xi"), ``alpha_index``, ``flag`` and ``res2`` (squared residual per candidate).
+    ``output="none"`` stops after step 2.  ``bins`` (optional) restricts step 2 to a subset of
+    the flattened frequencies; every other frequency gets the zero solution, which is exact when
+    the data spectrum vanishes there (a zero right-hand side has the zero Tikhonov solution).
     """
     zy = np.atleast_1d(np.asarray(zy, np.float64))
     zr = np.atleast_1d(np.asarray(zr, np.float64))
@@ -323,31 +323,31 @@ def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int =
     sel = np.arange(L * L) if bins is None else np.asarray(bins)
 
     def solve(a):
-        Z = np.zeros((L * L, Mp, Q), np.complex128)
+        """Tikhonov solutions on the selected frequencies, [len(sel), M', Q]."""
+        Z = np.empty((sel.size, Mp, Q), np.complex128)
         for s in range(0, sel.size, chunk):
             b = sel[s:s + chunk]
-            Z[b] = tikhonov_qr(Af[b], Uf[b], a * s2)
+            Z[s:s + b.size] = tikhonov_qr(Af[b], Uf[b], a * s2)
         return Z
 
     res2 = None
     flag = 0
     if alpha is not None:
         k = -1
-        Zh = solve(float(alpha))
+        Zs = solve(float(alpha))
     else:
         alphas = np.asarray(alphas, np.float64)
-        res2 = np.empty(alphas.size)
-        sols = []
-        for t, a in enumerate(alphas):
-            Z = solve(float(a))
-            res2[t] = residual_sq(Af[sel], Z[sel], Uf[sel]) * (sel.size / (L * L)) if bins is not None \
-                else residual_sq(Af, Z, Uf)
-            sols.append(Z)
+        res2 = np.array([residual_sq(Af[sel], solve(float(a)), Uf[sel], L * L) for a in alphas])
         k, flag = choose_alpha_index(res2, float(delta), tau)
-        Zh = sols[k]
-    Zs = np.transpose(Zh, (2, 1, 0)).reshape(Q, Mp, L, L)
-    zeta = idft2(Zs).real[..., :n, :n]
-    out = {"zeta": zeta, "alpha_index": k, "flag": flag, "res2": res2, "s2": s2}
+        Zs = solve(float(alphas[k]))
+    out = {"alpha_index": k, "flag": flag, "res2": res2, "s2": s2}
+    if output == "none":
+        return out
+    Zh = np.zeros((L * L, Mp, Q), np.complex128)
+    Zh[sel] = Zs
+    Zq = np.transpose(Zh, (2, 1, 0)).reshape(Q, Mp, L, L)
+    zeta = idft2(Zq).real[..., :n, :n]
+    out["zeta"] = zeta
     if sources is not None and output == "xi":
         out["xi"] = combine_sources(zeta, sources, n, x0, h, zr, A0)
     return out

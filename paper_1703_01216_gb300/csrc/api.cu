@@ -1,0 +1,355 @@
+// C ABI of the library (include/fr3d.h): argument checks, workspace planning and the launch
+// sequences of Algorithm 1 (Sec. 4-5) and of the forward operator (Eq. (4)-(6)).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ops.cuh"
+
+namespace fr3d {
+
+namespace {
+
+constexpr double kFourPi = 12.566370614359172953850573533118;
+constexpr size_t kChunkBytes = 128ull << 20;  // cap of the per-depth-chunk spectrum buffer
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int ensure_sources(Handle* H, const fr3d_sources* s) {
+  if (!s || s->q < 1 || s->n_points < 1 || !s->xyz) return FR3D_ERR_INVALID_ARG;
+  if ((long)s->q * s->n_points > FR3D_MAX_SOURCE_POINTS) return FR3D_ERR_UNSUPPORTED_SIZE;
+  if (!(s->A0 != 0.0) || !isfinite(s->A0)) return FR3D_ERR_INVALID_ARG;
+  const int np = s->q * s->n_points;
+  std::vector<double> key(3 + 3 * (size_t)np);
+  key[0] = s->q;
+  key[1] = s->n_points;
+  key[2] = s->A0;
+  for (int i = 0; i < 3 * np; ++i) {
+    if (!isfinite(s->xyz[i])) return FR3D_ERR_INVALID_ARG;
+    key[3 + i] = s->xyz[i];
+  }
+  if (key == H->src_key) return FR3D_OK;
+  if (!H->pts32) {
+    FR3D_CUDA_TRY(cudaMalloc(&H->pts32, sizeof(float4) * FR3D_MAX_SOURCE_POINTS));
+    FR3D_CUDA_TRY(cudaMalloc(&H->pts64, sizeof(double) * 3 * FR3D_MAX_SOURCE_POINTS));
+  }
+  std::vector<float4> p32(np);
+  for (int i = 0; i < np; ++i)
+    p32[i] = make_float4((float)s->xyz[3 * i], (float)s->xyz[3 * i + 1], (float)s->xyz[3 * i + 2], 0.f);
+  FR3D_CUDA_TRY(cudaMemcpy(H->pts32, p32.data(), sizeof(float4) * np, cudaMemcpyHostToDevice));
+  FR3D_CUDA_TRY(cudaMemcpy(H->pts64, s->xyz, sizeof(double) * 3 * np, cudaMemcpyHostToDevice));
+  H->src_key.swap(key);
+  return FR3D_OK;
+}
+
+SrcHost src_host(const Handle* H, int precision, const fr3d_sources* s) {
+  SrcHost r;
+  r.pts = precision == FR3D_PREC_FP64 ? (const void*)H->pts64 : (const void*)H->pts32;
+  r.L = s->n_points;
+  r.coef = -s->A0 / kFourPi;  // V0 = -A0/(4 pi) sum_l 1/|x - x_l| (Sec. 6)
+  return r;
+}
+
+bool valid_precision(int p) { return p == FR3D_PREC_FP32 || p == FR3D_PREC_FP64; }
+
+// ------------------------------------------------------------------ forward operator
+template <typename T>
+int fwd_impl(Handle* H, const T* zeta, int Q, T* U, cudaStream_t st) {
+  using C = typename Ops<T>::C;
+  const int n = H->n;
+  const long ps = (long)(n / 2 + 1) * n;
+  const size_t zb = align_up(sizeof(C) * ps * H->Mp), ub = align_up(sizeof(C) * ps * H->M);
+  FR3D_TRY(ensure_ws(H, zb + ub));
+  C* Zh = reinterpret_cast<C*>(H->ws);
+  C* Uh = reinterpret_cast<C*>((char*)H->ws + zb);
+  const T* A;
+  if constexpr (sizeof(T) == 4) A = H->A32;
+  else {
+    FR3D_TRY(build_dense64(H, st));
+    A = H->A64d;
+  }
+  int launches = 0;
+  for (int q = 0; q < Q; ++q) {
+    FR3D_TRY(Ops<T>::row_r2c(H, zeta + (long)q * H->Mp * n * n, (long)n * n, Zh, H->Mp, st));
+    FR3D_TRY(Ops<T>::col_plain(H, Zh, Zh, H->Mp, false, st));
+    FR3D_TRY(Ops<T>::contract_fwd(H, Zh, Uh, A, 1, st));
+    FR3D_TRY(Ops<T>::col_plain(H, Uh, Uh, H->M, true, st));
+    FR3D_TRY(Ops<T>::row_c2r_plain(H, Uh, U + (long)q * H->M * n * n, H->M, 1, 0, 0, st));
+    launches += 5;
+  }
+  H->last_launches = launches;
+  return FR3D_OK;
+}
+
+// ------------------------------------------------------------------ data transform + alpha rule
+template <typename T>
+int data_fft(Handle* H, const T* U, int Q, typename Ops<T>::C* Uh, cudaStream_t st) {
+  const int n = H->n;
+  FR3D_TRY(Ops<T>::row_r2c(H, U, (long)n * n, Uh, Q * H->M, st));
+  prof_mark(H, kStRowR2C, st);
+  FR3D_TRY(Ops<T>::col_plain(H, Uh, Uh, Q * H->M, false, st));
+  prof_mark(H, kStColFwd, st);
+  return FR3D_OK;
+}
+
+int check_alphas(const double* alphas, int n_alpha) {
+  if (!alphas || n_alpha < 1) return FR3D_ERR_INVALID_ARG;
+  if (n_alpha > FR3D_MAX_ALPHAS) return FR3D_ERR_UNSUPPORTED_SIZE;
+  for (int k = 0; k < n_alpha; ++k) {
+    if (!(alphas[k] > 0) || !isfinite(alphas[k])) return FR3D_ERR_INVALID_ARG;
+    if (k && !(alphas[k] > alphas[k - 1])) return FR3D_ERR_INVALID_ARG;
+  }
+  return FR3D_OK;
+}
+
+template <typename T>
+int choose_impl(Handle* H, const T* U, int Q, const double* alphas, int n_alpha, double delta, double tau,
+                int* alpha_idx, double* residuals, int* info, cudaStream_t st) {
+  using C = typename Ops<T>::C;
+  const long ps = (long)(H->n / 2 + 1) * H->n;
+  FR3D_TRY(ensure_ws(H, align_up(sizeof(C) * ps * Q * H->M)));
+  C* Uh = reinterpret_cast<C*>(H->ws);
+  FR3D_TRY(data_fft<T>(H, U, Q, Uh, st));
+  FR3D_TRY(alpha_tables(H, alphas, n_alpha, st));
+  const double thr = tau * delta;
+  FR3D_TRY(Ops<T>::alpha_choose(H, Uh, Q * H->M, n_alpha, thr * thr, alpha_idx, residuals, info, st));
+  H->last_launches = 3;
+  return FR3D_OK;
+}
+
+// ------------------------------------------------------------------ Algorithm 1
+struct InvertPlan {
+  size_t uh_off, t_off, uin_off, out_off, total;
+  int chunk;
+};
+
+template <typename T>
+InvertPlan plan_invert(const Handle* H, int Q, bool host_io, int output) {
+  using C = typename Ops<T>::C;
+  const int n = H->n;
+  const size_t ps_b = sizeof(C) * (size_t)(n / 2 + 1) * n;
+  InvertPlan p;
+  p.uh_off = 0;
+  size_t off = align_up(ps_b * Q * H->M);
+  const size_t per_j = ps_b * Q;
+  int chunk = (int)std::max<size_t>(1, std::min<size_t>(H->Mp, kChunkBytes / per_j));
+  const int nch = (H->Mp + chunk - 1) / chunk;
+  chunk = (H->Mp + nch - 1) / nch;
+  p.chunk = chunk;
+  p.t_off = off;
+  off += align_up(per_j * chunk);
+  p.uin_off = p.out_off = 0;
+  if (host_io) {
+    p.uin_off = off;
+    off += align_up(sizeof(T) * (size_t)Q * H->M * n * n);
+    p.out_off = off;
+    off += align_up(sizeof(T) * (size_t)(output == FR3D_OUT_XI ? 1 : Q) * H->Mp * n * n);
+  }
+  p.total = off;
+  return p;
+}
+
+int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
+  if (!o || Q < 1) return FR3D_ERR_INVALID_ARG;
+  if (!valid_precision(o->precision)) return FR3D_ERR_INVALID_ARG;
+  if (H->M != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
+  if (o->output != FR3D_OUT_XI && o->output != FR3D_OUT_ZETA) return FR3D_ERR_INVALID_ARG;
+  if (o->alpha_mode == FR3D_ALPHA_FIXED) {
+    if (!(o->alpha > 0) || !isfinite(o->alpha)) return FR3D_ERR_INVALID_ARG;
+  } else if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
+    FR3D_TRY(check_alphas(o->alphas, o->n_alpha));
+    if (!(o->delta >= 0) || !isfinite(o->delta) || !(o->tau > 0) || !isfinite(o->tau)) return FR3D_ERR_INVALID_ARG;
+  } else {
+    return FR3D_ERR_INVALID_ARG;
+  }
+  if (o->output == FR3D_OUT_XI) {
+    if (!o->sources) return FR3D_ERR_INVALID_ARG;
+    if (o->sources->q != Q) return FR3D_ERR_INVALID_ARG;
+    FR3D_TRY(ensure_sources(H, o->sources));
+  }
+  return FR3D_OK;
+}
+
+template <typename T>
+int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out, const InvertPlan& p,
+                cudaStream_t st) {
+  using C = typename Ops<T>::C;
+  C* Uh = reinterpret_cast<C*>((char*)H->ws + p.uh_off);
+  C* Tb = reinterpret_cast<C*>((char*)H->ws + p.t_off);
+  int launches = 0;
+  prof_begin(H, st);
+  // step 1: 2D DFT of the data
+  FR3D_TRY(data_fft<T>(H, U, Q, Uh, st));
+  launches += 2;
+  // step 2 (parameter): alpha
+  const int* aidx;
+  const T* D;
+  if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    prof_mark(H, kStTable, st);
+    int* idx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
+    const double thr = o->tau * o->delta;
+    FR3D_TRY(Ops<T>::alpha_choose(H, Uh, Q * H->M, o->n_alpha, thr * thr, idx, o->residuals, o->info, st));
+    prof_mark(H, kStAlpha, st);
+    launches += 1;
+    aidx = idx;
+    if constexpr (sizeof(T) == 4) D = H->D32;
+    else D = H->D64;
+  } else {
+    FR3D_TRY(fixed_table(H, o->alpha, st));
+    prof_mark(H, kStTable, st);
+    aidx = H->zero_idx;
+    if constexpr (sizeof(T) == 4) D = H->Dfix32;
+    else D = H->Dfix64;
+    if (o->alpha_idx) FR3D_CUDA_TRY(cudaMemsetAsync(o->alpha_idx, 0, sizeof(int), st));
+    if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
+  }
+  const T* A;
+  if constexpr (sizeof(T) == 4) A = H->A32;
+  else {
+    FR3D_TRY(build_dense64(H, st));
+    A = H->A64d;
+  }
+  // step 2 (solve) + step 3 (inverse DFT) + step 4 (xi = zeta / V0), by chunks of depths
+  for (int j0 = 0; j0 < H->Mp; j0 += p.chunk) {
+    const int nj = std::min(p.chunk, H->Mp - j0);
+    FR3D_TRY(Ops<T>::col_solve1(H, Uh, Tb, A, D, aidx, Q, j0, nj, st));
+    prof_mark(H, kStColSolve, st);
+    if (o->output == FR3D_OUT_XI)
+      FR3D_TRY(Ops<T>::row_c2r_xi(H, Tb, out, nj, Q, j0, src_host(H, o->precision, o->sources), st));
+    else
+      FR3D_TRY(Ops<T>::row_c2r_plain(H, Tb, out, nj * Q, Q, j0, H->Mp, st));
+    prof_mark(H, kStRowC2R, st);
+    launches += 2;
+  }
+  H->last_launches = launches;
+  return FR3D_OK;
+}
+
+}  // namespace
+
+}  // namespace fr3d
+
+using fr3d::Handle;
+
+extern "C" int fr3d_fwd_apply(fr3d_handle* h, const void* zeta, int Q, void* U, int precision, void* stream) {
+  if (!h || !zeta || !U || Q < 1 || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == FR3D_PREC_FP64) return fr3d::fwd_impl<double>(H, (const double*)zeta, Q, (double*)U, st);
+  return fr3d::fwd_impl<float>(H, (const float*)zeta, Q, (float*)U, st);
+}
+
+extern "C" int fr3d_zeta_from_xi(fr3d_handle* h, const void* xi, const fr3d_sources* sources, void* zeta,
+                                 int precision, void* stream) {
+  if (!h || !xi || !zeta || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  FR3D_TRY(fr3d::ensure_sources(H, sources));
+  cudaStream_t st = (cudaStream_t)stream;
+  const fr3d::SrcHost s = fr3d::src_host(H, precision, sources);
+  H->last_launches = 1;
+  if (precision == FR3D_PREC_FP64)
+    return fr3d::Ops<double>::zeta_from_xi(H, (const double*)xi, (double*)zeta, sources->q, s, st);
+  return fr3d::Ops<float>::zeta_from_xi(H, (const float*)xi, (float*)zeta, sources->q, s, st);
+}
+
+extern "C" int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const double* alphas, int n_alpha,
+                                 double delta, double tau, int precision, int* alpha_idx, double* residuals,
+                                 int* info, void* stream) {
+  if (!h || !U || Q < 1 || !alpha_idx || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  FR3D_TRY(fr3d::check_alphas(alphas, n_alpha));
+  if (!(delta >= 0) || !isfinite(delta) || !(tau > 0) || !isfinite(tau)) return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  if (H->M != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == FR3D_PREC_FP64)
+    return fr3d::choose_impl<double>(H, (const double*)U, Q, alphas, n_alpha, delta, tau, alpha_idx, residuals,
+                                     info, st);
+  return fr3d::choose_impl<float>(H, (const float*)U, Q, alphas, n_alpha, delta, tau, alpha_idx, residuals, info,
+                                  st);
+}
+
+extern "C" int fr3d_invert(fr3d_handle* h, const void* U, int Q, const fr3d_invert_opts* opts, void* out,
+                           void* stream) {
+  if (!h || !U || !out) return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  FR3D_TRY(fr3d::check_invert_args(H, Q, opts));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (opts->precision == FR3D_PREC_FP64) {
+    const fr3d::InvertPlan p = fr3d::plan_invert<double>(H, Q, false, opts->output);
+    FR3D_TRY(fr3d::ensure_ws(H, p.total));
+    return fr3d::invert_impl<double>(H, (const double*)U, Q, opts, (double*)out, p, st);
+  }
+  const fr3d::InvertPlan p = fr3d::plan_invert<float>(H, Q, false, opts->output);
+  FR3D_TRY(fr3d::ensure_ws(H, p.total));
+  return fr3d::invert_impl<float>(H, (const float*)U, Q, opts, (float*)out, p, st);
+}
+
+template <typename T>
+static int invert_host_t(Handle* H, const void* U_host, int Q, const fr3d_invert_opts* o, void* out_host,
+                         cudaStream_t st) {
+  const fr3d::InvertPlan p = fr3d::plan_invert<T>(H, Q, true, o->output);
+  FR3D_TRY(fr3d::ensure_ws(H, p.total));
+  const int n = H->n;
+  T* Ud = reinterpret_cast<T*>((char*)H->ws + p.uin_off);
+  T* Od = reinterpret_cast<T*>((char*)H->ws + p.out_off);
+  const size_t in_b = sizeof(T) * (size_t)Q * H->M * n * n;
+  const size_t out_b = sizeof(T) * (size_t)(o->output == FR3D_OUT_XI ? 1 : Q) * H->Mp * n * n;
+  FR3D_CUDA_TRY(cudaMemcpyAsync(Ud, U_host, in_b, cudaMemcpyHostToDevice, st));
+  FR3D_TRY(fr3d::invert_impl<T>(H, Ud, Q, o, Od, p, st));
+  FR3D_CUDA_TRY(cudaMemcpyAsync(out_host, Od, out_b, cudaMemcpyDeviceToHost, st));
+  FR3D_CUDA_TRY(cudaStreamSynchronize(st));
+  return FR3D_OK;
+}
+
+extern "C" int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_invert_opts* opts,
+                                void* out_host, void* stream) {
+  if (!h || !U_host || !out_host) return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  FR3D_TRY(fr3d::check_invert_args(H, Q, opts));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (opts->precision == FR3D_PREC_FP64) return invert_host_t<double>(H, U_host, Q, opts, out_host, st);
+  return invert_host_t<float>(H, U_host, Q, opts, out_host, st);
+}
+
+extern "C" int fr3d_last_launch_count(fr3d_handle* h) { return h ? h->h.last_launches : -1; }
+
+extern "C" int fr3d_profile_enable(fr3d_handle* h, int enable) {
+  if (!h) return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  if (enable && !H->ev[0]) {
+    for (int i = 0; i < Handle::kMaxEv; ++i) FR3D_CUDA_TRY(cudaEventCreate(&H->ev[i]));
+  }
+  H->prof_on = enable != 0;
+  H->n_ev = 0;
+  return FR3D_OK;
+}
+
+extern "C" int fr3d_profile_read(fr3d_handle* h, int* kinds, float* ms, int cap) {
+  if (!h || (cap > 0 && (!kinds || !ms))) return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  if (H->n_ev < 2) return 0;
+  FR3D_CUDA_TRY(cudaEventSynchronize(H->ev[H->n_ev - 1]));
+  const int n = std::min(cap, H->n_ev - 1);
+  for (int i = 0; i < n; ++i) {
+    kinds[i] = H->ev_kind[i];
+    FR3D_CUDA_TRY(cudaEventElapsedTime(&ms[i], H->ev[i], H->ev[i + 1]));
+  }
+  return n;
+}
+
+extern "C" const char* fr3d_status_string(int s) {
+  switch (s) {
+    case FR3D_OK: return "ok";
+    case FR3D_ERR_INVALID_ARG: return "invalid argument";
+    case FR3D_ERR_BAD_GEOMETRY: return "bad geometry (R and Y must be disjoint: every z_i - z'_j non-zero; h > 0)";
+    case FR3D_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case FR3D_ERR_OOM: return "device allocation failed";
+    case FR3D_ERR_CUDA: return "CUDA runtime error";
+    case FR3D_ERR_TIMEOUT: return "bounded device wait gave up";
+    case FR3D_ERR_NONFINITE_INPUT: return "non-finite input";
+    default: return "unknown status";
+  }
+}

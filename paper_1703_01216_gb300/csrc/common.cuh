@@ -1,0 +1,126 @@
+// Shared host/device declarations of the fr3d library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/fr3d.h"
+
+namespace fr3d {
+
+#define FR3D_CUDA_TRY(expr)                              \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) {                             \
+      if (e_ == cudaErrorMemoryAllocation) return FR3D_ERR_OOM; \
+      return FR3D_ERR_CUDA;                              \
+    }                                                    \
+  } while (0)
+
+#define FR3D_TRY(expr)        \
+  do {                        \
+    int s_ = (expr);          \
+    if (s_ < 0) return s_;    \
+  } while (0)
+
+// Transform lengths with a radix plan (fft_engine.cuh); the 2D grid n must have n and n/2 in it.
+static const int kLengths[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+static const int kNumLengths = 13;
+
+// Frequency classes: (kx, ky) of the half spectrum (kx in [0, n/2], ky in [0, n)) folded by the
+// symmetries of the sampled kernel (k -> -k per axis and kx <-> ky on a square grid):
+// u = kx, v = min(ky, n - ky), class (p, q) = (max, min), index p (p + 1) / 2 + q.
+__host__ __device__ __forceinline__ int class_of(int kx, int ky, int n) {
+  int v = ky <= n - ky ? ky : n - ky;
+  int p = kx > v ? kx : v, q = kx > v ? v : kx;
+  return p * (p + 1) / 2 + q;
+}
+__host__ __device__ __forceinline__ int num_classes(int n) { return (n / 2 + 1) * (n / 2 + 2) / 2; }
+
+struct Handle {
+  int dev = 0;
+  int n = 0, M = 0, Mp = 0, C = 0;
+  double x0 = 0, y0 = 0, h = 0;
+  std::vector<double> zr, nu, zy;
+  // kernel tables (owned)
+  double* A64 = nullptr;      // [C][M][Mp]   nu_j K~(class c; z_i - z'_j)
+  double* nrm = nullptr;      // [C]          ||A^(c)||_F^2
+  double* s2 = nullptr;       // [1]          max_c nrm[c]
+  float* A32 = nullptr;       // [M][Mp][n/2+1][n]   dense per half-spectrum bin
+  double* A64d = nullptr;     // same, FP64 (built on the first FP64 call)
+  double* zr64 = nullptr;     // [Mp] depths of R on the device
+  float* zr32 = nullptr;
+  double s2_host = -1.0;
+  // twiddles exp(-2 pi i t / L) for every supported L, FP32 and FP64
+  float2* tw32 = nullptr;
+  double2* tw64 = nullptr;
+  int tw_off[kNumLengths] = {0};
+  // alpha tables, keyed by the candidate list
+  std::vector<double> alpha_key;
+  double* Ft = nullptr;       // [C][n_alpha]  ((alpha s^2) / (nrm + alpha s^2))^2
+  float* D32 = nullptr;       // [n_alpha][C]  1 / (n^2 (nrm + alpha s^2))
+  double* D64 = nullptr;      // [n_alpha][C]
+  int alpha_cap = 0;
+  // fixed-alpha table
+  double fixed_key = -1.0;
+  float* Dfix32 = nullptr;    // [C]
+  double* Dfix64 = nullptr;   // [C]
+  // sources, keyed by content
+  std::vector<double> src_key;
+  float4* pts32 = nullptr;    // [Q*L] (x, y, z, 0)
+  double* pts64 = nullptr;    // [Q*L*3]
+  int src_cap = 0;
+  // small device words
+  unsigned* counter = nullptr;   // last-block counter (self-resetting)
+  int* idx_scratch = nullptr;    // chosen alpha index when the caller passes none
+  int* zero_idx = nullptr;       // constant 0
+  int* info_scratch = nullptr;
+  double* partials = nullptr;    // [blocks][n_alpha]
+  int partial_cap = 0;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int last_launches = 0;
+  // stage profiling: events recorded between consecutive launches of one call
+  static constexpr int kMaxEv = 96;
+  bool prof_on = false;
+  cudaEvent_t ev[kMaxEv] = {};
+  int ev_kind[kMaxEv] = {0};
+  int n_ev = 0;
+  cudaStream_t create_stream = nullptr;
+  bool synced = false;
+};
+
+// launch-count bookkeeping (host)
+struct Launches {
+  int n = 0;
+  void add(int k = 1) { n += k; }
+};
+
+int ensure_ws(Handle* H, size_t bytes);
+
+// stage kinds reported by fr3d_profile_read
+enum StageKind { kStRowR2C = 0, kStColFwd = 1, kStAlpha = 2, kStColSolve = 3, kStRowC2R = 4, kStTable = 5,
+                 kStContract = 6, kStColInv = 7, kStOther = 8 };
+inline void prof_begin(Handle* H, cudaStream_t st) {
+  H->n_ev = 0;
+  if (!H->prof_on) return;
+  cudaEventRecord(H->ev[0], st);
+  H->n_ev = 1;
+}
+inline void prof_mark(Handle* H, int kind, cudaStream_t st) {
+  if (!H->prof_on || H->n_ev <= 0 || H->n_ev >= Handle::kMaxEv) return;
+  H->ev_kind[H->n_ev - 1] = kind;
+  cudaEventRecord(H->ev[H->n_ev], st);
+  ++H->n_ev;
+}
+int twiddle_offset(const Handle* H, int L);
+
+}  // namespace fr3d
+
+struct fr3d_handle {
+  fr3d::Handle h;
+};

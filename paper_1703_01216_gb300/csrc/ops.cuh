@@ -1,0 +1,44 @@
+// Host-side launchers of the per-precision kernels (internal interface between api.cu and
+// ops_f32.cu / ops_f64.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace fr3d {
+
+struct SrcHost {
+  const void* pts;  // float4* (FP32) or double* (FP64), device
+  int L;
+  double coef;      // -A0 / (4 pi)
+};
+
+template <typename T> struct Ops {
+  using C = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  // row pass real -> half spectrum for nplanes planes (plane stride in_ps reals)
+  static int row_r2c(const Handle* H, const T* in, long in_ps, C* out, int nplanes, cudaStream_t st);
+  // column pass in place/out of place, plain
+  static int col_plain(const Handle* H, const C* in, C* out, int nplanes, bool inverse, cudaStream_t st);
+  // inverse column pass with the M = 1 Tikhonov weights; output planes jc * Q + q, jc < nj
+  static int col_solve1(const Handle* H, const C* Uh, C* out, const T* A, const T* D, const int* aidx, int Q,
+                        int j0, int nj, cudaStream_t st);
+  // row pass half spectrum -> real; input plane ip -> output plane (ip % Q) * out_stride + j0 + ip / Q
+  static int row_c2r_plain(const Handle* H, const C* in, T* out, int nplanes, int Q, int j0, int out_stride,
+                           cudaStream_t st);
+  // row pass with the combination xi = sum_q V0_q zeta_q / sum_q V0_q^2 for depths j0 .. j0 + nj - 1
+  static int row_c2r_xi(const Handle* H, const C* in, T* out, int nj, int Q, int j0, const SrcHost& src,
+                        cudaStream_t st);
+  // U~[q][i] = (1/n^2) sum_j A[i][j] zeta~[q][j] for every half-spectrum bin
+  static int contract_fwd(const Handle* H, const C* Zh, C* Uh, const T* A, int Q, cudaStream_t st);
+  // zeta[q][j] = xi[j] * V0_q
+  static int zeta_from_xi(const Handle* H, const T* xi, T* zeta, int Q, const SrcHost& src, cudaStream_t st);
+  // discrepancy choice over the cached alpha tables (M = 1)
+  static int alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, double thr2, int* aidx,
+                          double* residuals, int* info, cudaStream_t st);
+};
+
+// precision-independent table builders (alpha tables, fixed alpha)
+int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st);
+int fixed_table(Handle* H, double alpha, cudaStream_t st);
+int build_dense64(Handle* H, cudaStream_t st);
+
+}  // namespace fr3d

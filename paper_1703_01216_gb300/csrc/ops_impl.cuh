@@ -1,0 +1,322 @@
+// Per-precision kernel launchers (included once per precision by ops_f32.cu / ops_f64.cu).
+#pragma once
+
+#include <type_traits>
+
+#include "fft2d.cuh"
+#include "ops.cuh"
+
+namespace fr3d {
+
+#define FR3D_FOR_EACH_N(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+template <typename K> static int set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+      return FR3D_ERR_CUDA;
+  }
+  return FR3D_OK;
+}
+
+template <typename T> static const typename cpx<T>::t* tw_of(const Handle* H, int L) {
+  const int off = twiddle_offset(H, L);
+  if constexpr (sizeof(T) == 4) return H->tw32 + off;
+  else return H->tw64 + off;
+}
+
+template <typename T, int N>
+static int row_r2c_n(const Handle* H, const T* in, long in_ps, typename cpx<T>::t* out, int nplanes, cudaStream_t st) {
+  constexpr size_t sm = row_r2c_smem<T, N>();
+  auto kern = k_row_r2c<T, N>;
+  FR3D_TRY(set_smem(kern, sm));
+  dim3 grid(N / RowTile<T, N>::v, nplanes);
+  kern<<<grid, kThreads, sm, st>>>(in, in_ps, out, tw_of<T>(H, N / 2), tw_of<T>(H, N));
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+template <typename T, int N, bool INV, class Op>
+static int col_n(const Handle* H, const Op& op, int nplanes, cudaStream_t st) {
+  constexpr size_t sm = col_smem<T, N>();
+  auto kern = k_col_fft<T, N, INV, Op>;
+  FR3D_TRY(set_smem(kern, sm));
+  constexpr int TC = ColTile<T, N>::v;
+  dim3 grid((N / 2 + 1 + TC - 1) / TC, nplanes);
+  kern<<<grid, kThreads, sm, st>>>(op, tw_of<T>(H, N));
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+template <typename T, int N, int MODE>
+static int row_c2r_n(const Handle* H, const typename cpx<T>::t* in, T* out, int nplanes, int Q, int j0,
+                     int out_stride, const SrcHost& src, cudaStream_t st) {
+  constexpr size_t sm = row_c2r_smem<T, N, MODE>();
+  auto kern = k_row_c2r<T, N, MODE>;
+  FR3D_TRY(set_smem(kern, sm));
+  typename SrcOf<T>::t s;
+  s.pts = reinterpret_cast<decltype(s.pts)>(src.pts);
+  s.L = src.L;
+  s.coef = (T)src.coef;
+  RowGeom g{H->x0, H->y0, H->h};
+  const T* zr;
+  if constexpr (sizeof(T) == 4) zr = H->zr32;
+  else zr = H->zr64;
+  dim3 grid(N / row_c2r_tile<T, N, MODE>(), nplanes);
+  kern<<<grid, kThreads, sm, st>>>(in, out, Q, j0, out_stride, s, g, zr, tw_of<T>(H, N / 2), tw_of<T>(H, N));
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+template <typename T>
+int Ops<T>::row_r2c(const Handle* H, const T* in, long in_ps, C* out, int nplanes, cudaStream_t st) {
+  switch (H->n) {
+#define X(N) \
+  case N: return row_r2c_n<T, N>(H, in, in_ps, out, nplanes, st);
+    FR3D_FOR_EACH_N(X)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+template <typename T>
+int Ops<T>::col_plain(const Handle* H, const C* in, C* out, int nplanes, bool inverse, cudaStream_t st) {
+  ColPlain<T> op{in, out, (long)(H->n / 2 + 1) * H->n};
+  switch (H->n) {
+#define X(N)                                                         \
+  case N:                                                            \
+    return inverse ? col_n<T, N, true>(H, op, nplanes, st) : col_n<T, N, false>(H, op, nplanes, st);
+    FR3D_FOR_EACH_N(X)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+template <typename T>
+int Ops<T>::col_solve1(const Handle* H, const C* Uh, C* out, const T* A, const T* D, const int* aidx, int Q, int j0,
+                       int nj, cudaStream_t st) {
+  ColSolve1<T> op;
+  op.Uh = Uh;
+  op.out = out;
+  op.A = A;
+  op.D = D;
+  op.aidx = aidx;
+  op.ps = (long)(H->n / 2 + 1) * H->n;
+  op.Q = Q;
+  op.j0 = j0;
+  op.n = H->n;
+  op.Cn = H->C;
+  op.drow = nullptr;
+  switch (H->n) {
+#define X(N) \
+  case N: return col_n<T, N, true>(H, op, nj * Q, st);
+    FR3D_FOR_EACH_N(X)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+template <typename T>
+int Ops<T>::row_c2r_plain(const Handle* H, const C* in, T* out, int nplanes, int Q, int j0, int out_stride,
+                          cudaStream_t st) {
+  SrcHost none{nullptr, 0, 0.0};
+  switch (H->n) {
+#define X(N) \
+  case N: return row_c2r_n<T, N, 0>(H, in, out, nplanes, Q, j0, out_stride, none, st);
+    FR3D_FOR_EACH_N(X)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+template <typename T>
+int Ops<T>::row_c2r_xi(const Handle* H, const C* in, T* out, int nj, int Q, int j0, const SrcHost& src,
+                       cudaStream_t st) {
+  switch (H->n) {
+#define X(N) \
+  case N: return row_c2r_n<T, N, 1>(H, in, out, nj, Q, j0, 0, src, st);
+    FR3D_FOR_EACH_N(X)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+// ---------------------------------------------------------------- forward contraction (Eq. (5)-(6))
+template <typename T, typename C>
+__global__ void k_contract_fwd(const C* __restrict__ Zh, C* __restrict__ Uh, const T* __restrict__ A, int Q, int M,
+                               int Mp, long ps, T inv_n2) {
+  const long total = (long)Q * M * ps;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const long bin = idx % ps;
+    const int qi = (int)(idx / ps);
+    const int q = qi / M, i = qi - q * M;
+    const C* z = Zh + (long)q * Mp * ps + bin;
+    const T* a = A + (long)i * Mp * ps + bin;
+    T re = 0, im = 0;
+    for (int j = 0; j < Mp; ++j) {
+      const T w = a[(long)j * ps];
+      const C v = z[(long)j * ps];
+      re += w * v.x;
+      im += w * v.y;
+    }
+    C r;
+    r.x = re * inv_n2;
+    r.y = im * inv_n2;
+    Uh[idx] = r;
+  }
+}
+
+template <typename T>
+int Ops<T>::contract_fwd(const Handle* H, const C* Zh, C* Uh, const T* A, int Q, cudaStream_t st) {
+  const long ps = (long)(H->n / 2 + 1) * H->n;
+  const long total = (long)Q * H->M * ps;
+  const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+  k_contract_fwd<T, C><<<blocks, 256, 0, st>>>(Zh, Uh, A, Q, H->M, H->Mp, ps, (T)(1.0 / ((double)H->n * H->n)));
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- zeta = xi V0 (Sec. 2)
+template <typename T, typename S>
+__global__ void k_zeta_from_xi(const T* __restrict__ xi, T* __restrict__ zeta, int Q, int Mp, int n, S src,
+                               RowGeom g, const T* __restrict__ zr) {
+  const long plane = (long)n * n;
+  const long total = (long)Q * Mp * plane;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const long pix = idx % plane;
+    const int qj = (int)(idx / plane);
+    const int q = qj / Mp, j = qj - q * Mp;
+    const int a = (int)(pix % n), b = (int)(pix / n);
+    const T x = (T)g.x0 + ((T)a + (T)0.5) * (T)g.h, y = (T)g.y0 + ((T)b + (T)0.5) * (T)g.h;
+    zeta[idx] = xi[(long)j * plane + pix] * v0_at(src, q, x, y, zr[j]);
+  }
+}
+
+template <typename T>
+int Ops<T>::zeta_from_xi(const Handle* H, const T* xi, T* zeta, int Q, const SrcHost& src, cudaStream_t st) {
+  typename SrcOf<T>::t s;
+  s.pts = reinterpret_cast<decltype(s.pts)>(src.pts);
+  s.L = src.L;
+  s.coef = (T)src.coef;
+  RowGeom g{H->x0, H->y0, H->h};
+  const T* zr;
+  if constexpr (sizeof(T) == 4) zr = H->zr32;
+  else zr = H->zr64;
+  const long total = (long)Q * H->Mp * H->n * H->n;
+  const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+  k_zeta_from_xi<T><<<blocks, 256, 0, st>>>(xi, zeta, Q, H->Mp, H->n, s, g, zr);
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- discrepancy principle (Sec. 4)
+// Power of the data spectrum in frequency class c, summed over planes, with the Hermitian weight
+// of each stored half-spectrum bin (1 on the kx = 0 and kx = n/2 columns, 2 elsewhere).
+template <typename C>
+__device__ double class_power(const C* __restrict__ Uh, long ps, int nplanes, int n, int c) {
+  int p = (int)((sqrt(8.0 * c + 1.0) - 1.0) * 0.5);
+  while ((p + 1) * (p + 2) / 2 <= c) ++p;
+  while (p * (p + 1) / 2 > c) --p;
+  const int q = c - p * (p + 1) / 2;
+  double acc = 0.0;
+  auto add = [&](int kx, int ky) {
+    const double wt = (kx == 0 || 2 * kx == n) ? 1.0 : 2.0;
+    for (int pl = 0; pl < nplanes; ++pl) {
+      const C v = Uh[pl * ps + (long)kx * n + ky];
+      const double re = (double)v.x, im = (double)v.y;
+      acc += wt * (re * re + im * im);
+    }
+  };
+  add(p, q);
+  if (q != 0 && 2 * q != n) add(p, n - q);
+  if (p != q) {
+    add(q, p);
+    if (p != 0 && 2 * p != n) add(q, n - p);
+  }
+  return acc;
+}
+
+constexpr int kAlphaCPB = 64;  // classes per block
+
+// r^2(alpha_k) = n^-2 sum_c Ft[c][k] P[c]  (Parseval; M = 1 closed form of ||A zeta_alpha - U||^2),
+// deterministic: per-block partial sums in fixed order, reduced by the last block to finish.
+template <typename C>
+__global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
+                                                      const double* __restrict__ Ft, int na, double thr2, double inv_n2,
+                                                      double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                      int* __restrict__ aidx, double* __restrict__ res_out,
+                                                      int* __restrict__ info) {
+  __shared__ double sP[kAlphaCPB];
+  __shared__ double red[256];
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * kAlphaCPB;
+  if (tid < kAlphaCPB) {
+    const int c = c0 + tid;
+    sP[tid] = c < Cn ? class_power(Uh, ps, nplanes, n, c) : 0.0;
+  }
+  __syncthreads();
+  const int S = 256 / na;
+  if (tid < S * na) {
+    const int k = tid % na, sub = tid / na;
+    double acc = 0.0;
+    for (int cc = sub; cc < kAlphaCPB; cc += S) {
+      const int c = c0 + cc;
+      if (c < Cn) acc = fma(__ldg(Ft + (long)c * na + k), sP[cc], acc);
+    }
+    red[tid] = acc;
+  }
+  __syncthreads();
+  if (tid < na) {
+    double s = 0.0;
+    for (int sub = 0; sub < S; ++sub) s += red[sub * na + tid];
+    partials[(long)blockIdx.x * na + tid] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double r2[FR3D_MAX_ALPHAS];
+  if (tid < na) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + (long)b * na + tid);
+    r2[tid] = s * inv_n2;
+    if (res_out) res_out[tid] = s * inv_n2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int best = -1, flags = 0, ok = 0;
+    for (int k = 0; k < na; ++k) {
+      if (!isfinite(r2[k])) flags |= FR3D_INFO_NONFINITE;
+      if (r2[k] <= thr2) {
+        best = k;
+        ++ok;
+      }
+    }
+    if (best < 0) {
+      best = 0;
+      flags |= FR3D_INFO_ALPHA_NONE_SATISFIES;
+    } else if (ok == na) {
+      flags |= FR3D_INFO_ALPHA_ALL_SATISFY;
+    }
+    *aidx = best;
+    if (info) *info = flags;
+    *counter = 0u;
+  }
+}
+
+template <typename T>
+int Ops<T>::alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, double thr2, int* aidx, double* residuals,
+                         int* info, cudaStream_t st) {
+  const int blocks = (H->C + kAlphaCPB - 1) / kAlphaCPB;
+  if (H->partial_cap < blocks * n_alpha) {
+    if (H->partials) cudaFree(H->partials);
+    H->partials = nullptr;
+    H->partial_cap = 0;
+    FR3D_CUDA_TRY(cudaMalloc(&H->partials, sizeof(double) * blocks * FR3D_MAX_ALPHAS));
+    H->partial_cap = blocks * FR3D_MAX_ALPHAS;
+  }
+  const long ps = (long)(H->n / 2 + 1) * H->n;
+  k_alpha_choose<C><<<blocks, 256, 0, st>>>(Uh, ps, nplanes, H->n, H->C, H->Ft, n_alpha, thr2,
+                                            1.0 / ((double)H->n * H->n), H->partials, H->counter, aidx, residuals,
+                                            info);
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+}  // namespace fr3d

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libfr3d.so (include/fr3d.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts Python
+values and torch CUDA tensors (device memory and streams only) into the C ABI's
+pointers and sizes, and raises Fr3dError on a negative status.  There is no
+fallback: if the library is missing, ``load()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libfr3d.so")
+
+OK = 0
+PREC_FP32, PREC_FP64 = 0, 1
+ALPHA_FIXED, ALPHA_DISCREPANCY = 0, 1
+OUT_ZETA, OUT_XI = 0, 1
+INFO_ALPHA_NONE_SATISFIES, INFO_ALPHA_ALL_SATISFY, INFO_NONFINITE = 1, 2, 4
+K_DZ_INV_R = 0
+MAX_ALPHAS = 128
+MAX_SOURCE_POINTS = 256
+
+_dp = ct.POINTER(ct.c_double)
+
+
+class Geometry(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("x0", ct.c_double), ("y0", ct.c_double),
+                ("hx", ct.c_double), ("hy", ct.c_double), ("pad", ct.c_int), ("nzr", ct.c_int),
+                ("zr", _dp), ("nu", _dp), ("nzy", ct.c_int), ("zy", _dp), ("kernel_kind", ct.c_int)]
+
+
+class Sources(ct.Structure):
+    _fields_ = [("q", ct.c_int), ("n_points", ct.c_int), ("xyz", _dp), ("A0", ct.c_double)]
+
+
+class InvertOpts(ct.Structure):
+    _fields_ = [("alpha_mode", ct.c_int), ("alpha", ct.c_double), ("alphas", _dp), ("n_alpha", ct.c_int),
+                ("delta", ct.c_double), ("tau", ct.c_double), ("output", ct.c_int), ("precision", ct.c_int),
+                ("sources", ct.POINTER(Sources)), ("alpha_idx", ct.c_void_p), ("residuals", ct.c_void_p),
+                ("info", ct.c_void_p)]
+
+
+class Fr3dError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+# the names the C ABI exports (include/fr3d.h)
+EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", "fr3d_fwd_apply",
+           "fr3d_zeta_from_xi", "fr3d_choose_alpha", "fr3d_invert", "fr3d_invert_host",
+           "fr3d_last_launch_count", "fr3d_profile_enable", "fr3d_profile_read", "fr3d_status_string")
+
+
+def load(path: str | None = None):
+    """Load libfr3d.so (built by paper_1703_01216_gb300.build); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_1703_01216_gb300.build.build()")
+    lib = ct.CDLL(p)
+    vp, i, d = ct.c_void_p, ct.c_int, ct.c_double
+    lib.fr3d_kernel_transform.argtypes = [ct.POINTER(Geometry), ct.POINTER(vp), vp]
+    lib.fr3d_handle_destroy.argtypes = [vp]
+    lib.fr3d_handle_destroy.restype = None
+    lib.fr3d_handle_query.argtypes = [vp, ct.POINTER(i), ct.POINTER(i), ct.POINTER(i), ct.POINTER(d)]
+    lib.fr3d_fwd_apply.argtypes = [vp, vp, i, vp, i, vp]
+    lib.fr3d_zeta_from_xi.argtypes = [vp, vp, ct.POINTER(Sources), vp, i, vp]
+    lib.fr3d_choose_alpha.argtypes = [vp, vp, i, _dp, i, d, d, i, vp, vp, vp, vp]
+    lib.fr3d_invert.argtypes = [vp, vp, i, ct.POINTER(InvertOpts), vp, vp]
+    lib.fr3d_invert_host.argtypes = [vp, vp, i, ct.POINTER(InvertOpts), vp, vp]
+    lib.fr3d_last_launch_count.argtypes = [vp]
+    lib.fr3d_profile_enable.argtypes = [vp, i]
+    lib.fr3d_profile_read.argtypes = [vp, ct.POINTER(i), ct.POINTER(ct.c_float), i]
+    lib.fr3d_status_string.argtypes = [i]
+    lib.fr3d_status_string.restype = ct.c_char_p
+    for name in EXPORTS:
+        if name not in ("fr3d_handle_destroy", "fr3d_status_string"):
+            getattr(lib, name).restype = ct.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().fr3d_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status < 0:
+        raise Fr3dError(status, what)
+    return status
+
+
+def _f64(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a, a.ctypes.data_as(_dp)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ct.c_void_p(stream)
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ct.c_void_p(t)
+    if hasattr(t, "data_ptr"):
+        return ct.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return ct.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+def make_sources(points, A0: float = 1.0):
+    """points [Q, L, 3] -> (Sources, keepalive)."""
+    pts, p = _f64(points)
+    if pts.ndim != 3 or pts.shape[2] != 3:
+        raise ValueError("points must be [Q, L, 3]")
+    return Sources(pts.shape[0], pts.shape[1], p, float(A0)), pts
+
+
+class Handle:
+    """Owns an fr3d_handle (fr3d_kernel_transform ... fr3d_handle_destroy)."""
+
+    def __init__(self, n, x0, h, zr, zy, nu=None, stream=None):
+        lib = load()
+        self._zr, zrp = _f64(zr)
+        self._zy, zyp = _f64(zy)
+        if nu is None:
+            self._nu, nup = None, None
+        else:
+            self._nu, nup = _f64(nu)
+        g = Geometry(int(n), int(n), float(x0), float(x0), float(h), float(h), 1, self._zr.size, zrp, nup,
+                     self._zy.size, zyp, K_DZ_INV_R)
+        hp = ct.c_void_p()
+        _check(lib.fr3d_kernel_transform(ct.byref(g), ct.byref(hp), _stream(stream)), "fr3d_kernel_transform")
+        self.ptr = hp
+        n_, m_, mp_, s2 = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_double()
+        _check(lib.fr3d_handle_query(hp, ct.byref(n_), ct.byref(m_), ct.byref(mp_), ct.byref(s2)), "query")
+        self.n, self.M, self.Mp, self.s2 = n_.value, m_.value, mp_.value, s2.value
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().fr3d_handle_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_transform(n, x0, h, zr, zy, nu=None, stream=None) -> Handle:
+    return Handle(n, x0, h, zr, zy, nu, stream)
+
+
+def fwd_apply(handle: Handle, zeta, Q: int, U, precision: int = PREC_FP32, stream=None):
+    _check(load().fr3d_fwd_apply(handle.ptr, _ptr(zeta), int(Q), _ptr(U), int(precision), _stream(stream)),
+           "fr3d_fwd_apply")
+
+
+def zeta_from_xi(handle: Handle, xi, points, zeta, A0: float = 1.0, precision: int = PREC_FP32, stream=None):
+    src, keep = make_sources(points, A0)
+    _check(load().fr3d_zeta_from_xi(handle.ptr, _ptr(xi), ct.byref(src), _ptr(zeta), int(precision),
+                                    _stream(stream)), "fr3d_zeta_from_xi")
+
+
+def choose_alpha(handle: Handle, U, Q: int, alphas, delta: float, tau: float, alpha_idx, residuals=None, info=None,
+                 precision: int = PREC_FP32, stream=None):
+    a, ap = _f64(alphas)
+    _check(load().fr3d_choose_alpha(handle.ptr, _ptr(U), int(Q), ap, a.size, float(delta), float(tau),
+                                    int(precision), _ptr(alpha_idx), _ptr(residuals), _ptr(info), _stream(stream)),
+           "fr3d_choose_alpha")
+
+
+class Opts:
+    """Builds fr3d_invert_opts and keeps its host arrays alive."""
+
+    def __init__(self, *, alpha=None, alphas=None, delta=0.0, tau=1.1, output=OUT_XI, precision=PREC_FP32,
+                 points=None, A0=1.0, alpha_idx=None, residuals=None, info=None):
+        o = InvertOpts()
+        if alpha is not None:
+            o.alpha_mode, o.alpha = ALPHA_FIXED, float(alpha)
+            self._a = None
+        else:
+            self._a, ap = _f64(alphas)
+            o.alpha_mode, o.alphas, o.n_alpha = ALPHA_DISCREPANCY, ap, self._a.size
+        o.delta, o.tau, o.output, o.precision = float(delta), float(tau), int(output), int(precision)
+        if points is not None:
+            self._src, self._pts = make_sources(points, A0)
+            o.sources = ct.pointer(self._src)
+        o.alpha_idx = _ptr(alpha_idx)
+        o.residuals = _ptr(residuals)
+        o.info = _ptr(info)
+        self.c = o
+
+
+def invert(handle: Handle, U, Q: int, out, opts: Opts, stream=None):
+    _check(load().fr3d_invert(handle.ptr, _ptr(U), int(Q), ct.byref(opts.c), _ptr(out), _stream(stream)),
+           "fr3d_invert")
+
+
+def invert_host(handle: Handle, U_host, Q: int, out_host, opts: Opts, stream=None):
+    _check(load().fr3d_invert_host(handle.ptr, _ptr(U_host), int(Q), ct.byref(opts.c), _ptr(out_host),
+                                   _stream(stream)), "fr3d_invert_host")
+
+
+def last_launch_count(handle: Handle) -> int:
+    return int(load().fr3d_last_launch_count(handle.ptr))
+
+
+STAGE_NAMES = ("row_r2c", "col_fwd", "alpha", "col_solve", "row_c2r", "table", "contract", "col_inv", "other")
+
+
+def profile_enable(handle: Handle, enable: bool = True):
+    _check(load().fr3d_profile_enable(handle.ptr, int(bool(enable))), "fr3d_profile_enable")
+
+
+def profile_read(handle: Handle, cap: int = 96):
+    """[(stage name, ms)] for the launches of the latest call (waits for them)."""
+    kinds = (ct.c_int * cap)()
+    ms = (ct.c_float * cap)()
+    n = _check(load().fr3d_profile_read(handle.ptr, kinds, ms, cap), "fr3d_profile_read")
+    return [(STAGE_NAMES[kinds[i]], float(ms[i])) for i in range(n)]

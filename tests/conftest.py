@@ -1,6 +1,9 @@
 import os
 import sys
 
+# the oracle's many tiny LAPACK calls run faster without BLAS thread fan-out
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
