@@ -55,6 +55,7 @@ _lib = None
 
 # the names the C ABI exports (include/fr3d.h)
 EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", "fr3d_fwd_apply",
+           "fr3d_fwd_apply_noalloc",
            "fr3d_zeta_from_xi", "fr3d_choose_alpha", "fr3d_invert", "fr3d_invert_host",
            "fr3d_last_launch_count", "fr3d_profile_enable", "fr3d_profile_read", "fr3d_status_string")
 
@@ -74,6 +75,7 @@ def load(path: str | None = None):
     lib.fr3d_handle_destroy.restype = None
     lib.fr3d_handle_query.argtypes = [vp, ct.POINTER(i), ct.POINTER(i), ct.POINTER(i), ct.POINTER(d)]
     lib.fr3d_fwd_apply.argtypes = [vp, vp, i, vp, i, vp]
+    lib.fr3d_fwd_apply_noalloc.argtypes = [vp, vp, i, vp, vp]
     lib.fr3d_zeta_from_xi.argtypes = [vp, vp, ct.POINTER(Sources), vp, i, vp]
     lib.fr3d_choose_alpha.argtypes = [vp, vp, i, _dp, i, d, d, i, vp, vp, vp, vp]
     lib.fr3d_invert.argtypes = [vp, vp, i, ct.POINTER(InvertOpts), vp, vp]
@@ -173,6 +175,12 @@ def kernel_transform(n, x0, h, zr, zy, nu=None, stream=None) -> Handle:
 def fwd_apply(handle: Handle, zeta, Q: int, U, precision: int = PREC_FP32, stream=None):
     _check(load().fr3d_fwd_apply(handle.ptr, _ptr(zeta), int(Q), _ptr(U), int(precision), _stream(stream)),
            "fr3d_fwd_apply")
+
+
+def fwd_apply_noalloc(handle: Handle, zeta, Q: int, U, stream=None):
+    """fr3d_fwd_apply_noalloc: FP32 forward operator using the library's static scratch (no allocation)."""
+    _check(load().fr3d_fwd_apply_noalloc(handle.ptr, _ptr(zeta), int(Q), _ptr(U), _stream(stream)),
+           "fr3d_fwd_apply_noalloc")
 
 
 def zeta_from_xi(handle: Handle, xi, points, zeta, A0: float = 1.0, precision: int = PREC_FP32, stream=None):
