@@ -133,6 +133,8 @@ def recorded_traffic(stage: str):
 def stage_bytes(stage: str, n: int, mp: int, q: int, nj: int) -> float:
     """Algorithmic DRAM bytes of one launch: every input read once, every output written once."""
     ps = (n // 2 + 1) * n                     # half-spectrum bins per plane
+    if stage == "inv_fused":                  # data spectra + kernel table in, 1/sum V0^2 in, xi out
+        return q * ps * 8.0 + mp * ps * 4.0 + mp * n * n * 8.0
     if stage == "row_c2r":                    # spectra of nj depths x q sources in, xi of nj depths out
         return nj * q * ps * 8.0 + nj * n * n * 4.0
     if stage == "col_solve":                  # data spectra + weights in, per-depth spectra out

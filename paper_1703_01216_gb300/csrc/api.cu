@@ -54,6 +54,22 @@ SrcHost src_host(const Handle* H, int precision, const fr3d_sources* s) {
 
 bool valid_precision(int p) { return p == FR3D_PREC_FP32 || p == FR3D_PREC_FP64; }
 
+// combination weights W_q = V0_q / sum_q' V0_q'^2 for the cached sources (rebuilt when they change)
+int ensure_wtab(Handle* H, const fr3d_sources* s, cudaStream_t st) {
+  if (H->wtab && H->wtab_key == H->src_key) return FR3D_OK;
+  const size_t need = sizeof(float) * (size_t)s->q * H->Mp * H->n * H->n;
+  if (H->wtab_cap < need) {
+    if (H->wtab) cudaFree(H->wtab);
+    H->wtab = nullptr;
+    H->wtab_cap = 0;
+    FR3D_CUDA_TRY(cudaMalloc(&H->wtab, need));
+    H->wtab_cap = need;
+  }
+  FR3D_TRY(build_wtab(H, H->wtab, s->q, H->pts64, s->n_points, -s->A0 / kFourPi, st));
+  H->wtab_key = H->src_key;
+  return FR3D_OK;
+}
+
 // ------------------------------------------------------------------ forward operator
 template <typename T>
 int fwd_impl(Handle* H, const T* zeta, int Q, T* U, cudaStream_t st) {
@@ -134,7 +150,21 @@ InvertPlan plan_invert(const Handle* H, int Q, bool host_io, int output) {
   p.uh_off = 0;
   size_t off = align_up(ps_b * Q * H->M);
   const size_t per_j = ps_b * Q;
-  int chunk = (int)std::max<size_t>(1, std::min<size_t>(H->Mp, kChunkBytes / per_j));
+  const bool fused = sizeof(T) == 4 && fused_supported(n);
+  int chunk = fused ? 0 : (int)std::max<size_t>(1, std::min<size_t>(H->Mp, kChunkBytes / per_j));
+  if (fused) {
+    p.chunk = H->Mp;
+    p.t_off = off;
+    p.uin_off = p.out_off = 0;
+    if (host_io) {
+      p.uin_off = off;
+      off += align_up(sizeof(T) * (size_t)Q * H->M * n * n);
+      p.out_off = off;
+      off += align_up(sizeof(T) * (size_t)(output == FR3D_OUT_XI ? 1 : Q) * H->Mp * n * n);
+    }
+    p.total = off;
+    return p;
+  }
   const int nch = (H->Mp + chunk - 1) / chunk;
   chunk = (H->Mp + nch - 1) / nch;
   p.chunk = chunk;
@@ -205,6 +235,20 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
     else D = H->Dfix64;
     if (o->alpha_idx) FR3D_CUDA_TRY(cudaMemsetAsync(o->alpha_idx, 0, sizeof(int), st));
     if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (fused_supported(H->n)) {
+      // steps 2 (solve) + 3 (inverse DFT) + 4 (combination) fused, one launch for all depths
+      if (o->output == FR3D_OUT_XI) {
+        FR3D_TRY(ensure_wtab(H, o->sources, st));
+        prof_mark(H, kStTable, st);
+      }
+      const float* Dd = o->alpha_mode == FR3D_ALPHA_DISCREPANCY ? H->Dd32 : H->Ddfix32;
+      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, H->wtab, out, Q, 0, H->Mp, o->output, st));
+      prof_mark(H, kStFused, st);
+      H->last_launches = launches + 1;
+      return FR3D_OK;
+    }
   }
   const T* A;
   if constexpr (sizeof(T) == 4) A = H->A32;

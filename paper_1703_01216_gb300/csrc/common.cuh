@@ -62,15 +62,20 @@ struct Handle {
   std::vector<double> alpha_key;
   double* Ft = nullptr;       // [C][n_alpha]  ((alpha s^2) / (nrm + alpha s^2))^2
   float* D32 = nullptr;       // [n_alpha][C]  1 / (n^2 (nrm + alpha s^2))
+  float* Dd32 = nullptr;      // [n_alpha][n/2+1][n]  the same per half-spectrum bin
   double* D64 = nullptr;      // [n_alpha][C]
   int alpha_cap = 0;
   // fixed-alpha table
   double fixed_key = -1.0;
   float* Dfix32 = nullptr;    // [C]
+  float* Ddfix32 = nullptr;   // [n/2+1][n]
   double* Dfix64 = nullptr;   // [C]
   // sources, keyed by content
   std::vector<double> src_key;
   float4* pts32 = nullptr;    // [Q*L] (x, y, z, 0)
+  float* wtab = nullptr;      // [Q][M'][n][n] V0_q / sum_q' V0_q'^2 for src_key (built on demand)
+  std::vector<double> wtab_key;
+  size_t wtab_cap = 0;
   double* pts64 = nullptr;    // [Q*L*3]
   int src_cap = 0;
   // small device words
@@ -104,7 +109,7 @@ int ensure_ws(Handle* H, size_t bytes);
 
 // stage kinds reported by fr3d_profile_read
 enum StageKind { kStRowR2C = 0, kStColFwd = 1, kStAlpha = 2, kStColSolve = 3, kStRowC2R = 4, kStTable = 5,
-                 kStContract = 6, kStColInv = 7, kStOther = 8 };
+                 kStContract = 6, kStColInv = 7, kStOther = 8, kStFused = 9 };
 inline void prof_begin(Handle* H, cudaStream_t st) {
   H->n_ev = 0;
   if (!H->prof_on) return;

@@ -41,24 +41,26 @@ template <typename T, int N> struct ColTile {
 
 // ---------------------------------------------------------------- row pass, real -> half spectrum
 // in: planes of TY x n reals (plane stride in_ps); out: [plane][kx][y] complex.
-template <typename T, int N>
+template <typename T, int N, int TY>
 __global__ void __launch_bounds__(kThreads) k_row_r2c(const T* __restrict__ in, long in_ps,
                                                      typename cpx<T>::t* __restrict__ out,
                                                      const typename cpx<T>::t* __restrict__ tw_half,
                                                      const typename cpx<T>::t* __restrict__ tw_full) {
   using C = typename cpx<T>::t;
-  constexpr int L = N / 2, TY = RowTile<T, N>::v, SS = Smem<C, L>::ss, STS = TY + 1;
+  constexpr int L = N / 2, SS = Smem<C, L>::ss, STS = TY + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tws = reinterpret_cast<C*>(smem_raw);       // exp(-2 pi i t / n), t < n
+  C* buf = tws + N;
   C* stg = buf + TY * SS;
   const int tid = threadIdx.x, plane = blockIdx.y, y0 = blockIdx.x * TY;
   const C* src = reinterpret_cast<const C*>(in + plane * in_ps + (long)y0 * N);
+  for (int e = tid; e < N; e += kThreads) tws[e] = __ldg(tw_full + e);
   for (int e = tid; e < TY * L; e += kThreads) {
     const int r = e / L, m = e - r * L;
     buf[r * SS + pidx<C>(m)] = src[(long)r * L + m];
   }
   __syncthreads();
-  fft_smem<L, false, TY, kThreads>(buf, SS, tw_half, tid);
+  fft_smem<L, false, TY, kThreads, 2>(buf, SS, tws, tid);
   const T half = (T)0.5;
   for (int e = tid; e < TY * (L + 1); e += kThreads) {
     const int k = e / TY, r = e - k * TY;
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const T* __restrict__ in, 
     const C zc = cconj(buf[r * SS + pidx<C>(k == 0 ? 0 : L - k)]);
     const C E = cscale(cadd(zk, zc), half);
     const C O = cmul_mi<false>(cscale(csub(zk, zc), half));  // (Z[k] - conj Z[L-k]) / (2i)
-    stg[k * STS + r] = cadd(E, cmul(__ldg(tw_full + k), O));  // X[k] = E[k] + w^k O[k]
+    stg[k * STS + r] = cadd(E, cmul(tws[k], O));  // X[k] = E[k] + w^k O[k]
   }
   __syncthreads();
   C* dst = out + (long)plane * (L + 1) * N + y0;
@@ -79,13 +81,15 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const T* __restrict__ in, 
 // ---------------------------------------------------------------- column pass along ky
 // Op supplies: src(plane) -> const C*, dst(plane) -> C*, and load(plane, kx, ky, value) -> C
 // (a per-bin multiplier for the solve).  One CTA transforms TC consecutive columns of one plane.
-template <typename T, int N, bool INV, class Op>
+template <typename T, int N, bool INV, class Op, int TC>
 __global__ void __launch_bounds__(kThreads) k_col_fft(Op op, const typename cpx<T>::t* __restrict__ tw) {
   using C = typename cpx<T>::t;
-  constexpr int TC = ColTile<T, N>::v, SS = Smem<C, N>::ss, H1 = N / 2 + 1;
+  constexpr int SS = Smem<C, N>::ss, H1 = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tws = reinterpret_cast<C*>(smem_raw);       // exp(-2 pi i t / n), t < n
+  C* buf = tws + N;
   const int tid = threadIdx.x, plane = blockIdx.y, c0 = blockIdx.x * TC;
+  for (int e = tid; e < N; e += kThreads) tws[e] = __ldg(tw + e);
   op.begin(plane);
   const C* src = op.src(plane);
   for (int e = tid; e < TC * N; e += kThreads) {
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_col_fft(Op op, const typename cpx<
     buf[col * SS + pidx<C>(ky)] = v;
   }
   __syncthreads();
-  fft_smem<N, INV, TC, kThreads>(buf, SS, tw, tid);
+  fft_smem<N, INV, TC, kThreads>(buf, SS, tws, tid);
   C* dst = op.dst(plane);
   for (int e = tid; e < TC * N; e += kThreads) {
     const int col = e / N, ky = e - col * N, kx = c0 + col;
@@ -192,9 +196,11 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const typename cpx<T>::t* 
   constexpr int SS = Smem<C, L>::ss;
   constexpr int EPT = (TY * L + kThreads - 1) / kThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tws = reinterpret_cast<C*>(smem_raw);       // exp(-2 pi i t / n), t < n
+  C* buf = tws + N;
   const int tid = threadIdx.x, y0 = blockIdx.x * TY;
   const long ps = (long)(L + 1) * N;
+  for (int e = tid; e < N; e += kThreads) tws[e] = __ldg(tw_full + e);
   T num[EPT][2], den[EPT][2];
   if (MODE == 1) {
 #pragma unroll
@@ -216,17 +222,17 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const typename cpx<T>::t* 
       const C a = row[pidx<C>(k)], b = row[pidx<C>(L - k)];
       {
         const C sum = cadd(a, cconj(b)), dif = csub(a, cconj(b));
-        const C t = cmul_mi<true>(cmul(cconj(__ldg(tw_full + k)), dif));
+        const C t = cmul_mi<true>(cmul(cconj(tws[k]), dif));
         row[pidx<C>(k)] = cadd(sum, t);
       }
       if (k != 0 && 2 * k != L) {
         const C sum = cadd(b, cconj(a)), dif = csub(b, cconj(a));
-        const C t = cmul_mi<true>(cmul(cconj(__ldg(tw_full + (L - k))), dif));
+        const C t = cmul_mi<true>(cmul(cconj(tws[L - k]), dif));
         row[pidx<C>(L - k)] = cadd(sum, t);
       }
     }
     __syncthreads();
-    fft_smem<L, true, TY, kThreads>(buf, SS, tw_half, tid);
+    fft_smem<L, true, TY, kThreads, 2>(buf, SS, tws, tid);
     if (MODE == 0) {
       const int jc = ip / Q, qq = ip - jc * Q;
       T* o = out + ((long)qq * out_stride + j0 + jc) * N * N + (long)y0 * N;
@@ -270,22 +276,27 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const typename cpx<T>::t* 
   }
 }
 
-template <typename T, int N> constexpr size_t row_r2c_smem() {
+template <typename T, int N, int TY> constexpr size_t row_r2c_smem() {
   using C = typename cpx<T>::t;
-  constexpr int L = N / 2, TY = RowTile<T, N>::v;
-  return sizeof(C) * ((size_t)TY * Smem<C, L>::ss + (size_t)(L + 1) * (TY + 1));
+  constexpr int L = N / 2;
+  return sizeof(C) * ((size_t)N + (size_t)TY * Smem<C, L>::ss + (size_t)(L + 1) * (TY + 1));
 }
-template <typename T, int N> constexpr size_t col_smem() {
+template <typename T, int N, int TC> constexpr size_t col_smem() {
   using C = typename cpx<T>::t;
-  return sizeof(C) * (size_t)ColTile<T, N>::v * Smem<C, N>::ss;
+  return sizeof(C) * ((size_t)N + (size_t)TC * Smem<C, N>::ss);
 }
+// small tiles for transforms of few planes (more CTAs in flight)
+template <int N> struct SmallTile {
+  static constexpr int row = divisor_at_most(N, 8);
+  static constexpr int col = 4;
+};
 template <typename T, int N, int MODE> constexpr int row_c2r_tile() {
   constexpr int TY0 = RowTile<T, N>::v;
   return (MODE == 1 && TY0 % 2 == 0) ? TY0 / 2 : TY0;
 }
 template <typename T, int N, int MODE> constexpr size_t row_c2r_smem() {
   using C = typename cpx<T>::t;
-  return sizeof(C) * (size_t)row_c2r_tile<T, N, MODE>() * Smem<C, N / 2>::ss;
+  return sizeof(C) * ((size_t)N + (size_t)row_c2r_tile<T, N, MODE>() * Smem<C, N / 2>::ss);
 }
 
 }  // namespace fr3d

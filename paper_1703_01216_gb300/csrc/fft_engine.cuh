@@ -161,8 +161,9 @@ template <typename C> __device__ __forceinline__ int pidx(int e) { return e + (e
 
 // One Stockham pass.  Butterfly j of a sequence reads elements j + r L/R (r < R), multiplies
 // element r by w^(r (j mod NS) L/(NS R)), with w = exp(-+2 pi i / L), and writes the R-point
-// DFT to positions (j / NS) NS R + (j mod NS) + r NS.
-template <int L, int R, int NS, bool INV, int NSEQ, int NTHR, typename C>
+// DFT to positions (j / NS) NS R + (j mod NS) + r NS.  The twiddle table holds exp(-2 pi i t / (TS L))
+// (every TS-th entry is used), usually staged in shared memory by the calling kernel.
+template <int L, int R, int NS, bool INV, int NSEQ, int NTHR, int TS, typename C>
 __device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __restrict__ tw, int tid) {
   constexpr int BPS = L / R;
   constexpr int NB = NSEQ * BPS;
@@ -180,7 +181,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __re
       for (int r = 0; r < R; ++r) {
         C x = base[pidx<C>(j + r * BPS)];
         if (NS > 1 && r > 0) {
-          C w = __ldg(tw + r * jj * (L / (NS * R)));
+          C w = tw[r * jj * (L / (NS * R)) * TS];
           if (INV) w = cconj(w);
           x = cmul(x, w);
         }
@@ -205,12 +206,12 @@ __device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __re
   __syncthreads();
 }
 
-template <int L, bool INV, int NSEQ, int NTHR, int P = 0, int NS = 1, typename C>
+template <int L, bool INV, int NSEQ, int NTHR, int TS = 1, int P = 0, int NS = 1, typename C>
 __device__ __forceinline__ void fft_smem(C* buf, int sstride, const C* __restrict__ tw, int tid) {
   if constexpr (P < Plan<L>::np) {
     constexpr int R = Plan<L>::radix(P);
-    stockham_pass<L, R, NS, INV, NSEQ, NTHR>(buf, sstride, tw, tid);
-    fft_smem<L, INV, NSEQ, NTHR, P + 1, NS * R>(buf, sstride, tw, tid);
+    stockham_pass<L, R, NS, INV, NSEQ, NTHR, TS>(buf, sstride, tw, tid);
+    fft_smem<L, INV, NSEQ, NTHR, TS, P + 1, NS * R>(buf, sstride, tw, tid);
   }
 }
 

@@ -1,0 +1,256 @@
+// Fused Algorithm 1 steps 2-4 for M = 1 (FP32): per depth z'_j, the Tikhonov weights, the inverse
+// 2D DFT of every source parameter's spectrum and the combination xi = sum_q W_q zeta_q, in one
+// kernel with no spectrum intermediate in global memory.
+//
+// One thread-block cluster of CL CTAs handles one depth j.
+//   set-up        CTA r stages the solve weights w_j(kx, ky) = A_j / (n^2 (||A||^2 + alpha s^2))
+//                 (Eq. (6) with M = 1) of the columns it owns in shared memory; they do not depend
+//                 on the source parameter q.
+//   For each q:
+//   column phase  the n/2 + 1 columns kx of the half spectrum are handled as n/2 complex columns:
+//                 column 0 carries kx = 0 in its real part and kx = n/2 in its imaginary part (both
+//                 are Hermitian in ky, so their inverse column DFTs are real and one complex DFT
+//                 yields both).  CTA r owns columns [r n/(2 CL), (r + 1) n/(2 CL)), loads
+//                 U~_q w_j and runs the inverse column DFTs along ky in shared memory;
+//   row phase     after a cluster barrier, CTA r owns rows [r n/CL, (r + 1) n/CL); it reads each
+//                 row's spectrum from the owners' shared memory (distributed shared memory), forms
+//                 the length-n/2 complex sequence of the real inverse, transforms it and
+//                 accumulates W_q zeta_q in shared memory, W_q = V0_q / sum_q' V0_q'^2 read from a
+//                 per-voxel table that depends only on the geometry and the sources;
+//   a second cluster barrier lets the peers finish reading before the next q overwrites.
+// After the last q the accumulated xi of the owned rows is stored.  ZETA mode stores zeta_q.
+// Global loads are issued in unrolled batches so that several are in flight per thread.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "fft2d.cuh"
+
+namespace fr3d {
+
+namespace cg = cooperative_groups;
+
+template <int N> struct FusedCfg;
+// CL: CTAs per cluster, NT: threads, RB: rows per row batch, MINB: resident CTAs per SM that the
+// register budget is sized for
+template <> struct FusedCfg<16> { static constexpr int CL = 1, NT = 128, RB = 16, MINB = 4; };
+template <> struct FusedCfg<24> { static constexpr int CL = 1, NT = 96, RB = 24, MINB = 4; };
+template <> struct FusedCfg<32> { static constexpr int CL = 1, NT = 128, RB = 32, MINB = 4; };
+template <> struct FusedCfg<48> { static constexpr int CL = 1, NT = 128, RB = 48, MINB = 3; };
+template <> struct FusedCfg<64> { static constexpr int CL = 2, NT = 256, RB = 32, MINB = 2; };
+template <> struct FusedCfg<96> { static constexpr int CL = 2, NT = 256, RB = 48, MINB = 2; };
+template <> struct FusedCfg<128> { static constexpr int CL = 4, NT = 256, RB = 32, MINB = 2; };
+template <> struct FusedCfg<192> { static constexpr int CL = 4, NT = 256, RB = 16, MINB = 2; };
+template <> struct FusedCfg<256> { static constexpr int CL = 8, NT = 256, RB = 16, MINB = 2; };
+template <> struct FusedCfg<384> { static constexpr int CL = 8, NT = 512, RB = 16, MINB = 1; };
+
+template <int N> struct FusedGeom {
+  using Cf = FusedCfg<N>;
+  static constexpr int CL = Cf::CL, NT = Cf::NT, RB = Cf::RB;
+  static constexpr int L = N / 2;
+  static constexpr int CPC = L / CL;                   // packed columns per CTA
+  static constexpr int NRW = N / CL;                   // rows per CTA
+  static constexpr int NB = NRW / RB;                  // row batches
+  static constexpr int SSC = Smem<float2, N>::ss;      // column stride in shared memory
+  static constexpr int SSR = Smem<float2, L>::ss;      // row stride
+  static constexpr int EPT = RB * L / NT;              // complex outputs per thread per batch
+  static constexpr int NSPL = RB * (L / 2 + 1);        // Hermitian-split pairs per batch
+  // shared memory: columns, rows, twiddles, weights (+ the kx = n/2 weights), xi accumulator
+  static constexpr size_t smem_zeta =
+      sizeof(float2) * ((size_t)CPC * SSC + (size_t)RB * SSR + N) + sizeof(float) * (size_t)(CPC + 1) * N;
+  static constexpr size_t smem_xi = smem_zeta + sizeof(float) * (size_t)NRW * N;
+  static_assert(L % CL == 0, "column split");
+  static_assert(NRW % RB == 0, "row batches");
+  static_assert((RB * L) % NT == 0, "outputs per thread");
+  static_assert((CPC * N) % NT == 0, "column loads per thread");
+};
+
+struct FusedArgs {
+  const float2* Uh;    // [Q][n/2+1][n] data spectra
+  const float* A;      // [M' = j][n/2+1][n] dense kernel table
+  const float* Dd;     // [n_alpha][n/2+1][n] dense solve weights
+  const int* aidx;     // chosen row of Dd
+  const float* W;      // [Q][M'][n][n] combination weights V0_q / sum_q' V0_q'^2 (XI mode)
+  float* out;          // XI: [M'][n][n]; ZETA: [Q][M'][n][n]
+  const float2* tw_n;  // length-n twiddles
+  int Q, j0, Mp;
+};
+
+template <int N, int MODE>
+__global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
+    k_inv_fused(FusedArgs a) {
+  using G = FusedGeom<N>;
+  constexpr int CL = G::CL, NT = G::NT, RB = G::RB, L = G::L;
+  constexpr int CPC = G::CPC, NRW = G::NRW, NB = G::NB, SSC = G::SSC, SSR = G::SSR, EPT = G::EPT;
+  constexpr int CLD = CPC * N / NT;           // column elements per thread
+  constexpr int CB = divisor_at_most(CLD, 8);  // loads in flight per batch
+  static_assert(CLD % CB == 0, "load batches");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* colbuf = reinterpret_cast<float2*>(smem_raw);
+  float2* rowbuf = colbuf + CPC * SSC;
+  float2* tws = rowbuf + RB * SSR;           // exp(-2 pi i t / n), t < n
+  float* wsm = reinterpret_cast<float*>(tws + N);   // [CPC][n] weights of the owned columns, then w(n/2, .)
+  float2* accs = reinterpret_cast<float2*>(wsm + (CPC + 1) * N);  // XI: [NRW][n/2] pairs of the owned rows
+  const int tid = threadIdx.x;
+  int r = 0;
+  if constexpr (CL > 1) r = (int)cg::this_cluster().block_rank();
+  const int jl = blockIdx.x / CL;
+  const int j = a.j0 + jl;
+  const int c0 = r * CPC;
+  const int y0 = r * NRW;
+  const long ps = (long)(L + 1) * N;
+
+  // ---------------- set-up: twiddles and the q-invariant solve weights of the owned columns
+  {
+    const float* Aj = a.A + (long)j * ps;
+    const float* drow = a.Dd + (long)(*a.aidx) * ps;
+    for (int e = tid; e < N; e += NT) tws[e] = __ldg(a.tw_n + e);
+#pragma unroll
+    for (int b0 = 0; b0 < CLD; b0 += CB) {
+      float wa[CB], wd[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        const long o = (long)c0 * N + tid + (b0 + i) * NT;   // columns c0.. are contiguous
+        wa[i] = __ldg(Aj + o);
+        wd[i] = __ldg(drow + o);
+      }
+#pragma unroll
+      for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = wa[i] * wd[i];
+    }
+    if (r == 0)
+      for (int e = tid; e < N; e += NT) wsm[CPC * N + e] = __ldg(Aj + (long)L * N + e) * __ldg(drow + (long)L * N + e);
+  }
+  __syncthreads();
+
+  // X(kx, y) after the column phase, from the shared memory of the column's owner (kx in [0, n/2])
+  auto xat = [&](int kx, int y) -> float2 {
+    const int c = kx == L ? 0 : kx;
+    const int o = c / CPC, idx = (c - o * CPC) * SSC + pidx<float2>(y);
+    float2 v;
+    if constexpr (CL == 1) {
+      v = colbuf[idx];
+    } else {
+      if (o == r) v = colbuf[idx];
+      else v = *cg::this_cluster().map_shared_rank(colbuf + idx, (unsigned)o);
+    }
+    if (kx == 0) return make_float2(v.x, 0.f);   // packed column 0: real part is kx = 0
+    if (kx == L) return make_float2(v.y, 0.f);   // imaginary part is kx = n/2
+    return v;
+  };
+
+  for (int q = 0; q < a.Q; ++q) {
+    const float2* Zq = a.Uh + (long)q * ps;
+    // ---------------- column phase
+#pragma unroll
+    for (int b0 = 0; b0 < CLD; b0 += CB) {
+      float2 u[CB], un[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        const int e = tid + (b0 + i) * NT;
+        u[i] = __ldg(Zq + (long)c0 * N + e);
+        if (r == 0 && e < N) un[i] = __ldg(Zq + (long)L * N + e);
+      }
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        const int e = tid + (b0 + i) * NT;
+        const int col = e / N, ky = e % N;
+        const float w = wsm[e];
+        float2 v = make_float2(u[i].x * w, u[i].y * w);
+        if (r == 0 && e < N) {   // packed column 0: add i * w(n/2, ky) U~(n/2, ky)
+          const float wl = wsm[CPC * N + e];
+          v.x -= un[i].y * wl;
+          v.y += un[i].x * wl;
+        }
+        colbuf[col * SSC + pidx<float2>(ky)] = v;
+      }
+    }
+    __syncthreads();
+    fft_smem<N, true, CPC, NT>(colbuf, SSC, tws, tid);
+    if constexpr (CL > 1) cg::this_cluster().sync();
+    // ---------------- row phase
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      // Hermitian split Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), pairs (k, L - k)
+      constexpr int SIT = (G::NSPL + NT - 1) / NT;
+      float2 xa[SIT], xb[SIT];
+#pragma unroll
+      for (int i = 0; i < SIT; ++i) {
+        const int e = tid + i * NT;
+        if (G::NSPL % NT == 0 || e < G::NSPL) {
+          const int row = e % RB, k = e / RB, y = y0 + b * RB + row;
+          xa[i] = xat(k, y);
+          xb[i] = xat(L - k, y);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < SIT; ++i) {
+        const int e = tid + i * NT;
+        if (G::NSPL % NT == 0 || e < G::NSPL) {
+          const int row = e % RB, k = e / RB;
+          float2* rw = rowbuf + row * SSR;
+          {
+            const float2 sum = cadd(xa[i], cconj(xb[i])), dif = csub(xa[i], cconj(xb[i]));
+            rw[pidx<float2>(k)] = cadd(sum, cmul_mi<true>(cmul(cconj(tws[k]), dif)));
+          }
+          if (k != 0 && 2 * k != L) {
+            const float2 sum = cadd(xb[i], cconj(xa[i])), dif = csub(xb[i], cconj(xa[i]));
+            rw[pidx<float2>(L - k)] = cadd(sum, cmul_mi<true>(cmul(cconj(tws[L - k]), dif)));
+          }
+        }
+      }
+      __syncthreads();
+      fft_smem<L, true, RB, NT, 2>(rowbuf, SSR, tws, tid);
+      if constexpr (MODE == 1) {
+        const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + j) * N + y0 + b * RB) * N);
+        float2 wv[EPT];
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) wv[i] = __ldg(wq + tid + i * NT);   // [row][mm] pairs of the batch
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+          const int e = tid + i * NT;
+          const int row = e / L, mm = e % L;
+          const float2 v = rowbuf[row * SSR + pidx<float2>(mm)];
+          float2* ac = accs + b * RB * L + e;
+          const float2 prev = q == 0 ? make_float2(0.f, 0.f) : *ac;
+          *ac = make_float2(fmaf(wv[i].x, v.x, prev.x), fmaf(wv[i].y, v.y, prev.y));
+        }
+      } else {
+        float2* o = reinterpret_cast<float2*>(a.out + (((long)q * a.Mp + j) * N + y0 + b * RB) * N);
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+          const int e = tid + i * NT;
+          const int row = e / L, mm = e % L;
+          o[e] = rowbuf[row * SSR + pidx<float2>(mm)];
+        }
+      }
+      __syncthreads();
+    }
+    if constexpr (CL > 1) cg::this_cluster().sync();
+  }
+  if constexpr (MODE == 1) {
+    // xi of the owned rows; the last barrier of the q loop ordered every accumulator write first
+    float2* ov = reinterpret_cast<float2*>(a.out + ((long)j * N + y0) * N);
+#pragma unroll 4
+    for (int e = tid; e < NRW * L; e += NT) ov[e] = accs[e];
+  }
+}
+
+// W_q = V0_q / sum_q' V0_q'^2 on the R grid (Algorithm 1 step 4 for several source parameters),
+// in FP64, stored as FP32; depends only on the geometry and the sources
+__global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, double x0, double y0, double h,
+                       const double* __restrict__ zr) {
+  const long plane = (long)n * n, total = (long)Mp * plane;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / plane);
+    const long pix = idx % plane;
+    const double x = x0 + ((double)(pix % n) + 0.5) * h, y = y0 + ((double)(pix / n) + 0.5) * h;
+    double s = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      const double v = v0_at(src, q, x, y, zr[j]);
+      s += v * v;
+    }
+    for (int q = 0; q < Q; ++q) W[(long)q * total + idx] = (float)(v0_at(src, q, x, y, zr[j]) / s);
+  }
+}
+
+}  // namespace fr3d

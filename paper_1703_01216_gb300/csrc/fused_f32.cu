@@ -1,0 +1,65 @@
+// Launchers of the fused inverse (fused.cuh) and of the 1 / sum_q V0_q^2 table.
+#include "fused.cuh"
+#include "ops.cuh"
+
+namespace fr3d {
+
+namespace {
+
+template <int N, int MODE>
+int launch_fused(const Handle* H, const FusedArgs& a, int nj, cudaStream_t st) {
+  using G = FusedGeom<N>;
+  auto kern = k_inv_fused<N, MODE>;
+  constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;
+  if (sm > 48 * 1024)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      return FR3D_ERR_CUDA;
+  kern<<<nj * G::CL, G::NT, sm, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+}  // namespace
+
+bool fused_supported(int n) {
+  switch (n) {
+    case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192: case 256: case 384:
+      return true;
+  }
+  return false;
+}
+
+int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
+                  int Q, int j0, int nj, int output, cudaStream_t st) {
+  FusedArgs a;
+  a.Uh = Uh;
+  a.A = H->A32;
+  a.Dd = Dd;
+  a.aidx = aidx;
+  a.W = W;
+  a.out = out;
+  a.tw_n = H->tw32 + twiddle_offset(H, H->n);
+  a.Q = Q;
+  a.j0 = j0;
+  a.Mp = H->Mp;
+  const bool xi = output == FR3D_OUT_XI;
+  switch (H->n) {
+#define X(N) \
+  case N: return xi ? launch_fused<N, 1>(H, a, nj, st) : launch_fused<N, 0>(H, a, nj, st);
+    X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st) {
+  Src64 s;
+  s.pts = pts64;
+  s.L = L;
+  s.coef = coef;
+  const long total = (long)H->Mp * H->n * H->n;
+  const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+  k_wtab<<<blocks, 256, 0, st>>>(W, Q, H->Mp, H->n, s, H->x0, H->y0, H->h, H->zr64);
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
+}  // namespace fr3d

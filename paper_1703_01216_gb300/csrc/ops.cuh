@@ -2,6 +2,8 @@
 // ops_f32.cu / ops_f64.cu).
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fr3d {
@@ -35,6 +37,13 @@ template <typename T> struct Ops {
   static int alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, double thr2, int* aidx,
                           double* residuals, int* info, cudaStream_t st);
 };
+
+// fused inverse (FP32, M = 1): solve + inverse 2D DFT + combination for depths j0 .. j0 + nj - 1
+bool fused_supported(int n);
+int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
+                  int Q, int j0, int nj, int output, cudaStream_t st);
+// W_q = V0_q / sum_q' V0_q'^2 on the R grid for the handle's cached sources
+int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st);
 
 // precision-independent table builders (alpha tables, fixed alpha)
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st);

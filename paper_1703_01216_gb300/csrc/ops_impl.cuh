@@ -24,25 +24,42 @@ template <typename T> static const typename cpx<T>::t* tw_of(const Handle* H, in
   else return H->tw64 + off;
 }
 
+constexpr int kSmallGrid = 2 * 152;  // below this many CTAs with the large tile, use the small one
+
+template <typename T, int N, int TY>
+static int row_r2c_t(const Handle* H, const T* in, long in_ps, typename cpx<T>::t* out, int nplanes, cudaStream_t st) {
+  constexpr size_t sm = row_r2c_smem<T, N, TY>();
+  auto kern = k_row_r2c<T, N, TY>;
+  FR3D_TRY(set_smem(kern, sm));
+  dim3 grid(N / TY, nplanes);
+  kern<<<grid, kThreads, sm, st>>>(in, in_ps, out, tw_of<T>(H, N / 2), tw_of<T>(H, N));
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+
 template <typename T, int N>
 static int row_r2c_n(const Handle* H, const T* in, long in_ps, typename cpx<T>::t* out, int nplanes, cudaStream_t st) {
-  constexpr size_t sm = row_r2c_smem<T, N>();
-  auto kern = k_row_r2c<T, N>;
+  constexpr int TY = RowTile<T, N>::v;
+  if ((long)nplanes * (N / TY) < kSmallGrid && SmallTile<N>::row < TY)
+    return row_r2c_t<T, N, SmallTile<N>::row>(H, in, in_ps, out, nplanes, st);
+  return row_r2c_t<T, N, TY>(H, in, in_ps, out, nplanes, st);
+}
+
+template <typename T, int N, bool INV, class Op, int TC>
+static int col_t(const Handle* H, const Op& op, int nplanes, cudaStream_t st) {
+  constexpr size_t sm = col_smem<T, N, TC>();
+  auto kern = k_col_fft<T, N, INV, Op, TC>;
   FR3D_TRY(set_smem(kern, sm));
-  dim3 grid(N / RowTile<T, N>::v, nplanes);
-  kern<<<grid, kThreads, sm, st>>>(in, in_ps, out, tw_of<T>(H, N / 2), tw_of<T>(H, N));
+  dim3 grid((N / 2 + 1 + TC - 1) / TC, nplanes);
+  kern<<<grid, kThreads, sm, st>>>(op, tw_of<T>(H, N));
   return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
 }
 
 template <typename T, int N, bool INV, class Op>
 static int col_n(const Handle* H, const Op& op, int nplanes, cudaStream_t st) {
-  constexpr size_t sm = col_smem<T, N>();
-  auto kern = k_col_fft<T, N, INV, Op>;
-  FR3D_TRY(set_smem(kern, sm));
   constexpr int TC = ColTile<T, N>::v;
-  dim3 grid((N / 2 + 1 + TC - 1) / TC, nplanes);
-  kern<<<grid, kThreads, sm, st>>>(op, tw_of<T>(H, N));
-  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+  if ((long)nplanes * ((N / 2 + TC) / TC) < kSmallGrid && SmallTile<N>::col < TC)
+    return col_t<T, N, INV, Op, SmallTile<N>::col>(H, op, nplanes, st);
+  return col_t<T, N, INV, Op, TC>(H, op, nplanes, st);
 }
 
 template <typename T, int N, int MODE>
@@ -204,36 +221,24 @@ int Ops<T>::zeta_from_xi(const Handle* H, const T* xi, T* zeta, int Q, const Src
 }
 
 // ---------------------------------------------------------------- discrepancy principle (Sec. 4)
-// Power of the data spectrum in frequency class c, summed over planes, with the Hermitian weight
-// of each stored half-spectrum bin (1 on the kx = 0 and kx = n/2 columns, 2 elsewhere).
-template <typename C>
-__device__ double class_power(const C* __restrict__ Uh, long ps, int nplanes, int n, int c) {
-  int p = (int)((sqrt(8.0 * c + 1.0) - 1.0) * 0.5);
+// (p, q) of class c = p (p + 1) / 2 + q, q <= p (exact integer correction of a float estimate)
+__device__ __forceinline__ void class_pq(int c, int& p, int& q) {
+  p = (int)((sqrtf(8.f * (float)c + 1.f) - 1.f) * 0.5f);
   while ((p + 1) * (p + 2) / 2 <= c) ++p;
   while (p * (p + 1) / 2 > c) --p;
-  const int q = c - p * (p + 1) / 2;
-  double acc = 0.0;
-  auto add = [&](int kx, int ky) {
-    const double wt = (kx == 0 || 2 * kx == n) ? 1.0 : 2.0;
-    for (int pl = 0; pl < nplanes; ++pl) {
-      const C v = Uh[pl * ps + (long)kx * n + ky];
-      const double re = (double)v.x, im = (double)v.y;
-      acc += wt * (re * re + im * im);
-    }
-  };
-  add(p, q);
-  if (q != 0 && 2 * q != n) add(p, n - q);
-  if (p != q) {
-    add(q, p);
-    if (p != 0 && 2 * p != n) add(q, n - p);
-  }
-  return acc;
+  q = c - p * (p + 1) / 2;
 }
 
+__device__ __forceinline__ double sq_abs(float2 v) { return (double)fmaf(v.x, v.x, v.y * v.y); }
+__device__ __forceinline__ double sq_abs(double2 v) { return fma(v.x, v.x, v.y * v.y); }
+
 constexpr int kAlphaCPB = 64;  // classes per block
+constexpr int kAlphaSplit = 4; // threads per class in the power gather
 
 // r^2(alpha_k) = n^-2 sum_c Ft[c][k] P[c]  (Parseval; M = 1 closed form of ||A zeta_alpha - U||^2),
-// deterministic: per-block partial sums in fixed order, reduced by the last block to finish.
+// with P[c] the data power of class c: every stored half-spectrum bin of the class, weighted 1 on
+// the kx = 0 and kx = n/2 columns and 2 elsewhere (their mirror bins are not stored), summed over
+// planes.  Deterministic: fixed-order partial sums per block, reduced by the last block to finish.
 template <typename C>
 __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
                                                       const double* __restrict__ Ft, int na, double thr2, double inv_n2,
@@ -243,11 +248,46 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
   __shared__ double sP[kAlphaCPB];
   __shared__ double red[256];
   __shared__ bool last;
+  extern __shared__ double sF[];             // [kAlphaCPB][na] slab of Ft for this block's classes
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * kAlphaCPB;
+  {
+    const int nF = min(kAlphaCPB, Cn - c0) * na;
+    const double* src = Ft + (long)c0 * na;
+#pragma unroll 4
+    for (int e = tid; e < nF; e += 256) sF[e] = __ldg(src + e);
+  }
+  {
+    const int cl = tid / kAlphaSplit, sub = tid % kAlphaSplit, c = c0 + cl;
+    double acc = 0.0;
+    if (c < Cn) {
+      int p, q;
+      class_pq(c, p, q);
+      // members (kx, ky) of the class in the half spectrum and their weights
+      int kxs[4], kys[4], nm = 0;
+      kxs[nm] = p; kys[nm++] = q;
+      if (q != 0 && 2 * q != n) { kxs[nm] = p; kys[nm++] = n - q; }
+      if (p != q) {
+        kxs[nm] = q; kys[nm++] = p;
+        if (p != 0 && 2 * p != n) { kxs[nm] = q; kys[nm++] = n - p; }
+      }
+      for (int mi = 0; mi < nm; ++mi) {
+        const double wt = (kxs[mi] == 0 || 2 * kxs[mi] == n) ? 1.0 : 2.0;
+        const C* b = Uh + (long)kxs[mi] * n + kys[mi];
+        double s = 0.0;
+#pragma unroll 4
+        for (int pl = sub; pl < nplanes; pl += kAlphaSplit) s += sq_abs(__ldg(b + pl * ps));
+        acc = fma(wt, s, acc);
+      }
+    }
+    red[tid] = acc;
+  }
+  __syncthreads();
   if (tid < kAlphaCPB) {
-    const int c = c0 + tid;
-    sP[tid] = c < Cn ? class_power(Uh, ps, nplanes, n, c) : 0.0;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kAlphaSplit; ++k) s += red[tid * kAlphaSplit + k];
+    sP[tid] = s;
   }
   __syncthreads();
   const int S = 256 / na;
@@ -256,7 +296,7 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
     double acc = 0.0;
     for (int cc = sub; cc < kAlphaCPB; cc += S) {
       const int c = c0 + cc;
-      if (c < Cn) acc = fma(__ldg(Ft + (long)c * na + k), sP[cc], acc);
+      if (c < Cn) acc = fma(sF[cc * na + k], sP[cc], acc);
     }
     red[tid] = acc;
   }
@@ -273,9 +313,19 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
   if (!last) return;
   __threadfence();
   __shared__ double r2[FR3D_MAX_ALPHAS];
+  // the S threads of candidate k sum every S-th block's partial (independent loads in flight),
+  // then the S sums are added in a fixed order
+  if (tid < S * na) {
+    const int k = tid % na, sub = tid / na;
+    double s = 0.0;
+#pragma unroll 4
+    for (int b = sub; b < (int)gridDim.x; b += S) s += __ldcg(partials + (long)b * na + k);
+    red[tid] = s;
+  }
+  __syncthreads();
   if (tid < na) {
     double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + (long)b * na + tid);
+    for (int sub = 0; sub < S; ++sub) s += red[sub * na + tid];
     r2[tid] = s * inv_n2;
     if (res_out) res_out[tid] = s * inv_n2;
   }
@@ -313,7 +363,9 @@ int Ops<T>::alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, doubl
     H->partial_cap = blocks * FR3D_MAX_ALPHAS;
   }
   const long ps = (long)(H->n / 2 + 1) * H->n;
-  k_alpha_choose<C><<<blocks, 256, 0, st>>>(Uh, ps, nplanes, H->n, H->C, H->Ft, n_alpha, thr2,
+  const size_t sm = sizeof(double) * kAlphaCPB * n_alpha;
+  FR3D_TRY(set_smem(k_alpha_choose<C>, sm));
+  k_alpha_choose<C><<<blocks, 256, sm, st>>>(Uh, ps, nplanes, H->n, H->C, H->Ft, n_alpha, thr2,
                                             1.0 / ((double)H->n * H->n), H->partials, H->counter, aidx, residuals,
                                             info);
   return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;

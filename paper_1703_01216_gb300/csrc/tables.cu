@@ -2,7 +2,8 @@
 // for every frequency class c and candidate alpha_k, with the regulariser alpha s^2,
 //   D[k][c]  = 1 / (n^2 (||A^(c)||^2 + alpha_k s^2))             (solve weight, M = 1)
 //   Ft[c][k] = (alpha_k s^2 / (||A^(c)||^2 + alpha_k s^2))^2     (residual filter, M = 1)
-// They are cached in the handle and rebuilt only when the candidate list changes.
+// They are cached in the handle and rebuilt only when the candidate list changes; D also has a
+// dense copy in the half-spectrum layout for the fused inverse.
 #include <string.h>
 
 #include "ops.cuh"
@@ -30,6 +31,16 @@ __global__ void k_alpha_tables(AlphaList al, int na, const double* __restrict__ 
   }
 }
 
+// dense per-bin copy of the solve weights: Dd[k][kx][ky] = D[k][class(kx, ky)]
+__global__ void k_dense_d(const float* __restrict__ D, int na, int Cn, int n, float* __restrict__ Dd) {
+  const long ps = (long)(n / 2 + 1) * n, total = na * ps;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / ps);
+    const long bin = idx % ps;
+    Dd[idx] = D[(long)k * Cn + class_of((int)(bin / n), (int)(bin % n), n)];
+  }
+}
+
 }  // namespace
 
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) {
@@ -39,20 +50,25 @@ int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) 
     cudaFree(H->Ft);
     cudaFree(H->D32);
     cudaFree(H->D64);
+    cudaFree(H->Dd32);
     H->Ft = nullptr;
     H->D32 = nullptr;
     H->D64 = nullptr;
+    H->Dd32 = nullptr;
     H->alpha_cap = 0;
-    FR3D_CUDA_TRY(cudaMalloc(&H->Ft, sizeof(double) * H->C * FR3D_MAX_ALPHAS));
-    FR3D_CUDA_TRY(cudaMalloc(&H->D32, sizeof(float) * H->C * FR3D_MAX_ALPHAS));
-    FR3D_CUDA_TRY(cudaMalloc(&H->D64, sizeof(double) * H->C * FR3D_MAX_ALPHAS));
-    H->alpha_cap = FR3D_MAX_ALPHAS;
+    const size_t ps = (size_t)(H->n / 2 + 1) * H->n;
+    FR3D_CUDA_TRY(cudaMalloc(&H->Ft, sizeof(double) * H->C * n_alpha));
+    FR3D_CUDA_TRY(cudaMalloc(&H->D32, sizeof(float) * H->C * n_alpha));
+    FR3D_CUDA_TRY(cudaMalloc(&H->D64, sizeof(double) * H->C * n_alpha));
+    FR3D_CUDA_TRY(cudaMalloc(&H->Dd32, sizeof(float) * ps * n_alpha));
+    H->alpha_cap = n_alpha;
   }
   AlphaList al;
   for (int k = 0; k < n_alpha; ++k) al.a[k] = alphas[k];
   const double inv_n2 = 1.0 / ((double)H->n * H->n);
   const int total = n_alpha * H->C;
   k_alpha_tables<<<(total + 255) / 256, 256, 0, st>>>(al, n_alpha, H->nrm, H->s2, H->C, inv_n2, H->Ft, H->D32, H->D64);
+  k_dense_d<<<1024, 256, 0, st>>>(H->D32, n_alpha, H->C, H->n, H->Dd32);
   FR3D_CUDA_TRY(cudaGetLastError());
   H->alpha_key.assign(alphas, alphas + n_alpha);
   return FR3D_OK;
@@ -63,12 +79,14 @@ int fixed_table(Handle* H, double alpha, cudaStream_t st) {
   if (!H->Dfix32) {
     FR3D_CUDA_TRY(cudaMalloc(&H->Dfix32, sizeof(float) * H->C));
     FR3D_CUDA_TRY(cudaMalloc(&H->Dfix64, sizeof(double) * H->C));
+    FR3D_CUDA_TRY(cudaMalloc(&H->Ddfix32, sizeof(float) * (size_t)(H->n / 2 + 1) * H->n));
   }
   AlphaList al;
   al.a[0] = alpha;
   const double inv_n2 = 1.0 / ((double)H->n * H->n);
   k_alpha_tables<<<(H->C + 255) / 256, 256, 0, st>>>(al, 1, H->nrm, H->s2, H->C, inv_n2, nullptr, H->Dfix32,
                                                      H->Dfix64);
+  k_dense_d<<<256, 256, 0, st>>>(H->Dfix32, 1, H->C, H->n, H->Ddfix32);
   FR3D_CUDA_TRY(cudaGetLastError());
   H->fixed_key = alpha;
   return FR3D_OK;

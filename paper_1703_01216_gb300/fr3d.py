@@ -233,7 +233,8 @@ def last_launch_count(handle: Handle) -> int:
     return int(load().fr3d_last_launch_count(handle.ptr))
 
 
-STAGE_NAMES = ("row_r2c", "col_fwd", "alpha", "col_solve", "row_c2r", "table", "contract", "col_inv", "other")
+STAGE_NAMES = ("row_r2c", "col_fwd", "alpha", "col_solve", "row_c2r", "table", "contract", "col_inv", "other",
+               "inv_fused")
 
 
 def profile_enable(handle: Handle, enable: bool = True):

@@ -182,7 +182,7 @@ def test_repeatable_and_launch_count(F):
         F.invert(H, Ud, w.Q, xi, F.Opts(alphas=w.alphas, delta=delta, points=w.sources))
         outs.append(host(xi))
     assert np.array_equal(outs[0], outs[1])          # deterministic reductions, no atomics on data
-    assert F.last_launch_count(H) >= 5
+    assert F.last_launch_count(H) >= 4
 
 
 # ------------------------------------------------------------------ full size (256^2 x 64, Q = 8, 64 alphas)
