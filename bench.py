@@ -133,8 +133,8 @@ def recorded_traffic(stage: str):
 def stage_bytes(stage: str, n: int, mp: int, q: int, nj: int) -> float:
     """Algorithmic DRAM bytes of one launch: every input read once, every output written once."""
     ps = (n // 2 + 1) * n                     # half-spectrum bins per plane
-    if stage == "inv_fused":                  # data spectra + kernel table in, 1/sum V0^2 in, xi out
-        return q * ps * 8.0 + mp * ps * 4.0 + mp * n * n * 8.0
+    if stage == "inv_fused":                  # data spectra, kernel table, solve row, combination weights in; xi out
+        return q * ps * 8.0 + mp * ps * 4.0 + ps * 4.0 + q * mp * n * n * 4.0 + mp * n * n * 4.0
     if stage == "row_c2r":                    # spectra of nj depths x q sources in, xi of nj depths out
         return nj * q * ps * 8.0 + nj * n * n * 4.0
     if stage == "col_solve":                  # data spectra + weights in, per-depth spectra out
@@ -234,11 +234,24 @@ def run_fr3d(args):
     opts = fr3d.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx, info=info)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
     st = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    for _ in range(args.warmup):      # untimed; the first call builds the cached tables and workspace
         flush.fill_(1.0)
         fr3d.invert(H, U, Q, out, opts)
     torch.cuda.synchronize()
+    # one step captured as a CUDA graph (its launches, and the stage events of the tracer)
     fr3d.profile_enable(H, True)
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(st)
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            fr3d.invert(H, U, Q, out, opts)
+    st.wait_stream(cap)
+    launches_per_step = fr3d.last_launch_count(H)
+    for _ in range(max(3, args.warmup)):
+        flush.fill_(1.0)
+        graph.replay()
+    torch.cuda.synchronize()
     stage_ms = {}
     stage_launches = {}
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -250,10 +263,12 @@ def run_fr3d(args):
         for k in range(args.steps):
             flush.fill_(1.0)
             ev[k][0].record(st)
-            fr3d.invert(H, U, Q, out, opts)
+            graph.replay()
             ev[k][1].record(st)
-            launches += fr3d.last_launch_count(H)
+            launches += launches_per_step
             for name, ms in fr3d.profile_read(H):
+                if name == "table":
+                    continue
                 stage_ms[name] = stage_ms.get(name, 0.0) + ms
                 stage_launches[name] = stage_launches.get(name, 0) + 1
         torch.cuda.synchronize()
@@ -314,7 +329,7 @@ def run_fr3d(args):
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (FFT) + f64 (alpha rule)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "m_prime": Mp, "m": 1, "q_sources": Q, "n_alpha": int(w.alphas.size),
-                   "voxels_per_instance": voxels, "instances_per_gpu": 1, "l2": "flushed (256 MB write) before every step",
+                   "voxels_per_instance": voxels, "instances_per_gpu": 1, "l2": "flushed (256 MB write) before every step", "launch": "one CUDA graph replay per step",
                    "parallelism": f"replicas x{world} (independent instances)"},
         "gpu_launches": launches,
         "e2e": {"value": voxels * world * e2e_steps / e2e_total, "unit": "voxels/s",

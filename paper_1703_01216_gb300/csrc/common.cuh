@@ -107,19 +107,25 @@ struct Launches {
 
 int ensure_ws(Handle* H, size_t bytes);
 
+// Opt a kernel in to `bytes` of dynamic shared memory once per (kernel, device); later calls are a
+// lookup, so launches inside a stream capture make no attribute call.
+int smem_optin(const void* kernel, size_t bytes);
+
 // stage kinds reported by fr3d_profile_read
 enum StageKind { kStRowR2C = 0, kStColFwd = 1, kStAlpha = 2, kStColSolve = 3, kStRowC2R = 4, kStTable = 5,
                  kStContract = 6, kStColInv = 7, kStOther = 8, kStFused = 9 };
+// cudaEventRecordExternal: inside a stream capture the record becomes a graph node, so a replayed
+// graph records the stage events too
 inline void prof_begin(Handle* H, cudaStream_t st) {
   H->n_ev = 0;
   if (!H->prof_on) return;
-  cudaEventRecord(H->ev[0], st);
+  cudaEventRecordWithFlags(H->ev[0], st, cudaEventRecordExternal);
   H->n_ev = 1;
 }
 inline void prof_mark(Handle* H, int kind, cudaStream_t st) {
   if (!H->prof_on || H->n_ev <= 0 || H->n_ev >= Handle::kMaxEv) return;
   H->ev_kind[H->n_ev - 1] = kind;
-  cudaEventRecord(H->ev[H->n_ev], st);
+  cudaEventRecordWithFlags(H->ev[H->n_ev], st, cudaEventRecordExternal);
   ++H->n_ev;
 }
 int twiddle_offset(const Handle* H, int L);

@@ -39,6 +39,28 @@ template <typename T, int N> struct ColTile {
   static constexpr int v = v1 > N / 2 + 1 ? N / 2 + 1 : v1;
 };
 
+// Copy TOTAL elements with NT threads, element e = tid + i NT, issuing B loads before their stores
+// so that several global loads are in flight per thread (ld(e) -> value, st(e, value)).
+template <int TOTAL, int NT, int B, typename LD, typename ST>
+__device__ __forceinline__ void batched_copy(int tid, LD ld, ST st) {
+  constexpr int IT = (TOTAL + NT - 1) / NT;
+  constexpr bool FULL = TOTAL % NT == 0;
+#pragma unroll
+  for (int b0 = 0; b0 < IT; b0 += B) {
+    decltype(ld(0)) v[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int e = tid + (b0 + i) * NT;
+      if (b0 + i < IT && (FULL || e < TOTAL)) v[i] = ld(e);
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int e = tid + (b0 + i) * NT;
+      if (b0 + i < IT && (FULL || e < TOTAL)) st(e, v[i]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- row pass, real -> half spectrum
 // in: planes of TY x n reals (plane stride in_ps); out: [plane][kx][y] complex.
 template <typename T, int N, int TY>
@@ -50,17 +72,18 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const T* __restrict__ in, 
   constexpr int L = N / 2, SS = Smem<C, L>::ss, STS = TY + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tws = reinterpret_cast<C*>(smem_raw);       // exp(-2 pi i t / n), t < n
-  C* buf = tws + N;
+  C* ptw = tws + N;                              // pass tables of the length-n/2 transform
+  C* buf = ptw + passtw_size<L>();
   C* stg = buf + TY * SS;
   const int tid = threadIdx.x, plane = blockIdx.y, y0 = blockIdx.x * TY;
   const C* src = reinterpret_cast<const C*>(in + plane * in_ps + (long)y0 * N);
   for (int e = tid; e < N; e += kThreads) tws[e] = __ldg(tw_full + e);
-  for (int e = tid; e < TY * L; e += kThreads) {
-    const int r = e / L, m = e - r * L;
-    buf[r * SS + pidx<C>(m)] = src[(long)r * L + m];
-  }
+  build_passtw<L, 2, kThreads>(ptw, tw_full, tid);
+  batched_copy<TY * L, kThreads, 8>(
+      tid, [&](int e) { return __ldg(src + e); },
+      [&](int e, C v) { buf[(e / L) * SS + pidx<C>(e % L)] = v; });
   __syncthreads();
-  fft_smem<L, false, TY, kThreads, 2>(buf, SS, tws, tid);
+  fft_smem<L, false, TY, kThreads>(buf, SS, ptw, tid);
   const T half = (T)0.5;
   for (int e = tid; e < TY * (L + 1); e += kThreads) {
     const int k = e / TY, r = e - k * TY;
@@ -86,20 +109,24 @@ __global__ void __launch_bounds__(kThreads) k_col_fft(Op op, const typename cpx<
   using C = typename cpx<T>::t;
   constexpr int SS = Smem<C, N>::ss, H1 = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tws = reinterpret_cast<C*>(smem_raw);       // exp(-2 pi i t / n), t < n
-  C* buf = tws + N;
+  C* ptw = reinterpret_cast<C*>(smem_raw);       // pass tables of the length-n transform
+  C* buf = ptw + passtw_size<N>();
   const int tid = threadIdx.x, plane = blockIdx.y, c0 = blockIdx.x * TC;
-  for (int e = tid; e < N; e += kThreads) tws[e] = __ldg(tw + e);
+  build_passtw<N, 1, kThreads>(ptw, tw, tid);
   op.begin(plane);
   const C* src = op.src(plane);
-  for (int e = tid; e < TC * N; e += kThreads) {
-    const int col = e / N, ky = e - col * N, kx = c0 + col;
-    C v = cmk((T)0, (T)0);
-    if (kx < H1) v = op.load(plane, kx, ky, src[(long)kx * N + ky]);
-    buf[col * SS + pidx<C>(ky)] = v;
-  }
+  batched_copy<TC * N, kThreads, 8>(
+      tid,
+      [&](int e) {
+        const int kx = c0 + e / N;
+        return kx < H1 ? src[(long)c0 * N + e] : cmk((T)0, (T)0);
+      },
+      [&](int e, C v) {
+        const int col = e / N, ky = e - col * N, kx = c0 + col;
+        buf[col * SS + pidx<C>(ky)] = kx < H1 ? op.load(plane, kx, ky, v) : v;
+      });
   __syncthreads();
-  fft_smem<N, INV, TC, kThreads>(buf, SS, tws, tid);
+  fft_smem<N, INV, TC, kThreads>(buf, SS, ptw, tid);
   C* dst = op.dst(plane);
   for (int e = tid; e < TC * N; e += kThreads) {
     const int col = e / N, ky = e - col * N, kx = c0 + col;
@@ -197,10 +224,12 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const typename cpx<T>::t* 
   constexpr int EPT = (TY * L + kThreads - 1) / kThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tws = reinterpret_cast<C*>(smem_raw);       // exp(-2 pi i t / n), t < n
-  C* buf = tws + N;
+  C* ptw = tws + N;                              // pass tables of the length-n/2 transform
+  C* buf = ptw + passtw_size<L>();
   const int tid = threadIdx.x, y0 = blockIdx.x * TY;
   const long ps = (long)(L + 1) * N;
   for (int e = tid; e < N; e += kThreads) tws[e] = __ldg(tw_full + e);
+  build_passtw<L, 2, kThreads>(ptw, tw_full, tid);
   T num[EPT][2], den[EPT][2];
   if (MODE == 1) {
 #pragma unroll
@@ -232,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const typename cpx<T>::t* 
       }
     }
     __syncthreads();
-    fft_smem<L, true, TY, kThreads, 2>(buf, SS, tws, tid);
+    fft_smem<L, true, TY, kThreads>(buf, SS, ptw, tid);
     if (MODE == 0) {
       const int jc = ip / Q, qq = ip - jc * Q;
       T* o = out + ((long)qq * out_stride + j0 + jc) * N * N + (long)y0 * N;
@@ -279,11 +308,11 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const typename cpx<T>::t* 
 template <typename T, int N, int TY> constexpr size_t row_r2c_smem() {
   using C = typename cpx<T>::t;
   constexpr int L = N / 2;
-  return sizeof(C) * ((size_t)N + (size_t)TY * Smem<C, L>::ss + (size_t)(L + 1) * (TY + 1));
+  return sizeof(C) * ((size_t)N + passtw_size<L>() + (size_t)TY * Smem<C, L>::ss + (size_t)(L + 1) * (TY + 1));
 }
 template <typename T, int N, int TC> constexpr size_t col_smem() {
   using C = typename cpx<T>::t;
-  return sizeof(C) * ((size_t)N + (size_t)TC * Smem<C, N>::ss);
+  return sizeof(C) * ((size_t)passtw_size<N>() + (size_t)TC * Smem<C, N>::ss);
 }
 // small tiles for transforms of few planes (more CTAs in flight)
 template <int N> struct SmallTile {
@@ -296,7 +325,7 @@ template <typename T, int N, int MODE> constexpr int row_c2r_tile() {
 }
 template <typename T, int N, int MODE> constexpr size_t row_c2r_smem() {
   using C = typename cpx<T>::t;
-  return sizeof(C) * ((size_t)N + (size_t)row_c2r_tile<T, N, MODE>() * Smem<C, N / 2>::ss);
+  return sizeof(C) * ((size_t)N + passtw_size<N / 2>() + (size_t)row_c2r_tile<T, N, MODE>() * Smem<C, N / 2>::ss);
 }
 
 }  // namespace fr3d

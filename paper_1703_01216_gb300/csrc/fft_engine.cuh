@@ -159,12 +159,46 @@ template <typename C> struct PadShift { static constexpr int v = sizeof(C) == 8 
 template <int L, typename C> struct PaddedLen { static constexpr int v = L + (L >> PadShift<C>::v); };
 template <typename C> __device__ __forceinline__ int pidx(int e) { return e + (e >> PadShift<C>::v); }
 
+// Per-pass twiddle tables.  Pass p of length L (radix R_p, NS_p = product of the earlier radices)
+// with NS_p > 1 needs w^(r jj L/(NS_p R_p)) for r in [1, R_p) and jj in [0, NS_p), w = exp(-2 pi i / L).
+// They are stored pass after pass as blocks [r - 1][jj]: a warp's lanes (consecutive jj) read
+// consecutive entries, so shared-memory reads are free of bank conflicts.
+template <int L> constexpr int passtw_offset(int p) {
+  int off = 0, ns = 1;
+  for (int i = 0; i < p; ++i) {
+    const int R = Plan<L>::radix(i);
+    if (ns > 1) off += (R - 1) * ns;
+    ns *= R;
+  }
+  return off;
+}
+template <int L> constexpr int passtw_size() { return passtw_offset<L>(Plan<L>::np); }
+
+// Fill the pass tables of length L from tw_g[t] = exp(-2 pi i t / (TS L)), t < TS L (global memory).
+template <int L, int TS, int NTHR, typename C>
+__device__ __forceinline__ void build_passtw(C* dst, const C* __restrict__ tw_g, int tid) {
+  constexpr int NP = Plan<L>::np;
+  int ns = 1, off = 0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int R = Plan<L>::radix(p);
+    if (ns > 1) {
+      const int cnt = (R - 1) * ns, step = L / (ns * R);
+      for (int e = tid; e < cnt; e += NTHR) {
+        const int r = e / ns + 1, jj = e % ns;
+        dst[off + e] = __ldg(tw_g + r * jj * step * TS);
+      }
+      off += cnt;
+    }
+    ns *= R;
+  }
+}
+
 // One Stockham pass.  Butterfly j of a sequence reads elements j + r L/R (r < R), multiplies
-// element r by w^(r (j mod NS) L/(NS R)), with w = exp(-+2 pi i / L), and writes the R-point
-// DFT to positions (j / NS) NS R + (j mod NS) + r NS.  The twiddle table holds exp(-2 pi i t / (TS L))
-// (every TS-th entry is used), usually staged in shared memory by the calling kernel.
-template <int L, int R, int NS, bool INV, int NSEQ, int NTHR, int TS, typename C>
-__device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __restrict__ tw, int tid) {
+// element r by w^(r (j mod NS) L/(NS R)), with w = exp(-+2 pi i / L), taken from the pass table
+// twp = [r - 1][j mod NS], and writes the R-point DFT to positions (j / NS) NS R + (j mod NS) + r NS.
+template <int L, int R, int NS, bool INV, int NSEQ, int NTHR, typename C>
+__device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __restrict__ twp, int tid) {
   constexpr int BPS = L / R;
   constexpr int NB = NSEQ * BPS;
   constexpr int K = (NB + NTHR - 1) / NTHR;
@@ -181,7 +215,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __re
       for (int r = 0; r < R; ++r) {
         C x = base[pidx<C>(j + r * BPS)];
         if (NS > 1 && r > 0) {
-          C w = tw[r * jj * (L / (NS * R)) * TS];
+          C w = twp[(r - 1) * NS + jj];
           if (INV) w = cconj(w);
           x = cmul(x, w);
         }
@@ -206,12 +240,13 @@ __device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __re
   __syncthreads();
 }
 
-template <int L, bool INV, int NSEQ, int NTHR, int TS = 1, int P = 0, int NS = 1, typename C>
-__device__ __forceinline__ void fft_smem(C* buf, int sstride, const C* __restrict__ tw, int tid) {
+// All passes of an L-point FFT on NSEQ sequences (stride sstride); twp = pass tables of length L.
+template <int L, bool INV, int NSEQ, int NTHR, int P = 0, int NS = 1, typename C>
+__device__ __forceinline__ void fft_smem(C* buf, int sstride, const C* __restrict__ twp, int tid) {
   if constexpr (P < Plan<L>::np) {
     constexpr int R = Plan<L>::radix(P);
-    stockham_pass<L, R, NS, INV, NSEQ, NTHR, TS>(buf, sstride, tw, tid);
-    fft_smem<L, INV, NSEQ, NTHR, TS, P + 1, NS * R>(buf, sstride, tw, tid);
+    stockham_pass<L, R, NS, INV, NSEQ, NTHR>(buf, sstride, twp + passtw_offset<L>(P), tid);
+    fft_smem<L, INV, NSEQ, NTHR, P + 1, NS * R>(buf, sstride, twp, tid);
   }
 }
 

@@ -30,6 +30,13 @@ namespace fr3d {
 
 namespace cg = cooperative_groups;
 
+// Split cluster barrier: arrive without ordering memory (the caller's reads of peer shared memory
+// have completed: their values were consumed) and wait later.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
+
 template <int N> struct FusedCfg;
 // CL: CTAs per cluster, NT: threads, RB: rows per row batch, MINB: resident CTAs per SM that the
 // register budget is sized for
@@ -55,9 +62,11 @@ template <int N> struct FusedGeom {
   static constexpr int SSR = Smem<float2, L>::ss;      // row stride
   static constexpr int EPT = RB * L / NT;              // complex outputs per thread per batch
   static constexpr int NSPL = RB * (L / 2 + 1);        // Hermitian-split pairs per batch
-  // shared memory: columns, rows, twiddles, weights (+ the kx = n/2 weights), xi accumulator
-  static constexpr size_t smem_zeta =
-      sizeof(float2) * ((size_t)CPC * SSC + (size_t)RB * SSR + N) + sizeof(float) * (size_t)(CPC + 1) * N;
+  // shared memory: columns, rows, twiddles, pass tables (length n, n/2), weights (+ the kx = n/2
+  // weights), xi accumulator
+  static constexpr int PTC = passtw_size<N>(), PTR = passtw_size<L>();
+  static constexpr size_t smem_zeta = sizeof(float2) * ((size_t)CPC * SSC + (size_t)RB * SSR + N + PTC + PTR) +
+                                      sizeof(float) * (size_t)(CPC + 1) * N;
   static constexpr size_t smem_xi = smem_zeta + sizeof(float) * (size_t)NRW * N;
   static_assert(L % CL == 0, "column split");
   static_assert(NRW % RB == 0, "row batches");
@@ -89,7 +98,9 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
   float2* colbuf = reinterpret_cast<float2*>(smem_raw);
   float2* rowbuf = colbuf + CPC * SSC;
   float2* tws = rowbuf + RB * SSR;           // exp(-2 pi i t / n), t < n
-  float* wsm = reinterpret_cast<float*>(tws + N);   // [CPC][n] weights of the owned columns, then w(n/2, .)
+  float2* ptc = tws + N;                     // pass tables, length n (columns)
+  float2* ptr = ptc + G::PTC;                // pass tables, length n/2 (rows)
+  float* wsm = reinterpret_cast<float*>(ptr + G::PTR);   // [CPC][n] weights of the owned columns, then w(n/2, .)
   float2* accs = reinterpret_cast<float2*>(wsm + (CPC + 1) * N);  // XI: [NRW][n/2] pairs of the owned rows
   const int tid = threadIdx.x;
   int r = 0;
@@ -105,6 +116,8 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
     const float* Aj = a.A + (long)j * ps;
     const float* drow = a.Dd + (long)(*a.aidx) * ps;
     for (int e = tid; e < N; e += NT) tws[e] = __ldg(a.tw_n + e);
+    build_passtw<N, 1, NT>(ptc, a.tw_n, tid);
+    build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
 #pragma unroll
     for (int b0 = 0; b0 < CLD; b0 += CB) {
       float wa[CB], wd[CB];
@@ -140,6 +153,9 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
 
   for (int q = 0; q < a.Q; ++q) {
     const float2* Zq = a.Uh + (long)q * ps;
+    // the peers' reads of this CTA's columns for q - 1 are done (arrive below) before overwriting
+    if constexpr (CL > 1)
+      if (q > 0) cluster_wait();
     // ---------------- column phase
 #pragma unroll
     for (int b0 = 0; b0 < CLD; b0 += CB) {
@@ -165,11 +181,19 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
       }
     }
     __syncthreads();
-    fft_smem<N, true, CPC, NT>(colbuf, SSC, tws, tid);
+    fft_smem<N, true, CPC, NT>(colbuf, SSC, ptc, tid);
     if constexpr (CL > 1) cg::this_cluster().sync();
     // ---------------- row phase
 #pragma unroll 1
     for (int b = 0; b < NB; ++b) {
+      // combination weights of this batch, requested now so that the HBM latency overlaps the
+      // split and the row transforms
+      float2 wv[EPT];
+      if constexpr (MODE == 1) {
+        const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + j) * N + y0 + b * RB) * N);
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) wv[i] = __ldg(wq + tid + i * NT);   // [row][mm] pairs of the batch
+      }
       // Hermitian split Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), pairs (k, L - k)
       constexpr int SIT = (G::NSPL + NT - 1) / NT;
       float2 xa[SIT], xb[SIT];
@@ -182,6 +206,8 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
           xb[i] = xat(L - k, y);
         }
       }
+      if constexpr (CL > 1)
+        if (b == NB - 1) cluster_arrive_relaxed();   // last reads of peer columns for this q
 #pragma unroll
       for (int i = 0; i < SIT; ++i) {
         const int e = tid + i * NT;
@@ -199,12 +225,8 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
         }
       }
       __syncthreads();
-      fft_smem<L, true, RB, NT, 2>(rowbuf, SSR, tws, tid);
+      fft_smem<L, true, RB, NT>(rowbuf, SSR, ptr, tid);
       if constexpr (MODE == 1) {
-        const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + j) * N + y0 + b * RB) * N);
-        float2 wv[EPT];
-#pragma unroll
-        for (int i = 0; i < EPT; ++i) wv[i] = __ldg(wq + tid + i * NT);   // [row][mm] pairs of the batch
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
           const int e = tid + i * NT;
@@ -225,8 +247,9 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
       }
       __syncthreads();
     }
-    if constexpr (CL > 1) cg::this_cluster().sync();
   }
+  // no CTA leaves while a peer may still read its shared memory
+  if constexpr (CL > 1) cluster_wait();
   if constexpr (MODE == 1) {
     // xi of the owned rows; the last barrier of the q loop ordered every accumulator write first
     float2* ov = reinterpret_cast<float2*>(a.out + ((long)j * N + y0) * N);

@@ -11,9 +11,7 @@ int launch_fused(const Handle* H, const FusedArgs& a, int nj, cudaStream_t st) {
   using G = FusedGeom<N>;
   auto kern = k_inv_fused<N, MODE>;
   constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;
-  if (sm > 48 * 1024)
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-      return FR3D_ERR_CUDA;
+  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(kern), sm));
   kern<<<nj * G::CL, G::NT, sm, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
 }

@@ -11,11 +11,7 @@ namespace fr3d {
 #define FR3D_FOR_EACH_N(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
 
 template <typename K> static int set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-      return FR3D_ERR_CUDA;
-  }
-  return FR3D_OK;
+  return smem_optin(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 template <typename T> static const typename cpx<T>::t* tw_of(const Handle* H, int L) {
@@ -251,37 +247,50 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
   extern __shared__ double sF[];             // [kAlphaCPB][na] slab of Ft for this block's classes
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * kAlphaCPB;
-  {
-    const int nF = min(kAlphaCPB, Cn - c0) * na;
-    const double* src = Ft + (long)c0 * na;
-#pragma unroll 4
-    for (int e = tid; e < nF; e += 256) sF[e] = __ldg(src + e);
-  }
-  {
-    const int cl = tid / kAlphaSplit, sub = tid % kAlphaSplit, c = c0 + cl;
-    double acc = 0.0;
-    if (c < Cn) {
-      int p, q;
-      class_pq(c, p, q);
-      // members (kx, ky) of the class in the half spectrum and their weights
-      int kxs[4], kys[4], nm = 0;
-      kxs[nm] = p; kys[nm++] = q;
-      if (q != 0 && 2 * q != n) { kxs[nm] = p; kys[nm++] = n - q; }
-      if (p != q) {
-        kxs[nm] = q; kys[nm++] = p;
-        if (p != 0 && 2 * p != n) { kxs[nm] = q; kys[nm++] = n - p; }
-      }
-      for (int mi = 0; mi < nm; ++mi) {
-        const double wt = (kxs[mi] == 0 || 2 * kxs[mi] == n) ? 1.0 : 2.0;
-        const C* b = Uh + (long)kxs[mi] * n + kys[mi];
-        double s = 0.0;
-#pragma unroll 4
-        for (int pl = sub; pl < nplanes; pl += kAlphaSplit) s += sq_abs(__ldg(b + pl * ps));
-        acc = fma(wt, s, acc);
-      }
+  const int nF = min(kAlphaCPB, Cn - c0) * na;
+  const double* slab = Ft + (long)c0 * na;
+  // one round of global loads: this thread's share of the class powers and of the filter slab
+  const int cl = tid / kAlphaSplit, sub = tid % kAlphaSplit, c = c0 + cl;
+  int kxs[4] = {0, 0, 0, 0}, kys[4] = {0, 0, 0, 0}, nm = 0;
+  if (c < Cn) {
+    int p, q;
+    class_pq(c, p, q);
+    // members (kx, ky) of the class in the half spectrum
+    kxs[nm] = p; kys[nm++] = q;
+    if (q != 0 && 2 * q != n) { kxs[nm] = p; kys[nm++] = n - q; }
+    if (p != q) {
+      kxs[nm] = q; kys[nm++] = p;
+      if (p != 0 && 2 * p != n) { kxs[nm] = q; kys[nm++] = n - p; }
     }
-    red[tid] = acc;
   }
+  double f[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int e = tid + i * 256;
+    f[i] = e < nF ? __ldg(slab + e) : 0.0;
+  }
+  double acc = 0.0;
+  for (int pl0 = sub; pl0 < nplanes; pl0 += 2 * kAlphaSplit) {
+    double s[4][2];
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int pl = pl0 + u * kAlphaSplit;
+        s[mi][u] = (mi < nm && pl < nplanes) ? sq_abs(__ldg(Uh + pl * ps + (long)kxs[mi] * n + kys[mi])) : 0.0;
+      }
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+      if (mi < nm) acc = fma((kxs[mi] == 0 || 2 * kxs[mi] == n) ? 1.0 : 2.0, s[mi][0] + s[mi][1], acc);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int e = tid + i * 256;
+    if (e < nF) sF[e] = f[i];
+  }
+  // slabs longer than 16 loads per thread (more than 64 candidates) finish here
+  for (int e = tid + 16 * 256; e < nF; e += 256) sF[e] = __ldg(slab + e);
+  red[tid] = acc;
   __syncthreads();
   if (tid < kAlphaCPB) {
     double s = 0.0;
@@ -292,18 +301,17 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
   __syncthreads();
   const int S = 256 / na;
   if (tid < S * na) {
-    const int k = tid % na, sub = tid / na;
-    double acc = 0.0;
-    for (int cc = sub; cc < kAlphaCPB; cc += S) {
-      const int c = c0 + cc;
-      if (c < Cn) acc = fma(sF[cc * na + k], sP[cc], acc);
+    const int k = tid % na, sb = tid / na;
+    double a2 = 0.0;
+    for (int cc = sb; cc < kAlphaCPB; cc += S) {
+      if (c0 + cc < Cn) a2 = fma(sF[cc * na + k], sP[cc], a2);
     }
-    red[tid] = acc;
+    red[tid] = a2;
   }
   __syncthreads();
   if (tid < na) {
     double s = 0.0;
-    for (int sub = 0; sub < S; ++sub) s += red[sub * na + tid];
+    for (int sb = 0; sb < S; ++sb) s += red[sb * na + tid];
     partials[(long)blockIdx.x * na + tid] = s;
   }
   __threadfence();
@@ -313,19 +321,27 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
   if (!last) return;
   __threadfence();
   __shared__ double r2[FR3D_MAX_ALPHAS];
-  // the S threads of candidate k sum every S-th block's partial (independent loads in flight),
+  // the S threads of candidate k sum every S-th block's partial, 16 loads in flight per round,
   // then the S sums are added in a fixed order
   if (tid < S * na) {
-    const int k = tid % na, sub = tid / na;
+    const int k = tid % na, sb = tid / na;
     double s = 0.0;
-#pragma unroll 4
-    for (int b = sub; b < (int)gridDim.x; b += S) s += __ldcg(partials + (long)b * na + k);
+    for (int b0 = sb; b0 < (int)gridDim.x; b0 += 16 * S) {
+      double v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int b = b0 + i * S;
+        v[i] = b < (int)gridDim.x ? __ldcg(partials + (long)b * na + k) : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) s += v[i];
+    }
     red[tid] = s;
   }
   __syncthreads();
   if (tid < na) {
     double s = 0.0;
-    for (int sub = 0; sub < S; ++sub) s += red[sub * na + tid];
+    for (int sb = 0; sb < S; ++sb) s += red[sb * na + tid];
     r2[tid] = s * inv_n2;
     if (res_out) res_out[tid] = s * inv_n2;
   }

@@ -10,7 +10,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -125,6 +127,20 @@ int twiddle_offset(const Handle* H, int L) {
   for (int i = 0; i < kNumLengths; ++i)
     if (kLengths[i] == L) return H->tw_off[i];
   return -1;
+}
+
+int smem_optin(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return FR3D_OK;
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  FR3D_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& d : done)
+    if (d.first == kernel && d.second == dev) return FR3D_OK;
+  FR3D_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done.emplace_back(kernel, dev);
+  return FR3D_OK;
 }
 
 int ensure_ws(Handle* H, size_t bytes) {
