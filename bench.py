@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fr3d", choices=["fr3d", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -342,6 +343,8 @@ def run_fr3d(args):
     }
     clocks = clk.summary()
     result["clocks"] = clocks
+    if rank == 0 and not args.no_batch:
+        result["batched"] = bench_batched(args, dev, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -355,6 +358,66 @@ def run_fr3d(args):
         print(json.dumps(result))
     if dist:
         dist.destroy_process_group()
+
+
+def bench_batched(args, dev, flush, count=64):
+    """The uneven 64-instance workload (n in {64..256}, M' in {16..64}, 1-8 sources, 32 alphas):
+    one batch plan replayed as a CUDA graph, against the same instances inverted one call at a time
+    (also graph-captured).  voxels/s over all instances; L2 flushed before each timed repetition."""
+    import torch
+    from paper_1703_01216_gb300 import fr3d
+    from paper_1703_01216_gb300 import inputs as I
+    wls = I.batch_workloads(count)
+    items = []
+    voxels = 0
+    for w in wls:
+        H, U, delta = setup_gpu(w, dev)
+        idx = torch.zeros(1, dtype=torch.int32, device=dev)
+        opts = fr3d.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx)
+        out = torch.empty((w.Mp, w.n, w.n), device=dev)
+        items.append((H, U, w.Q, opts, out))
+        voxels += w.n * w.n * w.Mp
+    for (H, U, Q, opts, out) in items:            # build every instance's tables and workspace
+        fr3d.invert(H, U, Q, out, opts)
+    B = fr3d.Batch(items)
+    st = torch.cuda.current_stream(dev)
+    graphs = {}
+    for mode in ("batched", "looped"):
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(st)
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g, stream=cap):
+                if mode == "batched":
+                    B.run()
+                else:
+                    for (H, U, Q, opts, out) in items:
+                        fr3d.invert(H, U, Q, out, opts)
+        st.wait_stream(cap)
+        graphs[mode] = g
+    res = {}
+    reps = max(5, min(args.steps, 20))
+    for mode, g in graphs.items():
+        for _ in range(3):
+            flush.fill_(1.0)
+            g.replay()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            g.replay()
+            b.record(st)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        res[mode] = voxels * reps / (tot * 1e-3)
+    launches_looped = sum(4 for _ in items)
+    out = {"workload": f"{count} uneven instances (n 64-256, M' 16-64, Q 1-8, 32 alphas)", "voxels": voxels,
+           "value": res["batched"], "looped_value": res["looped"], "unit": "voxels/s",
+           "launches_batched": B.launches, "launches_looped": launches_looped, "reps": reps}
+    B.close()
+    return out
 
 
 def run_reference(args):

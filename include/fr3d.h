@@ -170,6 +170,31 @@ int fr3d_invert(fr3d_handle* h, const void* U, int Q, const fr3d_invert_opts* op
 int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_invert_opts* opts,
                      void* out_host, void* stream);
 
+/* ---- batched inversion of independent instances of uneven size ----
+ * Each instance is one call of fr3d_invert (FP32, M = 1) with its own handle (geometry), data,
+ * options and output; all instances of a batch use the same output kind.  Instances must have
+ * distinct handles (a handle's workspace holds one instance's spectra).  A plan groups the
+ * instances by grid size n and runs Algorithm 1 for each group with four launches covering all of
+ * its instances (data row pass, data column pass, alpha rule, fused inverse).  fr3d_batch_create
+ * builds every table and workspace and uploads the descriptors (it synchronises `stream`); the
+ * device pointers and options of the instances are fixed at creation.  fr3d_batch_run only
+ * launches kernels (it can be captured in a CUDA graph).  The paper has no batch form: this is
+ * Algorithm 1 applied to many independent problems at once. */
+typedef struct fr3d_instance {
+  fr3d_handle* handle;            /* geometry and kernel tables (fr3d_kernel_transform) */
+  const float* U;                 /* device [Q][1][n][n] data */
+  int Q;                          /* source parameters of this instance */
+  const fr3d_invert_opts* opts;   /* alpha rule, sources (XI), output; precision must be FP32 */
+  float* out;                     /* device [M'][n][n] (XI) or [Q][M'][n][n] (ZETA) */
+} fr3d_instance;
+typedef struct fr3d_batch fr3d_batch;
+int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** out, void* stream);
+int fr3d_batch_run(fr3d_batch* b, void* stream);
+int fr3d_batch_launch_count(fr3d_batch* b);
+void fr3d_batch_destroy(fr3d_batch* b);
+/* create + run + synchronise + destroy in one call */
+int fr3d_invert_batched(const fr3d_instance* inst, int n, void* stream);
+
 /* Number of kernel launches the last call on this handle enqueued (cache rebuilds excluded). */
 int fr3d_last_launch_count(fr3d_handle* h);
 

@@ -274,6 +274,37 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
 
 }  // namespace
 
+// Everything a batched run of this instance needs, built now: sources, combination weights, alpha
+// tables, the data-spectrum workspace and the alpha-rule partial sums.  Returns the spectrum buffer,
+// the dense solve-weight table and the device word that will hold the chosen alpha index.
+int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** Uh, const float** Dd,
+                         const int** aidx, cudaStream_t st) {
+  FR3D_TRY(check_invert_args(H, Q, o));
+  const InvertPlan p = plan_invert<float>(H, Q, false, o->output);
+  FR3D_TRY(ensure_ws(H, p.total));
+  *Uh = reinterpret_cast<float2*>((char*)H->ws + p.uh_off);
+  if (o->output == FR3D_OUT_XI) FR3D_TRY(ensure_wtab(H, o->sources, st));
+  if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    const int blocks = (H->C + 63) / 64;
+    if (H->partial_cap < blocks * FR3D_MAX_ALPHAS) {
+      if (H->partials) cudaFree(H->partials);
+      H->partials = nullptr;
+      H->partial_cap = 0;
+      FR3D_CUDA_TRY(cudaMalloc(&H->partials, sizeof(double) * blocks * FR3D_MAX_ALPHAS));
+      H->partial_cap = blocks * FR3D_MAX_ALPHAS;
+    }
+    *Dd = H->Dd32;
+    *aidx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
+  } else {
+    FR3D_TRY(fixed_table(H, o->alpha, st));
+    *Dd = H->Ddfix32;
+    *aidx = H->zero_idx;
+  }
+  FR3D_CUDA_TRY(cudaStreamSynchronize(st));
+  return FR3D_OK;
+}
+
 }  // namespace fr3d
 
 using fr3d::Handle;

@@ -1,0 +1,222 @@
+// Batched inversion of many independent instances of uneven size (grid n, depths M', sources Q):
+// a batch plan groups the instances by n and runs Algorithm 1 for every group with four launches
+// (data row pass, data column pass, alpha rule, fused inverse), each covering all instances of the
+// group through device tables of per-plane, per-instance and per-cluster descriptors.  The plan
+// is built once (tables, workspaces, descriptors); running it only launches kernels, so it can be
+// captured in a CUDA graph.
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "fused.cuh"
+#include "ops_impl.cuh"
+
+namespace fr3d {
+
+struct AlphaInst {
+  const float2* Uh;
+  const double* Ft;
+  double* partials;
+  unsigned* counter;
+  int* aidx;
+  double* res;
+  int* info;
+  double thr2;
+  int nplanes, na, bstart, nblk;
+};
+
+__global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst, long ps, int n,
+                                                       int Cn, double inv_n2) {
+  int i = 0;
+  while (i + 1 < ninst && inst[i + 1].bstart <= (int)blockIdx.x) ++i;
+  const AlphaInst a = inst[i];
+  alpha_choose_body<float2>(a.Uh, ps, a.nplanes, n, Cn, a.Ft, a.na, a.thr2, inv_n2, a.partials, a.counter, a.aidx,
+                            a.res, a.info, (int)blockIdx.x - a.bstart, a.nblk);
+}
+
+int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st);
+void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
+                    int Q, FusedArgs* a);
+int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** Uh, const float** Dd, const int** aidx,
+                         cudaStream_t st);
+
+namespace {
+
+struct Group {
+  int n = 0;
+  const Handle* H0 = nullptr;
+  int nplanes = 0, nalpha_inst = 0, nalpha_blk = 0, nclusters = 0, max_na = 0;
+  size_t off_planes = 0, off_alpha = 0, off_fused = 0, off_map = 0;
+};
+
+template <int N>
+int run_group_n(const Group& g, const unsigned char* dev, int output, cudaStream_t st) {
+  const PlanePtr* planes = reinterpret_cast<const PlanePtr*>(dev + g.off_planes);
+  constexpr int TY = SmallTile<N>::row, TC = SmallTile<N>::col;
+  FR3D_TRY((row_r2c_t<float, N, TY, TablePlanes>(g.H0, TablePlanes{planes}, g.nplanes, st)));
+  FR3D_TRY((col_t<float, N, false, ColTable, TC>(g.H0, ColTable{planes}, g.nplanes, st)));
+  if (g.nalpha_inst > 0) {
+    const size_t sm = sizeof(double) * kAlphaCPB * g.max_na;
+    FR3D_TRY(smem_optin(reinterpret_cast<const void*>(k_alpha_batched), sm));
+    k_alpha_batched<<<g.nalpha_blk, 256, sm, st>>>(reinterpret_cast<const AlphaInst*>(dev + g.off_alpha),
+                                                   g.nalpha_inst, (long)(N / 2 + 1) * N, N, num_classes(N),
+                                                   1.0 / ((double)N * N));
+    FR3D_CUDA_TRY(cudaGetLastError());
+  }
+  return inv_fused_batched_f32(N, reinterpret_cast<const FusedArgs*>(dev + g.off_fused),
+                               reinterpret_cast<const int2*>(dev + g.off_map), g.nclusters, output, st);
+}
+
+int run_group(const Group& g, const unsigned char* dev, int output, cudaStream_t st) {
+  switch (g.n) {
+#define X(N) \
+  case N: return run_group_n<N>(g, dev, output, st);
+    X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct Batch {
+  std::vector<Group> groups;
+  unsigned char* dev = nullptr;
+  int output = FR3D_OUT_XI;
+  int launches = 0;
+};
+
+}  // namespace fr3d
+
+struct fr3d_batch {
+  fr3d::Batch b;
+};
+
+extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** out, void* stream) {
+  using namespace fr3d;
+  if (!inst || n < 1 || !out) return FR3D_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int output = inst[0].opts ? inst[0].opts->output : FR3D_OUT_XI;
+  // per-instance preparation (tables, workspaces), grouped by grid size
+  std::map<int, std::vector<int>> by_n;
+  std::vector<float2*> uh(n);
+  std::vector<const float*> dd(n);
+  std::vector<const int*> ai(n);
+  for (int i = 0; i < n; ++i) {
+    const fr3d_instance& I = inst[i];
+    if (!I.handle || !I.U || !I.out || !I.opts || I.Q < 1) return FR3D_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (inst[k].handle == I.handle) return FR3D_ERR_INVALID_ARG;   // one workspace per handle
+    if (I.opts->output != output || I.opts->precision != FR3D_PREC_FP32) return FR3D_ERR_INVALID_ARG;
+    Handle* H = &I.handle->h;
+    if (H->M != 1 || !fused_supported(H->n)) return FR3D_ERR_UNSUPPORTED_SIZE;
+    FR3D_TRY(prepare_instance_f32(H, I.Q, I.opts, &uh[i], &dd[i], &ai[i], st));
+    by_n[H->n].push_back(i);
+  }
+  // descriptor tables
+  Batch b;
+  b.output = output;
+  std::vector<unsigned char> host;
+  auto put = [&](const void* p, size_t bytes) {
+    const size_t off = al(host.size());
+    host.resize(off + bytes);
+    memcpy(host.data() + off, p, bytes);
+    return off;
+  };
+  for (auto& kv : by_n) {
+    Group g;
+    g.n = kv.first;
+    g.H0 = &inst[kv.second[0]].handle->h;
+    std::vector<PlanePtr> planes;
+    std::vector<AlphaInst> alph;
+    std::vector<FusedArgs> fa;
+    std::vector<int2> map;
+    const long ps = (long)(g.n / 2 + 1) * g.n;
+    for (int idx : kv.second) {
+      const fr3d_instance& I = inst[idx];
+      Handle* H = &I.handle->h;
+      for (int q = 0; q < I.Q; ++q) planes.push_back({I.U + (long)q * g.n * g.n, uh[idx] + q * ps});
+      if (I.opts->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
+        AlphaInst a;
+        a.Uh = uh[idx];
+        a.Ft = H->Ft;
+        a.partials = H->partials;
+        a.counter = H->counter;
+        a.aidx = const_cast<int*>(ai[idx]);
+        a.res = I.opts->residuals;
+        a.info = I.opts->info;
+        const double thr = I.opts->tau * I.opts->delta;
+        a.thr2 = thr * thr;
+        a.nplanes = I.Q;
+        a.na = I.opts->n_alpha;
+        a.bstart = g.nalpha_blk;
+        a.nblk = (H->C + kAlphaCPB - 1) / kAlphaCPB;
+        g.nalpha_blk += a.nblk;
+        g.max_na = std::max(g.max_na, a.na);
+        alph.push_back(a);
+      }
+      FusedArgs f;
+      fused_args_f32(H, uh[idx], dd[idx], ai[idx], H->wtab, I.out, I.Q, &f);
+      for (int j = 0; j < H->Mp; ++j) map.push_back(make_int2((int)fa.size(), j));
+      fa.push_back(f);
+    }
+    g.nplanes = (int)planes.size();
+    g.nalpha_inst = (int)alph.size();
+    g.nclusters = (int)map.size();
+    g.off_planes = put(planes.data(), planes.size() * sizeof(PlanePtr));
+    g.off_alpha = alph.empty() ? 0 : put(alph.data(), alph.size() * sizeof(AlphaInst));
+    g.off_fused = put(fa.data(), fa.size() * sizeof(FusedArgs));
+    g.off_map = put(map.data(), map.size() * sizeof(int2));
+    b.groups.push_back(g);
+  }
+  FR3D_CUDA_TRY(cudaMalloc(&b.dev, al(host.size())));
+  {
+    cudaError_t e = cudaMemcpyAsync(b.dev, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaFree(b.dev);
+      return FR3D_ERR_CUDA;
+    }
+  }
+  b.launches = 0;
+  for (const auto& g : b.groups) b.launches += 3 + (g.nalpha_inst > 0 ? 1 : 0);
+  fr3d_batch* h = new (std::nothrow) fr3d_batch();
+  if (!h) {
+    cudaFree(b.dev);
+    return FR3D_ERR_OOM;
+  }
+  h->b = std::move(b);
+  *out = h;
+  return FR3D_OK;
+}
+
+extern "C" int fr3d_batch_run(fr3d_batch* h, void* stream) {
+  if (!h) return FR3D_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (const auto& g : h->b.groups) FR3D_TRY(fr3d::run_group(g, h->b.dev, h->b.output, st));
+  return FR3D_OK;
+}
+
+extern "C" int fr3d_batch_launch_count(fr3d_batch* h) { return h ? h->b.launches : -1; }
+
+extern "C" void fr3d_batch_destroy(fr3d_batch* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  cudaFree(h->b.dev);
+  delete h;
+}
+
+extern "C" int fr3d_invert_batched(const fr3d_instance* inst, int n, void* stream) {
+  fr3d_batch* b = nullptr;
+  FR3D_TRY(fr3d_batch_create(inst, n, &b, stream));
+  const int rc = fr3d_batch_run(b, stream);
+  if (rc == FR3D_OK) cudaStreamSynchronize((cudaStream_t)stream);
+  fr3d_batch_destroy(b);
+  return rc;
+}

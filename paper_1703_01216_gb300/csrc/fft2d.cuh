@@ -62,12 +62,28 @@ __device__ __forceinline__ void batched_copy(int tid, LD ld, ST st) {
 }
 
 // ---------------------------------------------------------------- row pass, real -> half spectrum
-// in: planes of TY x n reals (plane stride in_ps); out: [plane][kx][y] complex.
-template <typename T, int N, int TY>
-__global__ void __launch_bounds__(kThreads) k_row_r2c(const T* __restrict__ in, long in_ps,
-                                                     typename cpx<T>::t* __restrict__ out,
-                                                     const typename cpx<T>::t* __restrict__ tw_half,
-                                                     const typename cpx<T>::t* __restrict__ tw_full) {
+// Plane maps: in(p) -> the real n x n plane p, out(p) -> its half spectrum [kx][ky].
+template <typename T> struct StridedPlanes {
+  const T* in;
+  long in_ps;
+  typename cpx<T>::t* out;
+  long out_ps;
+  __device__ const T* src(int p) const { return in + p * in_ps; }
+  __device__ typename cpx<T>::t* dst(int p) const { return out + p * out_ps; }
+};
+struct PlanePtr {            // one entry per plane of a batch of instances
+  const float* in;
+  float2* out;
+};
+struct TablePlanes {
+  const PlanePtr* t;
+  __device__ const float* src(int p) const { return t[p].in; }
+  __device__ float2* dst(int p) const { return t[p].out; }
+};
+
+// in: planes of n x n reals; out: [plane][kx][y] complex.  One CTA transforms TY rows of a plane.
+template <typename T, int N, int TY, class PM>
+__global__ void __launch_bounds__(kThreads) k_row_r2c(PM pm, const typename cpx<T>::t* __restrict__ tw_full) {
   using C = typename cpx<T>::t;
   constexpr int L = N / 2, SS = Smem<C, L>::ss, STS = TY + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -76,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const T* __restrict__ in, 
   C* buf = ptw + passtw_size<L>();
   C* stg = buf + TY * SS;
   const int tid = threadIdx.x, plane = blockIdx.y, y0 = blockIdx.x * TY;
-  const C* src = reinterpret_cast<const C*>(in + plane * in_ps + (long)y0 * N);
+  const C* src = reinterpret_cast<const C*>(pm.src(plane) + (long)y0 * N);
   for (int e = tid; e < N; e += kThreads) tws[e] = __ldg(tw_full + e);
   build_passtw<L, 2, kThreads>(ptw, tw_full, tid);
   batched_copy<TY * L, kThreads, 8>(
@@ -94,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const T* __restrict__ in, 
     stg[k * STS + r] = cadd(E, cmul(tws[k], O));  // X[k] = E[k] + w^k O[k]
   }
   __syncthreads();
-  C* dst = out + (long)plane * (L + 1) * N + y0;
+  C* dst = pm.dst(plane) + y0;
   for (int e = tid; e < TY * (L + 1); e += kThreads) {
     const int k = e / TY, r = e - k * TY;
     dst[(long)k * N + r] = stg[k * STS + r];
@@ -144,6 +160,15 @@ template <typename T> struct ColPlain {
   __device__ const C* src(int p) const { return in + p * ps; }
   __device__ C* dst(int p) const { return out + p * ps; }
   __device__ C load(int, int, int, C v) const { return v; }
+};
+
+// forward column pass over a table of planes (batched instances), in place
+struct ColTable {
+  const PlanePtr* t;
+  __device__ void begin(int) {}
+  __device__ const float2* src(int p) const { return t[p].out; }
+  __device__ float2* dst(int p) const { return t[p].out; }
+  __device__ float2 load(int, int, int, float2 v) const { return v; }
 };
 
 // Solve for M = 1 fused into the inverse column pass (Eq. (6) with a single observation depth):

@@ -86,8 +86,7 @@ struct FusedArgs {
 };
 
 template <int N, int MODE>
-__global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
-    k_inv_fused(FusedArgs a) {
+__device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   using G = FusedGeom<N>;
   constexpr int CL = G::CL, NT = G::NT, RB = G::RB, L = G::L;
   constexpr int CPC = G::CPC, NRW = G::NRW, NB = G::NB, SSC = G::SSC, SSR = G::SSR, EPT = G::EPT;
@@ -105,7 +104,6 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
   const int tid = threadIdx.x;
   int r = 0;
   if constexpr (CL > 1) r = (int)cg::this_cluster().block_rank();
-  const int jl = blockIdx.x / CL;
   const int j = a.j0 + jl;
   const int c0 = r * CPC;
   const int y0 = r * NRW;
@@ -258,22 +256,19 @@ __global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedC
   }
 }
 
-// W_q = V0_q / sum_q' V0_q'^2 on the R grid (Algorithm 1 step 4 for several source parameters),
-// in FP64, stored as FP32; depends only on the geometry and the sources
-__global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, double x0, double y0, double h,
-                       const double* __restrict__ zr) {
-  const long plane = (long)n * n, total = (long)Mp * plane;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / plane);
-    const long pix = idx % plane;
-    const double x = x0 + ((double)(pix % n) + 0.5) * h, y = y0 + ((double)(pix / n) + 0.5) * h;
-    double s = 0.0;
-    for (int q = 0; q < Q; ++q) {
-      const double v = v0_at(src, q, x, y, zr[j]);
-      s += v * v;
-    }
-    for (int q = 0; q < Q; ++q) W[(long)q * total + idx] = (float)(v0_at(src, q, x, y, zr[j]) / s);
-  }
+template <int N, int MODE>
+__global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
+    k_inv_fused(FusedArgs a) {
+  inv_fused_body<N, MODE>(a, (int)blockIdx.x / FusedCfg<N>::CL);
+}
+
+// Batched instances of one grid size n: cluster c handles depth map[c].y of instance map[c].x.
+template <int N, int MODE>
+__global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
+    k_inv_fused_batched(const FusedArgs* __restrict__ inst, const int2* __restrict__ map) {
+  const int2 m = map[blockIdx.x / FusedCfg<N>::CL];
+  const FusedArgs a = inst[m.x];
+  inv_fused_body<N, MODE>(a, m.y);
 }
 
 }  // namespace fr3d

@@ -4,6 +4,24 @@
 
 namespace fr3d {
 
+// W_q = V0_q / sum_q' V0_q'^2 on the R grid (Algorithm 1 step 4 for several source parameters),
+// in FP64, stored as FP32; depends only on the geometry and the sources
+__global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, double x0, double y0, double h,
+                       const double* __restrict__ zr) {
+  const long plane = (long)n * n, total = (long)Mp * plane;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / plane);
+    const long pix = idx % plane;
+    const double x = x0 + ((double)(pix % n) + 0.5) * h, y = y0 + ((double)(pix / n) + 0.5) * h;
+    double s = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      const double v = v0_at(src, q, x, y, zr[j]);
+      s += v * v;
+    }
+    for (int q = 0; q < Q; ++q) W[(long)q * total + idx] = (float)(v0_at(src, q, x, y, zr[j]) / s);
+  }
+}
+
 namespace {
 
 template <int N, int MODE>
@@ -47,6 +65,43 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
 #undef X
   }
   return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+namespace {
+template <int N, int MODE>
+int launch_fused_batched(const FusedArgs* inst, const int2* map, int nclusters, cudaStream_t st) {
+  using G = FusedGeom<N>;
+  auto kern = k_inv_fused_batched<N, MODE>;
+  constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;
+  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(kern), sm));
+  kern<<<nclusters * G::CL, G::NT, sm, st>>>(inst, map);
+  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+}
+}  // namespace
+
+int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st) {
+  const bool xi = output == FR3D_OUT_XI;
+  switch (n) {
+#define X(N) \
+  case N: return xi ? launch_fused_batched<N, 1>(inst, map, nclusters, st) : launch_fused_batched<N, 0>(inst, map, nclusters, st);
+    X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
+#undef X
+  }
+  return FR3D_ERR_UNSUPPORTED_SIZE;
+}
+
+void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
+                    int Q, FusedArgs* a) {
+  a->Uh = Uh;
+  a->A = H->A32;
+  a->Dd = Dd;
+  a->aidx = aidx;
+  a->W = W;
+  a->out = out;
+  a->tw_n = H->tw32 + twiddle_offset(H, H->n);
+  a->Q = Q;
+  a->j0 = 0;
+  a->Mp = H->Mp;
 }
 
 int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st) {

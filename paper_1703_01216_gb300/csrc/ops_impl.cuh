@@ -22,22 +22,23 @@ template <typename T> static const typename cpx<T>::t* tw_of(const Handle* H, in
 
 constexpr int kSmallGrid = 2 * 152;  // below this many CTAs with the large tile, use the small one
 
-template <typename T, int N, int TY>
-static int row_r2c_t(const Handle* H, const T* in, long in_ps, typename cpx<T>::t* out, int nplanes, cudaStream_t st) {
+template <typename T, int N, int TY, class PM = StridedPlanes<T>>
+static int row_r2c_t(const Handle* H, const PM& pm, int nplanes, cudaStream_t st) {
   constexpr size_t sm = row_r2c_smem<T, N, TY>();
-  auto kern = k_row_r2c<T, N, TY>;
+  auto kern = k_row_r2c<T, N, TY, PM>;
   FR3D_TRY(set_smem(kern, sm));
   dim3 grid(N / TY, nplanes);
-  kern<<<grid, kThreads, sm, st>>>(in, in_ps, out, tw_of<T>(H, N / 2), tw_of<T>(H, N));
+  kern<<<grid, kThreads, sm, st>>>(pm, tw_of<T>(H, N));
   return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
 }
 
 template <typename T, int N>
 static int row_r2c_n(const Handle* H, const T* in, long in_ps, typename cpx<T>::t* out, int nplanes, cudaStream_t st) {
   constexpr int TY = RowTile<T, N>::v;
+  const StridedPlanes<T> pm{in, in_ps, out, (long)(N / 2 + 1) * N};
   if ((long)nplanes * (N / TY) < kSmallGrid && SmallTile<N>::row < TY)
-    return row_r2c_t<T, N, SmallTile<N>::row>(H, in, in_ps, out, nplanes, st);
-  return row_r2c_t<T, N, TY>(H, in, in_ps, out, nplanes, st);
+    return row_r2c_t<T, N, SmallTile<N>::row>(H, pm, nplanes, st);
+  return row_r2c_t<T, N, TY>(H, pm, nplanes, st);
 }
 
 template <typename T, int N, bool INV, class Op, int TC>
@@ -236,17 +237,17 @@ constexpr int kAlphaSplit = 4; // threads per class in the power gather
 // the kx = 0 and kx = n/2 columns and 2 elsewhere (their mirror bins are not stored), summed over
 // planes.  Deterministic: fixed-order partial sums per block, reduced by the last block to finish.
 template <typename C>
-__global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
-                                                      const double* __restrict__ Ft, int na, double thr2, double inv_n2,
-                                                      double* __restrict__ partials, unsigned* __restrict__ counter,
-                                                      int* __restrict__ aidx, double* __restrict__ res_out,
-                                                      int* __restrict__ info) {
+__device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
+                                                  const double* __restrict__ Ft, int na, double thr2, double inv_n2,
+                                                  double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                  int* __restrict__ aidx, double* __restrict__ res_out,
+                                                  int* __restrict__ info, int blk, int nblk) {
   __shared__ double sP[kAlphaCPB];
   __shared__ double red[256];
   __shared__ bool last;
   extern __shared__ double sF[];             // [kAlphaCPB][na] slab of Ft for this block's classes
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * kAlphaCPB;
+  const int c0 = blk * kAlphaCPB;
   const int nF = min(kAlphaCPB, Cn - c0) * na;
   const double* slab = Ft + (long)c0 * na;
   // one round of global loads: this thread's share of the class powers and of the filter slab
@@ -312,11 +313,11 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
   if (tid < na) {
     double s = 0.0;
     for (int sb = 0; sb < S; ++sb) s += red[sb * na + tid];
-    partials[(long)blockIdx.x * na + tid] = s;
+    partials[(long)blk * na + tid] = s;
   }
   __threadfence();
   __syncthreads();
-  if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  if (tid == 0) last = atomicAdd(counter, 1u) == (unsigned)(nblk - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -326,12 +327,12 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
   if (tid < S * na) {
     const int k = tid % na, sb = tid / na;
     double s = 0.0;
-    for (int b0 = sb; b0 < (int)gridDim.x; b0 += 16 * S) {
+    for (int b0 = sb; b0 < nblk; b0 += 16 * S) {
       double v[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int b = b0 + i * S;
-        v[i] = b < (int)gridDim.x ? __ldcg(partials + (long)b * na + k) : 0.0;
+        v[i] = b < nblk ? __ldcg(partials + (long)b * na + k) : 0.0;
       }
 #pragma unroll
       for (int i = 0; i < 16; ++i) s += v[i];
@@ -365,6 +366,16 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
     if (info) *info = flags;
     *counter = 0u;
   }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
+                                                      const double* __restrict__ Ft, int na, double thr2, double inv_n2,
+                                                      double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                      int* __restrict__ aidx, double* __restrict__ res_out,
+                                                      int* __restrict__ info) {
+  alpha_choose_body(Uh, ps, nplanes, n, Cn, Ft, na, thr2, inv_n2, partials, counter, aidx, res_out, info,
+                    (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <typename T>

@@ -45,6 +45,11 @@ class InvertOpts(ct.Structure):
                 ("info", ct.c_void_p)]
 
 
+class Instance(ct.Structure):
+    _fields_ = [("handle", ct.c_void_p), ("U", ct.c_void_p), ("Q", ct.c_int), ("opts", ct.POINTER(InvertOpts)),
+                ("out", ct.c_void_p)]
+
+
 class Fr3dError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {status_string(status)} (status {status})")
@@ -57,7 +62,9 @@ _lib = None
 EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", "fr3d_fwd_apply",
            "fr3d_fwd_apply_noalloc",
            "fr3d_zeta_from_xi", "fr3d_choose_alpha", "fr3d_invert", "fr3d_invert_host",
-           "fr3d_last_launch_count", "fr3d_profile_enable", "fr3d_profile_read", "fr3d_status_string")
+           "fr3d_last_launch_count", "fr3d_profile_enable", "fr3d_profile_read", "fr3d_status_string",
+           "fr3d_batch_create", "fr3d_batch_run", "fr3d_batch_launch_count", "fr3d_batch_destroy",
+           "fr3d_invert_batched")
 
 
 def load(path: str | None = None):
@@ -83,10 +90,16 @@ def load(path: str | None = None):
     lib.fr3d_last_launch_count.argtypes = [vp]
     lib.fr3d_profile_enable.argtypes = [vp, i]
     lib.fr3d_profile_read.argtypes = [vp, ct.POINTER(i), ct.POINTER(ct.c_float), i]
+    lib.fr3d_batch_create.argtypes = [ct.POINTER(Instance), i, ct.POINTER(vp), vp]
+    lib.fr3d_batch_run.argtypes = [vp, vp]
+    lib.fr3d_batch_launch_count.argtypes = [vp]
+    lib.fr3d_batch_destroy.argtypes = [vp]
+    lib.fr3d_batch_destroy.restype = None
+    lib.fr3d_invert_batched.argtypes = [ct.POINTER(Instance), i, vp]
     lib.fr3d_status_string.argtypes = [i]
     lib.fr3d_status_string.restype = ct.c_char_p
     for name in EXPORTS:
-        if name not in ("fr3d_handle_destroy", "fr3d_status_string"):
+        if name not in ("fr3d_handle_destroy", "fr3d_status_string", "fr3d_batch_destroy"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -247,3 +260,39 @@ def profile_read(handle: Handle, cap: int = 96):
     ms = (ct.c_float * cap)()
     n = _check(load().fr3d_profile_read(handle.ptr, kinds, ms, cap), "fr3d_profile_read")
     return [(STAGE_NAMES[kinds[i]], float(ms[i])) for i in range(n)]
+
+
+class Batch:
+    """A batch plan over independent instances (fr3d_batch_create ... fr3d_batch_destroy).
+
+    ``items`` is a list of (Handle, U tensor, Q, Opts, out tensor); their device buffers and options
+    must stay alive and unchanged while the plan exists."""
+
+    def __init__(self, items, stream=None):
+        lib = load()
+        self._items = items
+        arr = (Instance * len(items))()
+        for k, (h, U, Q, opts, out) in enumerate(items):
+            arr[k] = Instance(h.ptr.value, U.data_ptr(), int(Q), ct.pointer(opts.c), out.data_ptr())
+        self._arr = arr
+        bp = ct.c_void_p()
+        _check(lib.fr3d_batch_create(arr, len(items), ct.byref(bp), _stream(stream)), "fr3d_batch_create")
+        self.ptr = bp
+
+    def run(self, stream=None):
+        _check(load().fr3d_batch_run(self.ptr, _stream(stream)), "fr3d_batch_run")
+
+    @property
+    def launches(self) -> int:
+        return int(load().fr3d_batch_launch_count(self.ptr))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().fr3d_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

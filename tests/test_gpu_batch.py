@@ -1,0 +1,96 @@
+"""Batched uneven instances (one plan, four launches per grid size) against per-instance calls and
+the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1703_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1703_01216_gb300 import build, fr3d
+    assert torch.cuda.is_available()
+    build.build()
+    fr3d.load()
+    return fr3d
+
+
+def _instances(F, shapes, seed):
+    items, refs, ws = [], [], []
+    for k, (n, mp, q) in enumerate(shapes):
+        w = I.make_workload(n, mp, q=q, n_incl=3, noise_level=0.01 + 0.005 * k, n_alpha=12, seed=seed + k)
+        zeta = O.zeta_from_xi(w.xi_true, w.sources, w.n, w.x0, w.h, w.zr)
+        U = O.forward_dft(zeta, w.n, w.h, w.zy, w.zr, w.nu)
+        nz = w.noise * (w.noise_level * np.linalg.norm(U) / np.linalg.norm(w.noise))
+        U = U + nz
+        H = F.kernel_transform(w.n, w.x0, w.h, w.zr, w.zy, w.nu)
+        Ud = torch.as_tensor(U, dtype=torch.float32, device="cuda")
+        idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+        opts = F.Opts(alphas=w.alphas, delta=float(np.linalg.norm(nz)), tau=1.1, points=w.sources, alpha_idx=idx)
+        out = torch.full((w.Mp, w.n, w.n), float("nan"), device="cuda")
+        items.append((H, Ud, w.Q, opts, out))
+        ws.append((w, U, float(np.linalg.norm(nz)), idx))
+    return items, ws
+
+
+SHAPES = [(32, 8, 2), (64, 5, 1), (48, 6, 3), (64, 12, 2), (96, 4, 1), (128, 3, 2), (32, 4, 1)]
+
+
+def test_batch_matches_single_calls_and_oracle(F):
+    items, ws = _instances(F, SHAPES, 700)
+    singles = []
+    for (H, Ud, Q, opts, out), (w, U, d, idx) in zip(items, ws):
+        o = torch.empty_like(out)
+        F.invert(H, Ud, Q, o, opts)
+        singles.append((o.clone(), int(idx.item())))
+    B = F.Batch(items)
+    assert B.launches == 4 * 5            # 5 grid sizes, 4 launches each
+    for (H, Ud, Q, opts, out) in items:
+        out.fill_(float("nan"))
+    B.run()
+    torch.cuda.synchronize()
+    for k, ((H, Ud, Q, opts, out), (w, U, d, idx), (o, k1)) in enumerate(zip(items, ws, singles)):
+        assert int(idx.item()) == k1
+        assert torch.equal(out, o), k                    # same kernels, same arithmetic
+    # one instance against the oracle end to end
+    w, U, d, idx = ws[3]
+    ref = O.invert(U, w.n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=d, tau=1.1, sources=w.sources)
+    got = items[3][4].double().cpu().numpy()
+    if ref["alpha_index"] == int(idx.item()):
+        assert np.linalg.norm(got - ref["xi"]) <= 1e-4 * np.linalg.norm(ref["xi"])
+    B.close()
+
+
+def test_batch_plan_replays_in_a_cuda_graph(F):
+    items, ws = _instances(F, SHAPES[:4], 800)
+    B = F.Batch(items)
+    B.run()
+    torch.cuda.synchronize()
+    ref = [it[4].clone() for it in items]
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            B.run()
+    torch.cuda.current_stream().wait_stream(s)
+    for it in items:
+        it[4].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for it, r in zip(items, ref):
+        assert torch.equal(it[4], r)
+    B.close()
+
+
+def test_batch_rejects_shared_handles(F):
+    items, ws = _instances(F, SHAPES[:2], 900)
+    H, Ud, Q, opts, out = items[0]
+    dup = [items[0], (H, items[1][1], items[1][2], items[1][3], items[1][4])]
+    with pytest.raises(F.Fr3dError):
+        F.Batch(dup)
