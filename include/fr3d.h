@@ -70,10 +70,12 @@ extern "C" {
 #define FR3D_PREC_FP64 1  /* FP64 throughout; data and outputs are double */
 #define FR3D_ALPHA_FIXED 0
 #define FR3D_ALPHA_DISCREPANCY 1
+#define FR3D_ALPHA_GIVEN 2        /* per-band indices into `alphas` supplied in alpha_idx (no sweep) */
 #define FR3D_OUT_ZETA 0   /* output zeta_q per source parameter: [Q][M'][n][n] */
 #define FR3D_OUT_XI 1     /* output xi (Algorithm 1 step 4): [M'][n][n] */
 
 #define FR3D_MAX_ALPHAS 128
+#define FR3D_MAX_BANDS 16
 #define FR3D_MAX_SOURCE_POINTS 256 /* total points over all source parameters q */
 
 /* Flat-layer geometry (Sec. 3: R = R^2 x [h, H], Y = R^2 x [h_Y, H_Y]; Sec. 5 grids). */
@@ -111,9 +113,16 @@ typedef struct fr3d_invert_opts {
   int output;              /* FR3D_OUT_ZETA or FR3D_OUT_XI */
   int precision;           /* FR3D_PREC_FP32 or FR3D_PREC_FP64 */
   const fr3d_sources* sources; /* required for FR3D_OUT_XI (sources->q == Q) */
-  int* alpha_idx;          /* device int[1] or NULL: index of the chosen alpha (0 for FIXED) */
-  double* residuals;       /* device double[n_alpha] or NULL: squared residuals ||A zeta_alpha - U||^2 */
+  int* alpha_idx;          /* device int[max(1, n_bands)] or NULL: index of the chosen alpha per band
+                              (0 for FIXED); for GIVEN it is the input (required) */
+  double* residuals;       /* device double[max(1, n_bands)][n_alpha] or NULL: squared residuals
+                              ||A zeta_alpha - U||^2 restricted to each band */
   int* info;               /* device int[1] or NULL: FR3D_INFO_* bits of this call (overwritten) */
+  int n_bands;             /* 0 or 1: one alpha for the whole spectrum (the paper's global rule);
+                              2..FR3D_MAX_BANDS: radial bands of |k| (band b holds the frequencies with
+                              b <= n_bands |k| / (sqrt(2) n/2) < b + 1), each with its own alpha; the
+                              discrepancy bound of band b is tau delta sqrt(frequencies in b / n^2)
+                              (white noise).  DISCREPANCY and GIVEN only, M = 1. */
 } fr3d_invert_opts;
 
 /* Step 1 for the kernel (Algorithm 1, Sec. 5): samples K at the periodic lags for every

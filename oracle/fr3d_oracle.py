@@ -42,7 +42,7 @@ import numpy as np
 __all__ = [
     "kernel_K", "wrapped_lags", "kernel_samples", "dft_matrix", "dft2", "idft2",
     "kernel_hat", "A_matrices", "alpha_scale", "forward_direct", "forward_dft",
-    "tikhonov_qr", "residual_sq", "choose_alpha_index", "V0", "zeta_from_xi",
+    "tikhonov_qr", "residual_sq", "radial_bands", "choose_alpha_index", "V0", "zeta_from_xi",
     "combine_sources", "invert", "A0_of", "A2_of",
 ]
 
@@ -217,6 +217,17 @@ def residual_sq(A: np.ndarray, Zh: np.ndarray, Uh: np.ndarray, n_freq: int | Non
     return float(np.sum(np.abs(r) ** 2) / (A.shape[0] if n_freq is None else n_freq))
 
 
+def radial_bands(L: int, n_bands: int) -> np.ndarray:
+    """Band of every frequency of the L x L DFT grid, flattened [ky, kx]: with the folded indices
+    k' = min(k, L - k) per axis, band = floor(n_bands |k'| / (sqrt(2) L/2)), clamped to n_bands - 1
+    (a reading: the paper only says step 2 is done per frequency; bands group frequencies by |w|)."""
+    k = np.arange(L)
+    kf = np.minimum(k, L - k)
+    rho = np.sqrt(kf[None, :] ** 2 + kf[:, None] ** 2)
+    b = np.floor(n_bands * rho / (np.sqrt(2.0) * (L // 2))).astype(int)
+    return np.minimum(b, n_bands - 1).ravel()
+
+
 def choose_alpha_index(res2, delta: float, tau: float):
     """Discrepancy principle (Sec. 4): the largest alpha_k whose residual is <= tau * delta.
 
@@ -291,7 +302,7 @@ def combine_sources(zeta: np.ndarray, sources: np.ndarray, n: int, x0: float, h:
 # --------------------------------------------------------------------------- Algorithm 1
 def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int = 1,
            alpha=None, alphas=None, delta=None, tau: float = 1.1, sources=None, A0: float = 1.0,
-           output: str = "xi", chunk: int = 4096, bins=None, A=None):
+           output: str = "xi", chunk: int = 4096, bins=None, A=None, n_bands: int = 1, band_alpha_index=None):
     """Algorithm 1 (Sec. 4) in its finite-dimensional form (Sec. 5).
 
     U: [Q, M, n, n] data for Q source parameters.
@@ -308,6 +319,11 @@ def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int =
     ``output="none"`` stops after step 2.  ``bins`` (optional) restricts step 2 to a subset of
     the flattened frequencies; every other frequency gets the zero solution, which is exact when
     the data spectrum vanishes there (a zero right-hand side has the zero Tikhonov solution).
+    ``n_bands`` > 1 applies the discrepancy principle per radial band of frequencies (see
+    radial_bands): band b gets its own alpha, the largest with residual_b <= tau delta_b, where
+    delta_b^2 = delta^2 (frequencies in b) / L^2 (the share of white noise in the band); ``res2``
+    is then [n_bands, n_alpha] and ``alpha_index`` a list.  ``band_alpha_index`` (with
+    ``alphas``) imposes the per-band indices instead of choosing them.
     """
     zy = np.atleast_1d(np.asarray(zy, np.float64))
     zr = np.atleast_1d(np.asarray(zr, np.float64))
@@ -335,11 +351,33 @@ def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int =
     if alpha is not None:
         k = -1
         Zs = solve(float(alpha))
-    else:
+    elif n_bands <= 1 and band_alpha_index is None:
         alphas = np.asarray(alphas, np.float64)
         res2 = np.array([residual_sq(Af[sel], solve(float(a)), Uf[sel], L * L) for a in alphas])
         k, flag = choose_alpha_index(res2, float(delta), tau)
         Zs = solve(float(alphas[k]))
+    else:
+        alphas = np.asarray(alphas, np.float64)
+        nb = max(int(n_bands), 1)
+        band = radial_bands(L, nb)[sel]
+        if band_alpha_index is None:
+            res2 = np.zeros((nb, alphas.size))
+            for t, a in enumerate(alphas):
+                r = np.sum(np.abs(Af[sel] @ solve(float(a)) - Uf[sel]) ** 2, axis=(1, 2)) / (L * L)
+                res2[:, t] = np.bincount(band, weights=r, minlength=nb)
+            count = np.bincount(radial_bands(L, nb), minlength=nb)
+            k, flag = [], 0
+            for b in range(nb):
+                kb, fb = choose_alpha_index(res2[b], float(delta) * np.sqrt(count[b] / (L * L)), tau)
+                k.append(kb)
+                flag |= fb
+        else:
+            k = [int(v) for v in band_alpha_index]
+        Zs = np.empty((sel.size, Mp, Q), np.complex128)
+        for kb in sorted(set(k)):
+            use = np.isin(band, [b for b in range(nb) if k[b] == kb])
+            full = solve(float(alphas[kb]))
+            Zs[use] = full[use]
     out = {"alpha_index": k, "flag": flag, "res2": res2, "s2": s2}
     if output == "none":
         return out

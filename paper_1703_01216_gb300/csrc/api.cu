@@ -10,6 +10,18 @@
 
 namespace fr3d {
 
+// (tau delta_b)^2 per band: the noise energy of a band is delta^2 times its share of the frequencies
+// (white noise), so delta_b^2 = delta^2 (frequencies in band b) / n^2
+void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double* thr2) {
+  const double t2 = (o->tau * o->delta) * (o->tau * o->delta);
+  if (nb == 1) {
+    thr2[0] = t2;
+    return;
+  }
+  const double n2 = (double)H->n * H->n;
+  for (int b = 0; b < nb; ++b) thr2[b] = t2 * H->band_count[b] / n2;
+}
+
 namespace {
 
 constexpr double kFourPi = 12.566370614359172953850573533118;
@@ -129,8 +141,8 @@ int choose_impl(Handle* H, const T* U, int Q, const double* alphas, int n_alpha,
   C* Uh = reinterpret_cast<C*>(H->ws);
   FR3D_TRY(data_fft<T>(H, U, Q, Uh, st));
   FR3D_TRY(alpha_tables(H, alphas, n_alpha, st));
-  const double thr = tau * delta;
-  FR3D_TRY(Ops<T>::alpha_choose(H, Uh, Q * H->M, n_alpha, thr * thr, alpha_idx, residuals, info, st));
+  const double thr2 = (tau * delta) * (tau * delta);
+  FR3D_TRY(Ops<T>::alpha_choose(H, Uh, Q * H->M, n_alpha, &thr2, 1, alpha_idx, residuals, info, st));
   H->last_launches = 3;
   return FR3D_OK;
 }
@@ -186,11 +198,16 @@ int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
   if (!valid_precision(o->precision)) return FR3D_ERR_INVALID_ARG;
   if (H->M != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
   if (o->output != FR3D_OUT_XI && o->output != FR3D_OUT_ZETA) return FR3D_ERR_INVALID_ARG;
+  if (o->n_bands < 0 || o->n_bands > FR3D_MAX_BANDS) return FR3D_ERR_INVALID_ARG;
   if (o->alpha_mode == FR3D_ALPHA_FIXED) {
     if (!(o->alpha > 0) || !isfinite(o->alpha)) return FR3D_ERR_INVALID_ARG;
+    if (o->n_bands > 1) return FR3D_ERR_INVALID_ARG;
   } else if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
     FR3D_TRY(check_alphas(o->alphas, o->n_alpha));
     if (!(o->delta >= 0) || !isfinite(o->delta) || !(o->tau > 0) || !isfinite(o->tau)) return FR3D_ERR_INVALID_ARG;
+  } else if (o->alpha_mode == FR3D_ALPHA_GIVEN) {
+    FR3D_TRY(check_alphas(o->alphas, o->n_alpha));
+    if (!o->alpha_idx) return FR3D_ERR_INVALID_ARG;
   } else {
     return FR3D_ERR_INVALID_ARG;
   }
@@ -216,17 +233,27 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
   // step 2 (parameter): alpha
   const int* aidx;
   const T* D;
+  const int nb = o->n_bands > 1 ? o->n_bands : 1;
+  if (nb > 1) FR3D_TRY(ensure_bands(H, nb, nullptr));
   if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
     FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
     prof_mark(H, kStTable, st);
     int* idx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
-    const double thr = o->tau * o->delta;
-    FR3D_TRY(Ops<T>::alpha_choose(H, Uh, Q * H->M, o->n_alpha, thr * thr, idx, o->residuals, o->info, st));
+    double thr2[FR3D_MAX_BANDS];
+    band_thresholds(H, o, nb, thr2);
+    FR3D_TRY(Ops<T>::alpha_choose(H, Uh, Q * H->M, o->n_alpha, thr2, nb, idx, o->residuals, o->info, st));
     prof_mark(H, kStAlpha, st);
     launches += 1;
     aidx = idx;
     if constexpr (sizeof(T) == 4) D = H->D32;
     else D = H->D64;
+  } else if (o->alpha_mode == FR3D_ALPHA_GIVEN) {
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    prof_mark(H, kStTable, st);
+    aidx = o->alpha_idx;
+    if constexpr (sizeof(T) == 4) D = H->D32;
+    else D = H->D64;
+    if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
   } else {
     FR3D_TRY(fixed_table(H, o->alpha, st));
     prof_mark(H, kStTable, st);
@@ -243,8 +270,8 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
         FR3D_TRY(ensure_wtab(H, o->sources, st));
         prof_mark(H, kStTable, st);
       }
-      const float* Dd = o->alpha_mode == FR3D_ALPHA_DISCREPANCY ? H->Dd32 : H->Ddfix32;
-      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, H->wtab, out, Q, 0, H->Mp, o->output, st));
+      const float* Dd = o->alpha_mode == FR3D_ALPHA_FIXED ? H->Ddfix32 : H->Dd32;
+      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, nb, H->wtab, out, Q, 0, H->Mp, o->output, st));
       prof_mark(H, kStFused, st);
       H->last_launches = launches + 1;
       return FR3D_OK;
@@ -259,7 +286,7 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
   // step 2 (solve) + step 3 (inverse DFT) + step 4 (xi = zeta / V0), by chunks of depths
   for (int j0 = 0; j0 < H->Mp; j0 += p.chunk) {
     const int nj = std::min(p.chunk, H->Mp - j0);
-    FR3D_TRY(Ops<T>::col_solve1(H, Uh, Tb, A, D, aidx, Q, j0, nj, st));
+    FR3D_TRY(Ops<T>::col_solve1(H, Uh, Tb, A, D, aidx, nb, Q, j0, nj, st));
     prof_mark(H, kStColSolve, st);
     if (o->output == FR3D_OUT_XI)
       FR3D_TRY(Ops<T>::row_c2r_xi(H, Tb, out, nj, Q, j0, src_host(H, o->precision, o->sources), st));
@@ -284,16 +311,11 @@ int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** U
   FR3D_TRY(ensure_ws(H, p.total));
   *Uh = reinterpret_cast<float2*>((char*)H->ws + p.uh_off);
   if (o->output == FR3D_OUT_XI) FR3D_TRY(ensure_wtab(H, o->sources, st));
-  if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
+  const int nb = o->n_bands > 1 ? o->n_bands : 1;
+  if (nb > 1) FR3D_TRY(ensure_bands(H, nb, nullptr));
+  if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY || o->alpha_mode == FR3D_ALPHA_GIVEN) {
     FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
-    const int blocks = (H->C + 63) / 64;
-    if (H->partial_cap < blocks * FR3D_MAX_ALPHAS) {
-      if (H->partials) cudaFree(H->partials);
-      H->partials = nullptr;
-      H->partial_cap = 0;
-      FR3D_CUDA_TRY(cudaMalloc(&H->partials, sizeof(double) * blocks * FR3D_MAX_ALPHAS));
-      H->partial_cap = blocks * FR3D_MAX_ALPHAS;
-    }
+    FR3D_TRY(ensure_partials(H));
     *Dd = H->Dd32;
     *aidx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
   } else {

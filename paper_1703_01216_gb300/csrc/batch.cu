@@ -19,13 +19,14 @@ namespace fr3d {
 struct AlphaInst {
   const float2* Uh;
   const double* Ft;
+  const unsigned char* cband;
   double* partials;
   unsigned* counter;
   int* aidx;
   double* res;
   int* info;
-  double thr2;
-  int nplanes, na, bstart, nblk;
+  BandThr thr2;
+  int nplanes, na, nb, bstart, nblk;
 };
 
 __global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst, long ps, int n,
@@ -33,13 +34,14 @@ __global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restri
   int i = 0;
   while (i + 1 < ninst && inst[i + 1].bstart <= (int)blockIdx.x) ++i;
   const AlphaInst a = inst[i];
-  alpha_choose_body<float2>(a.Uh, ps, a.nplanes, n, Cn, a.Ft, a.na, a.thr2, inv_n2, a.partials, a.counter, a.aidx,
-                            a.res, a.info, (int)blockIdx.x - a.bstart, a.nblk);
+  alpha_choose_body<float2>(a.Uh, ps, a.nplanes, n, Cn, a.Ft, a.na, a.thr2, a.cband, a.nb, inv_n2, a.partials,
+                            a.counter, a.aidx, a.res, a.info, (int)blockIdx.x - a.bstart, a.nblk);
 }
 
 int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st);
-void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
-                    int Q, FusedArgs* a);
+void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
+                    float* out, int Q, FusedArgs* a);
+void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double* thr2);
 int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** Uh, const float** Dd, const int** aidx,
                          cudaStream_t st);
 
@@ -146,13 +148,14 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
         AlphaInst a;
         a.Uh = uh[idx];
         a.Ft = H->Ft;
+        a.nb = I.opts->n_bands > 1 ? I.opts->n_bands : 1;
+        a.cband = H->cband;
+        band_thresholds(H, I.opts, a.nb, a.thr2.t);
         a.partials = H->partials;
         a.counter = H->counter;
         a.aidx = const_cast<int*>(ai[idx]);
         a.res = I.opts->residuals;
         a.info = I.opts->info;
-        const double thr = I.opts->tau * I.opts->delta;
-        a.thr2 = thr * thr;
         a.nplanes = I.Q;
         a.na = I.opts->n_alpha;
         a.bstart = g.nalpha_blk;
@@ -162,7 +165,7 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
         alph.push_back(a);
       }
       FusedArgs f;
-      fused_args_f32(H, uh[idx], dd[idx], ai[idx], H->wtab, I.out, I.Q, &f);
+      fused_args_f32(H, uh[idx], dd[idx], ai[idx], I.opts->n_bands > 1 ? I.opts->n_bands : 1, H->wtab, I.out, I.Q, &f);
       for (int j = 0; j < H->Mp; ++j) map.push_back(make_int2((int)fa.size(), j));
       fa.push_back(f);
     }

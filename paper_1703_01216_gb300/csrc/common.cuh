@@ -83,8 +83,11 @@ struct Handle {
   int* idx_scratch = nullptr;    // chosen alpha index when the caller passes none
   int* zero_idx = nullptr;       // constant 0
   int* info_scratch = nullptr;
-  double* partials = nullptr;    // [blocks][n_alpha]
+  double* partials = nullptr;    // [blocks][bands][n_alpha]
   int partial_cap = 0;
+  unsigned char* cband = nullptr; // [C] radial band of every class for cband_nb bands
+  int cband_nb = 0;
+  std::vector<double> band_count; // grid frequencies per band (sum of the classes' member weights)
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -107,26 +110,38 @@ struct Launches {
 
 int ensure_ws(Handle* H, size_t bytes);
 
-// Opt a kernel in to `bytes` of dynamic shared memory once per (kernel, device); later calls are a
-// lookup, so launches inside a stream capture make no attribute call.
+// Opt a kernel in to `bytes` of dynamic shared memory (beyond the 48 KB default that static and
+// dynamic shared memory share) once per (kernel, device); later calls are a lookup, so launches
+// inside a stream capture make no attribute call.  Returns an error if bytes exceed the device limit.
 int smem_optin(const void* kernel, size_t bytes);
 
 // stage kinds reported by fr3d_profile_read
 enum StageKind { kStRowR2C = 0, kStColFwd = 1, kStAlpha = 2, kStColSolve = 3, kStRowC2R = 4, kStTable = 5,
                  kStContract = 6, kStColInv = 7, kStOther = 8, kStFused = 9 };
-// cudaEventRecordExternal: inside a stream capture the record becomes a graph node, so a replayed
-// graph records the stage events too
+// Inside a stream capture an event is recorded with cudaEventRecordExternal so that it becomes a
+// graph node and a replayed graph records the stage events too; outside a capture it is a plain
+// record.  A failed record stops the tracing of this call (n_ev = 0) and clears the error.
+inline bool prof_record(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  const cudaError_t r = cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)
+                                                            : cudaEventRecord(e, st);
+  if (r != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
 inline void prof_begin(Handle* H, cudaStream_t st) {
   H->n_ev = 0;
   if (!H->prof_on) return;
-  cudaEventRecordWithFlags(H->ev[0], st, cudaEventRecordExternal);
-  H->n_ev = 1;
+  if (prof_record(H->ev[0], st)) H->n_ev = 1;
 }
 inline void prof_mark(Handle* H, int kind, cudaStream_t st) {
   if (!H->prof_on || H->n_ev <= 0 || H->n_ev >= Handle::kMaxEv) return;
   H->ev_kind[H->n_ev - 1] = kind;
-  cudaEventRecordWithFlags(H->ev[H->n_ev], st, cudaEventRecordExternal);
-  ++H->n_ev;
+  if (prof_record(H->ev[H->n_ev], st)) ++H->n_ev;
+  else H->n_ev = 0;
 }
 int twiddle_offset(const Handle* H, int L);
 

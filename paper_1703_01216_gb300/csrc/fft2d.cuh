@@ -180,16 +180,19 @@ template <typename T> struct ColSolve1 {
   C* out;             // [chunk Q][H1][n]
   const T* A;         // [M' = j][H1][n]
   const T* D;         // [n_alpha][C]
-  const int* aidx;    // chosen row of D
+  const int* aidx;    // chosen row of D per band
+  const unsigned char* cband;  // band of every class (nb > 1)
   long ps;
-  int Q, j0, n, Cn;
+  int Q, j0, n, Cn, nb;
   const T* drow;
   __device__ void begin(int) { drow = D + (long)(*aidx) * Cn; }
   __device__ const C* src(int p) const { return Uh + (p % Q) * ps; }
   __device__ C* dst(int p) const { return out + p * ps; }
   __device__ C load(int p, int kx, int ky, C v) const {
     const int j = j0 + p / Q;
-    const T w = A[(long)j * ps + (long)kx * n + ky] * drow[class_of(kx, ky, n)];
+    const int c = class_of(kx, ky, n);
+    const T d = nb == 1 ? drow[c] : D[(long)aidx[cband[c]] * Cn + c];
+    const T w = A[(long)j * ps + (long)kx * n + ky] * d;
     return cscale(v, w);
   }
 };

@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 
 #include "fft2d.cuh"
+#include "../../include/fr3d.h"
 
 namespace fr3d {
 
@@ -78,7 +79,9 @@ struct FusedArgs {
   const float2* Uh;    // [Q][n/2+1][n] data spectra
   const float* A;      // [M' = j][n/2+1][n] dense kernel table
   const float* Dd;     // [n_alpha][n/2+1][n] dense solve weights
-  const int* aidx;     // chosen row of Dd
+  const int* aidx;     // chosen row of Dd per band
+  const unsigned char* cband;  // band of every frequency class (nb > 1)
+  int nb;              // bands (1: one alpha for the whole spectrum)
   const float* W;      // [Q][M'][n][n] combination weights V0_q / sum_q' V0_q'^2 (XI mode)
   float* out;          // XI: [M'][n][n]; ZETA: [Q][M'][n][n]
   const float2* tw_n;  // length-n twiddles
@@ -110,9 +113,18 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   const long ps = (long)(L + 1) * N;
 
   // ---------------- set-up: twiddles and the q-invariant solve weights of the owned columns
+  __shared__ int s_aidx[FR3D_MAX_BANDS];
+  if (tid < a.nb) s_aidx[tid] = a.aidx[tid];
+  __syncthreads();
   {
     const float* Aj = a.A + (long)j * ps;
-    const float* drow = a.Dd + (long)(*a.aidx) * ps;
+    const float* drow = a.Dd + (long)s_aidx[0] * ps;
+    // solve weight of bin o = kx n + ky: the row of its band's alpha
+    auto dval = [&](long o) -> float {
+      if (a.nb == 1) return __ldg(drow + o);
+      const int kx = (int)(o / N), ky = (int)(o % N);
+      return __ldg(a.Dd + (long)s_aidx[a.cband[class_of(kx, ky, N)]] * ps + o);
+    };
     for (int e = tid; e < N; e += NT) tws[e] = __ldg(a.tw_n + e);
     build_passtw<N, 1, NT>(ptc, a.tw_n, tid);
     build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
@@ -123,13 +135,13 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
       for (int i = 0; i < CB; ++i) {
         const long o = (long)c0 * N + tid + (b0 + i) * NT;   // columns c0.. are contiguous
         wa[i] = __ldg(Aj + o);
-        wd[i] = __ldg(drow + o);
+        wd[i] = dval(o);
       }
 #pragma unroll
       for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = wa[i] * wd[i];
     }
     if (r == 0)
-      for (int e = tid; e < N; e += NT) wsm[CPC * N + e] = __ldg(Aj + (long)L * N + e) * __ldg(drow + (long)L * N + e);
+      for (int e = tid; e < N; e += NT) wsm[CPC * N + e] = __ldg(Aj + (long)L * N + e) * dval((long)L * N + e);
   }
   __syncthreads();
 

@@ -44,13 +44,15 @@ bool fused_supported(int n) {
   return false;
 }
 
-int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
-                  int Q, int j0, int nj, int output, cudaStream_t st) {
+int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
+                  float* out, int Q, int j0, int nj, int output, cudaStream_t st) {
   FusedArgs a;
   a.Uh = Uh;
   a.A = H->A32;
   a.Dd = Dd;
   a.aidx = aidx;
+  a.cband = H->cband;
+  a.nb = nb;
   a.W = W;
   a.out = out;
   a.tw_n = H->tw32 + twiddle_offset(H, H->n);
@@ -90,12 +92,14 @@ int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int ncl
   return FR3D_ERR_UNSUPPORTED_SIZE;
 }
 
-void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
-                    int Q, FusedArgs* a) {
+void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
+                    float* out, int Q, FusedArgs* a) {
   a->Uh = Uh;
   a->A = H->A32;
   a->Dd = Dd;
   a->aidx = aidx;
+  a->cband = H->cband;
+  a->nb = nb;
   a->W = W;
   a->out = out;
   a->tw_n = H->tw32 + twiddle_offset(H, H->n);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -21,8 +22,8 @@ template <typename T> struct Ops {
   // column pass in place/out of place, plain
   static int col_plain(const Handle* H, const C* in, C* out, int nplanes, bool inverse, cudaStream_t st);
   // inverse column pass with the M = 1 Tikhonov weights; output planes jc * Q + q, jc < nj
-  static int col_solve1(const Handle* H, const C* Uh, C* out, const T* A, const T* D, const int* aidx, int Q,
-                        int j0, int nj, cudaStream_t st);
+  static int col_solve1(const Handle* H, const C* Uh, C* out, const T* A, const T* D, const int* aidx, int nb,
+                        int Q, int j0, int nj, cudaStream_t st);
   // row pass half spectrum -> real; input plane ip -> output plane (ip % Q) * out_stride + j0 + ip / Q
   static int row_c2r_plain(const Handle* H, const C* in, T* out, int nplanes, int Q, int j0, int out_stride,
                            cudaStream_t st);
@@ -33,17 +34,23 @@ template <typename T> struct Ops {
   static int contract_fwd(const Handle* H, const C* Zh, C* Uh, const T* A, int Q, cudaStream_t st);
   // zeta[q][j] = xi[j] * V0_q
   static int zeta_from_xi(const Handle* H, const T* xi, T* zeta, int Q, const SrcHost& src, cudaStream_t st);
-  // discrepancy choice over the cached alpha tables (M = 1)
-  static int alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, double thr2, int* aidx,
+  // discrepancy choice over the cached alpha tables (M = 1), per band (nb = 1: whole spectrum);
+  // thr2[b] = (tau delta_b)^2
+  static int alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, const double* thr2, int nb, int* aidx,
                           double* residuals, int* info, cudaStream_t st);
 };
 
 // fused inverse (FP32, M = 1): solve + inverse 2D DFT + combination for depths j0 .. j0 + nj - 1
 bool fused_supported(int n);
-int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, const float* W, float* out,
-                  int Q, int j0, int nj, int output, cudaStream_t st);
+int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
+                  float* out, int Q, int j0, int nj, int output, cudaStream_t st);
 // W_q = V0_q / sum_q' V0_q'^2 on the R grid for the handle's cached sources
 int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st);
+
+// alpha-rule partial sums buffer (per block, band and candidate)
+int ensure_partials(Handle* H);
+// band of every frequency class for nb radial bands, and the number of grid frequencies per band
+int ensure_bands(Handle* H, int nb, std::vector<double>* count);
 
 // precision-independent table builders (alpha tables, fixed alpha)
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st);

@@ -103,9 +103,11 @@ int Ops<T>::col_plain(const Handle* H, const C* in, C* out, int nplanes, bool in
 }
 
 template <typename T>
-int Ops<T>::col_solve1(const Handle* H, const C* Uh, C* out, const T* A, const T* D, const int* aidx, int Q, int j0,
-                       int nj, cudaStream_t st) {
+int Ops<T>::col_solve1(const Handle* H, const C* Uh, C* out, const T* A, const T* D, const int* aidx, int nb, int Q,
+                       int j0, int nj, cudaStream_t st) {
   ColSolve1<T> op;
+  op.cband = H->cband;
+  op.nb = nb;
   op.Uh = Uh;
   op.out = out;
   op.A = A;
@@ -232,17 +234,26 @@ __device__ __forceinline__ double sq_abs(double2 v) { return fma(v.x, v.x, v.y *
 constexpr int kAlphaCPB = 64;  // classes per block
 constexpr int kAlphaSplit = 4; // threads per class in the power gather
 
-// r^2(alpha_k) = n^-2 sum_c Ft[c][k] P[c]  (Parseval; M = 1 closed form of ||A zeta_alpha - U||^2),
+// Per band b of frequency classes (one band: the whole spectrum),
+//   r_b^2(alpha_k) = n^-2 sum_{c in b} Ft[c][k] P[c]  (Parseval; M = 1 closed form of the residual),
 // with P[c] the data power of class c: every stored half-spectrum bin of the class, weighted 1 on
 // the kx = 0 and kx = n/2 columns and 2 elsewhere (their mirror bins are not stored), summed over
-// planes.  Deterministic: fixed-order partial sums per block, reduced by the last block to finish.
+// planes.  The discrepancy rule picks, per band, the largest alpha_k with r_b^2 <= thr2.t[b].
+// Deterministic: fixed-order partial sums per block, reduced by the last block to finish.
+struct BandThr {
+  double t[FR3D_MAX_BANDS];
+};
+
 template <typename C>
 __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
-                                                  const double* __restrict__ Ft, int na, double thr2, double inv_n2,
+                                                  const double* __restrict__ Ft, int na, const BandThr& thr2,
+                                                  const unsigned char* __restrict__ cband, int nb, double inv_n2,
                                                   double* __restrict__ partials, unsigned* __restrict__ counter,
                                                   int* __restrict__ aidx, double* __restrict__ res_out,
                                                   int* __restrict__ info, int blk, int nblk) {
   __shared__ double sP[kAlphaCPB];
+  __shared__ unsigned char sB[kAlphaCPB];
+  __shared__ int present[FR3D_MAX_BANDS];
   __shared__ double red[256];
   __shared__ bool last;
   extern __shared__ double sF[];             // [kAlphaCPB][na] slab of Ft for this block's classes
@@ -250,6 +261,7 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
   const int c0 = blk * kAlphaCPB;
   const int nF = min(kAlphaCPB, Cn - c0) * na;
   const double* slab = Ft + (long)c0 * na;
+  if (tid < FR3D_MAX_BANDS) present[tid] = 0;
   // one round of global loads: this thread's share of the class powers and of the filter slab
   const int cl = tid / kAlphaSplit, sub = tid % kAlphaSplit, c = c0 + cl;
   int kxs[4] = {0, 0, 0, 0}, kys[4] = {0, 0, 0, 0}, nm = 0;
@@ -298,22 +310,31 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
 #pragma unroll
     for (int k = 0; k < kAlphaSplit; ++k) s += red[tid * kAlphaSplit + k];
     sP[tid] = s;
+    const int b = (c0 + tid < Cn && nb > 1) ? (int)cband[c0 + tid] : 0;
+    sB[tid] = (unsigned char)b;
+    if (c0 + tid < Cn) present[b] = 1;
   }
   __syncthreads();
   const int S = 256 / na;
-  if (tid < S * na) {
-    const int k = tid % na, sb = tid / na;
-    double a2 = 0.0;
-    for (int cc = sb; cc < kAlphaCPB; cc += S) {
-      if (c0 + cc < Cn) a2 = fma(sF[cc * na + k], sP[cc], a2);
+  for (int b = 0; b < nb; ++b) {
+    if (present[b]) {
+      if (tid < S * na) {
+        const int k = tid % na, sb = tid / na;
+        double a2 = 0.0;
+        for (int cc = sb; cc < kAlphaCPB; cc += S) {
+          if (c0 + cc < Cn && sB[cc] == b) a2 = fma(sF[cc * na + k], sP[cc], a2);
+        }
+        red[tid] = a2;
+      }
+      __syncthreads();
     }
-    red[tid] = a2;
-  }
-  __syncthreads();
-  if (tid < na) {
-    double s = 0.0;
-    for (int sb = 0; sb < S; ++sb) s += red[sb * na + tid];
-    partials[(long)blk * na + tid] = s;
+    if (tid < na) {
+      double s = 0.0;
+      if (present[b])
+        for (int sb = 0; sb < S; ++sb) s += red[sb * na + tid];
+      partials[((long)blk * nb + b) * na + tid] = s;
+    }
+    __syncthreads();
   }
   __threadfence();
   __syncthreads();
@@ -321,37 +342,43 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
   __syncthreads();
   if (!last) return;
   __threadfence();
-  __shared__ double r2[FR3D_MAX_ALPHAS];
-  // the S threads of candidate k sum every S-th block's partial, 16 loads in flight per round,
-  // then the S sums are added in a fixed order
-  if (tid < S * na) {
-    const int k = tid % na, sb = tid / na;
+  __shared__ double r2[FR3D_MAX_BANDS * FR3D_MAX_ALPHAS];
+  // output o = (b, k): T threads per output each sum every T-th block's partial (16 loads in flight
+  // per round), then the T sums are added in a fixed order
+  const int O = nb * na;
+  const int T = O >= 256 ? 1 : 256 / O;
+  for (int o0 = 0; o0 < O; o0 += 256 / T) {
+    const int o = o0 + tid % (256 / T), sb = tid / (256 / T);
     double s = 0.0;
-    for (int b0 = sb; b0 < nblk; b0 += 16 * S) {
-      double v[16];
+    if (o < O && sb < T) {
+      for (int b0 = sb; b0 < nblk; b0 += 16 * T) {
+        double v[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int b = b0 + i * S;
-        v[i] = b < nblk ? __ldcg(partials + (long)b * na + k) : 0.0;
+        for (int i = 0; i < 16; ++i) {
+          const int bb = b0 + i * T;
+          v[i] = bb < nblk ? __ldcg(partials + (long)bb * O + o) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) s += v[i];
       }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) s += v[i];
     }
     red[tid] = s;
+    __syncthreads();
+    if (tid < 256 / T && o0 + tid < O) {
+      double t = 0.0;
+      for (int sb2 = 0; sb2 < T; ++sb2) t += red[sb2 * (256 / T) + tid];
+      r2[o0 + tid] = t * inv_n2;
+      if (res_out) res_out[o0 + tid] = t * inv_n2;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (tid < na) {
-    double s = 0.0;
-    for (int sb = 0; sb < S; ++sb) s += red[sb * na + tid];
-    r2[tid] = s * inv_n2;
-    if (res_out) res_out[tid] = s * inv_n2;
-  }
-  __syncthreads();
-  if (tid == 0) {
+  __shared__ int flg[FR3D_MAX_BANDS];
+  if (tid < nb) {
     int best = -1, flags = 0, ok = 0;
     for (int k = 0; k < na; ++k) {
-      if (!isfinite(r2[k])) flags |= FR3D_INFO_NONFINITE;
-      if (r2[k] <= thr2) {
+      const double v = r2[tid * na + k];
+      if (!isfinite(v)) flags |= FR3D_INFO_NONFINITE;
+      if (v <= thr2.t[tid]) {
         best = k;
         ++ok;
       }
@@ -362,7 +389,13 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
     } else if (ok == na) {
       flags |= FR3D_INFO_ALPHA_ALL_SATISFY;
     }
-    *aidx = best;
+    aidx[tid] = best;
+    flg[tid] = flags;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int flags = 0;
+    for (int b = 0; b < nb; ++b) flags |= flg[b];
     if (info) *info = flags;
     *counter = 0u;
   }
@@ -370,29 +403,26 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
-                                                      const double* __restrict__ Ft, int na, double thr2, double inv_n2,
+                                                      const double* __restrict__ Ft, int na, BandThr thr2,
+                                                      const unsigned char* __restrict__ cband, int nb, double inv_n2,
                                                       double* __restrict__ partials, unsigned* __restrict__ counter,
                                                       int* __restrict__ aidx, double* __restrict__ res_out,
                                                       int* __restrict__ info) {
-  alpha_choose_body(Uh, ps, nplanes, n, Cn, Ft, na, thr2, inv_n2, partials, counter, aidx, res_out, info,
+  alpha_choose_body(Uh, ps, nplanes, n, Cn, Ft, na, thr2, cband, nb, inv_n2, partials, counter, aidx, res_out, info,
                     (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <typename T>
-int Ops<T>::alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, double thr2, int* aidx, double* residuals,
-                         int* info, cudaStream_t st) {
+int Ops<T>::alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, const double* thr2, int nb, int* aidx,
+                         double* residuals, int* info, cudaStream_t st) {
   const int blocks = (H->C + kAlphaCPB - 1) / kAlphaCPB;
-  if (H->partial_cap < blocks * n_alpha) {
-    if (H->partials) cudaFree(H->partials);
-    H->partials = nullptr;
-    H->partial_cap = 0;
-    FR3D_CUDA_TRY(cudaMalloc(&H->partials, sizeof(double) * blocks * FR3D_MAX_ALPHAS));
-    H->partial_cap = blocks * FR3D_MAX_ALPHAS;
-  }
+  FR3D_TRY(ensure_partials(H));
   const long ps = (long)(H->n / 2 + 1) * H->n;
   const size_t sm = sizeof(double) * kAlphaCPB * n_alpha;
   FR3D_TRY(set_smem(k_alpha_choose<C>, sm));
-  k_alpha_choose<C><<<blocks, 256, sm, st>>>(Uh, ps, nplanes, H->n, H->C, H->Ft, n_alpha, thr2,
+  BandThr t;
+  for (int b = 0; b < nb; ++b) t.t[b] = thr2[b];
+  k_alpha_choose<C><<<blocks, 256, sm, st>>>(Uh, ps, nplanes, H->n, H->C, H->Ft, n_alpha, t, H->cband, nb,
                                             1.0 / ((double)H->n * H->n), H->partials, H->counter, aidx, residuals,
                                             info);
   return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;

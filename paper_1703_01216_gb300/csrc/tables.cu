@@ -4,7 +4,10 @@
 //   Ft[c][k] = (alpha_k s^2 / (||A^(c)||^2 + alpha_k s^2))^2     (residual filter, M = 1)
 // They are cached in the handle and rebuilt only when the candidate list changes; D also has a
 // dense copy in the half-spectrum layout for the fused inverse.
+#include <math.h>
 #include <string.h>
+
+#include <vector>
 
 #include "ops.cuh"
 
@@ -71,6 +74,52 @@ int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) 
   k_dense_d<<<1024, 256, 0, st>>>(H->D32, n_alpha, H->C, H->n, H->Dd32);
   FR3D_CUDA_TRY(cudaGetLastError());
   H->alpha_key.assign(alphas, alphas + n_alpha);
+  return FR3D_OK;
+}
+
+int ensure_partials(Handle* H) {
+  const int blocks = (H->C + 63) / 64;
+  const int need = blocks * FR3D_MAX_ALPHAS * FR3D_MAX_BANDS;
+  if (H->partial_cap >= need) return FR3D_OK;
+  if (H->partials) cudaFree(H->partials);
+  H->partials = nullptr;
+  H->partial_cap = 0;
+  FR3D_CUDA_TRY(cudaMalloc(&H->partials, sizeof(double) * need));
+  H->partial_cap = need;
+  return FR3D_OK;
+}
+
+// Radial band of frequency class (p, q): floor(nb |k| / |k|max) with |k| = sqrt(p^2 + q^2) and
+// |k|max = sqrt(2) n/2 (clamped to nb - 1).  count[b] = number of grid frequencies in band b (each
+// class counts its members with the weights of the stored half spectrum: 1 on the kx = 0 and
+// kx = n/2 columns, 2 elsewhere).
+int ensure_bands(Handle* H, int nb, std::vector<double>* count) {
+  if (H->cband_nb != nb || !H->cband) {
+    const int n = H->n;
+    std::vector<unsigned char> band(H->C);
+    std::vector<double> cnt(nb, 0.0);
+    const double rmax = sqrt(2.0) * (n / 2);
+    for (int p = 0; p <= n / 2; ++p)
+      for (int q = 0; q <= p; ++q) {
+        const int c = p * (p + 1) / 2 + q;
+        int b = (int)(nb * sqrt((double)p * p + (double)q * q) / rmax);
+        if (b > nb - 1) b = nb - 1;
+        band[c] = (unsigned char)b;
+        auto wt = [&](int kx) { return (kx == 0 || 2 * kx == n) ? 1.0 : 2.0; };
+        double w = wt(p);
+        if (q != 0 && 2 * q != n) w += wt(p);
+        if (p != q) {
+          w += wt(q);
+          if (p != 0 && 2 * p != n) w += wt(q);
+        }
+        cnt[b] += w;
+      }
+    if (!H->cband) FR3D_CUDA_TRY(cudaMalloc(&H->cband, H->C));
+    FR3D_CUDA_TRY(cudaMemcpy(H->cband, band.data(), H->C, cudaMemcpyHostToDevice));
+    H->cband_nb = nb;
+    H->band_count = cnt;
+  }
+  if (count) *count = H->band_count;
   return FR3D_OK;
 }
 

@@ -130,16 +130,28 @@ int twiddle_offset(const Handle* H, int L) {
 }
 
 int smem_optin(const void* kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return FR3D_OK;
+  // static shared memory counts against the same 48 KB default, so opt in whenever dynamic memory
+  // is used (at most once per kernel and device)
+  if (bytes == 0) return FR3D_OK;
+  struct Entry {
+    const void* k;
+    int dev;
+    size_t bytes;
+  };
   static std::mutex mu;
-  static std::vector<std::pair<const void*, int>> done;
+  static std::vector<Entry> done;
   int dev = 0;
   FR3D_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
-  for (const auto& d : done)
-    if (d.first == kernel && d.second == dev) return FR3D_OK;
+  for (auto& d : done)
+    if (d.k == kernel && d.dev == dev) {
+      if (d.bytes >= bytes) return FR3D_OK;
+      FR3D_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      d.bytes = bytes;
+      return FR3D_OK;
+    }
   FR3D_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  done.emplace_back(kernel, dev);
+  done.push_back({kernel, dev, bytes});
   return FR3D_OK;
 }
 
@@ -244,7 +256,7 @@ static int kernel_transform_impl(const fr3d_geometry* g, Handle* H, cudaStream_t
     TRYB(cudaMalloc(&H->zr64, H->Mp * sizeof(double)));
     TRYB(cudaMalloc(&H->zr32, H->Mp * sizeof(float)));
     TRYB(cudaMalloc(&H->counter, sizeof(unsigned)));
-    TRYB(cudaMalloc(&H->idx_scratch, sizeof(int)));
+    TRYB(cudaMalloc(&H->idx_scratch, sizeof(int) * FR3D_MAX_BANDS));
     TRYB(cudaMalloc(&H->zero_idx, sizeof(int)));
     TRYB(cudaMalloc(&H->info_scratch, sizeof(int)));
     TRYB(cudaMemsetAsync(H->counter, 0, sizeof(unsigned), st));
@@ -281,7 +293,7 @@ static int kernel_transform_impl(const fr3d_geometry* g, Handle* H, cudaStream_t
 void handle_free(Handle* H) {
   void* ptrs[] = {H->A64, H->nrm, H->s2, H->A32, H->A64d, H->tw32, H->tw64, H->Ft, H->D32, H->D64,
                   H->Dfix32, H->Dfix64, H->zr64, H->zr32, H->wtab, H->Dd32, H->Ddfix32, H->pts32, H->pts64, H->counter, H->idx_scratch, H->zero_idx,
-                  H->info_scratch, H->partials, H->ws};
+                  H->info_scratch, H->partials, H->cband, H->ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < Handle::kMaxEv; ++i)

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "lib", "libfr3d.so")
 
 OK = 0
 PREC_FP32, PREC_FP64 = 0, 1
-ALPHA_FIXED, ALPHA_DISCREPANCY = 0, 1
+ALPHA_FIXED, ALPHA_DISCREPANCY, ALPHA_GIVEN = 0, 1, 2
+MAX_BANDS = 16
 OUT_ZETA, OUT_XI = 0, 1
 INFO_ALPHA_NONE_SATISFIES, INFO_ALPHA_ALL_SATISFY, INFO_NONFINITE = 1, 2, 4
 K_DZ_INV_R = 0
@@ -42,7 +43,7 @@ class InvertOpts(ct.Structure):
     _fields_ = [("alpha_mode", ct.c_int), ("alpha", ct.c_double), ("alphas", _dp), ("n_alpha", ct.c_int),
                 ("delta", ct.c_double), ("tau", ct.c_double), ("output", ct.c_int), ("precision", ct.c_int),
                 ("sources", ct.POINTER(Sources)), ("alpha_idx", ct.c_void_p), ("residuals", ct.c_void_p),
-                ("info", ct.c_void_p)]
+                ("info", ct.c_void_p), ("n_bands", ct.c_int)]
 
 
 class Instance(ct.Structure):
@@ -214,14 +215,16 @@ class Opts:
     """Builds fr3d_invert_opts and keeps its host arrays alive."""
 
     def __init__(self, *, alpha=None, alphas=None, delta=0.0, tau=1.1, output=OUT_XI, precision=PREC_FP32,
-                 points=None, A0=1.0, alpha_idx=None, residuals=None, info=None):
+                 points=None, A0=1.0, alpha_idx=None, residuals=None, info=None, n_bands=1, given=False):
         o = InvertOpts()
         if alpha is not None:
             o.alpha_mode, o.alpha = ALPHA_FIXED, float(alpha)
             self._a = None
         else:
             self._a, ap = _f64(alphas)
-            o.alpha_mode, o.alphas, o.n_alpha = ALPHA_DISCREPANCY, ap, self._a.size
+            o.alpha_mode = ALPHA_GIVEN if given else ALPHA_DISCREPANCY
+            o.alphas, o.n_alpha = ap, self._a.size
+        o.n_bands = int(n_bands)
         o.delta, o.tau, o.output, o.precision = float(delta), float(tau), int(output), int(precision)
         if points is not None:
             self._src, self._pts = make_sources(points, A0)

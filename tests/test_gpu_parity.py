@@ -260,3 +260,34 @@ def test_invert_captures_into_a_cuda_graph(F):
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("n,mp,q,nb", [(32, 8, 1, 4), (48, 6, 2, 6), (64, 5, 3, 8)])
+def test_invert_per_band_discrepancy_and_given_bands(F, n, mp, q, nb):
+    w = I.make_workload(n, mp, q=q, n_incl=3, noise_level=0.02, n_alpha=16, seed=300 + n)
+    A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu)
+    U, delta, _ = noisy_data(w, A)
+    ref = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=delta, tau=1.1, sources=w.sources,
+                   A=A, n_bands=nb)
+    H = handle_for(F, w)
+    idx = torch.zeros(nb, dtype=torch.int32, device="cuda")
+    res = torch.zeros((nb, w.alphas.size), dtype=torch.float64, device="cuda")
+    xi = torch.empty((mp, n, n), device="cuda")
+    F.invert(H, dev(U), q, xi, F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx,
+                                      residuals=res, n_bands=nb))
+    r = host(res)
+    assert np.max(np.abs(r - ref["res2"]) / np.maximum(ref["res2"], 1e-300)) <= 1e-5
+    got = [int(v) for v in idx.cpu().numpy()]
+    count = np.bincount(O.radial_bands(n, nb), minlength=nb)
+    for b in range(nb):
+        thr2 = (1.1 * delta) ** 2 * count[b] / (n * n)
+        _check_choice(got[b], ref["res2"][b], thr2, 1e-4)
+    if got == ref["alpha_index"]:
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+    # the same per-band indices given explicitly (the learned path) reproduce the result
+    xg = torch.empty_like(xi)
+    F.invert(H, dev(U), q, xg, F.Opts(alphas=w.alphas, points=w.sources, alpha_idx=idx, n_bands=nb, given=True))
+    assert torch.equal(xg, xi)
+    ref2 = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, sources=w.sources, A=A, n_bands=nb,
+                    band_alpha_index=got)
+    assert rel(host(xg), ref2["xi"]) <= 1e-4

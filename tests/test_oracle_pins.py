@@ -284,3 +284,20 @@ def test_combination_recovers_shared_xi_exactly():
     c = x0 + (np.arange(n) + 0.5) * h
     v = O.V0(S[0], c[None, None, :], c[None, :, None], np.array(zr)[:, None, None])
     assert rel(O.combine_sources(zeta[:1], S[:1], n, x0, h, zr), zeta[0] / v) < 1e-14
+
+
+def test_band_residuals_partition_the_global_residual():
+    """Per-band residuals add up to the global one; the bands partition the grid; one band is the
+    global rule."""
+    n, h, zy, zr, nu = 12, 0.2, [0.0], [0.5, 0.7, 0.9], [0.2] * 3
+    rng = np.random.default_rng(21)
+    U = rng.standard_normal((2, 1, n, n))
+    al = np.logspace(-6, 0, 7)
+    g = O.invert(U, n, -1.2, h, zy, zr, nu, alphas=al, delta=0.5, tau=1.1, output="none")
+    b = O.invert(U, n, -1.2, h, zy, zr, nu, alphas=al, delta=0.5, tau=1.1, output="none", n_bands=4)
+    assert np.allclose(b["res2"].sum(axis=0), g["res2"], rtol=1e-12)
+    assert np.bincount(O.radial_bands(n, 4), minlength=4).sum() == n * n
+    assert np.all(np.bincount(O.radial_bands(n, 4), minlength=4) > 0)
+    one = O.invert(U, n, -1.2, h, zy, zr, nu, alphas=al, delta=0.5, tau=1.1, output="zeta", band_alpha_index=[3])
+    fix = O.invert(U, n, -1.2, h, zy, zr, nu, alpha=al[3], output="zeta")
+    assert np.allclose(one["zeta"], fix["zeta"], rtol=0, atol=1e-13 * np.abs(fix["zeta"]).max())
