@@ -1,2 +1,3 @@
 """FP64 CPU oracle (test infrastructure only; see fr3d_oracle's header)."""
 from .fr3d_oracle import *  # noqa: F401,F403
+from .learned_oracle import *  # noqa: F401,F403
