@@ -63,6 +63,9 @@ extern "C" {
 #define FR3D_INFO_ALPHA_NONE_SATISFIES 1 /* no candidate met the bound: the smallest alpha was used */
 #define FR3D_INFO_ALPHA_ALL_SATISFY 2    /* every candidate met the bound: the largest alpha was used */
 #define FR3D_INFO_NONFINITE 4            /* the data spectrum held NaN/Inf */
+#define FR3D_INFO_LEARNED_OUT_OF_RANGE 8 /* LEARNED: a band's predicted log10 alpha lay more than half a
+                                            decade outside the candidate grid (the nearest end was used;
+                                            the discrepancy rule is the fallback to run) */
 
 /* ---- enums ---- */
 #define FR3D_K_DZ_INV_R 0 /* K = d/dz (1/r), Eq. (4) (the equation the paper solves) */
@@ -71,6 +74,7 @@ extern "C" {
 #define FR3D_ALPHA_FIXED 0
 #define FR3D_ALPHA_DISCREPANCY 1
 #define FR3D_ALPHA_GIVEN 2        /* per-band indices into `alphas` supplied in alpha_idx (no sweep) */
+#define FR3D_ALPHA_LEARNED 3      /* per-band alpha predicted by a trained network (fr3d_mlp, below) */
 #define FR3D_OUT_ZETA 0   /* output zeta_q per source parameter: [Q][M'][n][n] */
 #define FR3D_OUT_XI 1     /* output xi (Algorithm 1 step 4): [M'][n][n] */
 
@@ -101,6 +105,7 @@ typedef struct fr3d_sources {
 } fr3d_sources;
 
 typedef struct fr3d_handle fr3d_handle;
+typedef struct fr3d_mlp fr3d_mlp;
 
 typedef struct fr3d_invert_opts {
   int alpha_mode;          /* FR3D_ALPHA_FIXED or FR3D_ALPHA_DISCREPANCY */
@@ -122,7 +127,8 @@ typedef struct fr3d_invert_opts {
                               2..FR3D_MAX_BANDS: radial bands of |k| (band b holds the frequencies with
                               b <= n_bands |k| / (sqrt(2) n/2) < b + 1), each with its own alpha; the
                               discrepancy bound of band b is tau delta sqrt(frequencies in b / n^2)
-                              (white noise).  DISCREPANCY and GIVEN only, M = 1. */
+                              (white noise).  DISCREPANCY, GIVEN and LEARNED only, M = 1. */
+  const fr3d_mlp* net;     /* LEARNED: the network (n_in == n_out == max(1, n_bands)); NULL otherwise */
 } fr3d_invert_opts;
 
 /* Step 1 for the kernel (Algorithm 1, Sec. 5): samples K at the periodic lags for every
@@ -203,6 +209,49 @@ int fr3d_batch_launch_count(fr3d_batch* b);
 void fr3d_batch_destroy(fr3d_batch* b);
 /* create + run + synchronise + destroy in one call */
 int fr3d_invert_batched(const fr3d_instance* inst, int n, void* stream);
+
+/* ---- learned per-band alpha (FR3D_ALPHA_LEARNED) ----
+ * The paper chooses one alpha by the discrepancy principle (Sec. 4); it has no learned rule.  This
+ * one replaces the alpha sweep by a small network that maps per-band statistics of the data to one
+ * alpha per radial band (the bands of fr3d_invert_opts.n_bands).  Features, per band b:
+ *     f_b = log10( sum over the frequencies k of b and all planes of |U~_k|^2 / (count_b delta^2) ),
+ * the data power per frequency over that of white noise of total norm delta.  Network:
+ *     y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3,  x = f / 4,  y_b = (log10 alpha_b + 4.5) / 3.5,
+ * parameters in one vector [W1 (n_hidden x n_in, row-major), b1, W2 (n_hidden x n_hidden), b2,
+ * W3 (n_out x n_hidden), b3]; the kernels use a BF16 copy of the weights with FP32 arithmetic, the
+ * update keeps an FP32 master copy (Adam, beta1 0.9, beta2 0.999, eps 1e-8, loss = mean squared
+ * error).  Inference (inside fr3d_invert, LEARNED) takes per band the candidate of opts.alphas nearest
+ * to the predicted log10 alpha; delta must be > 0; FP32 only; residuals are not written.
+ * Training targets (fr3d_band_alpha_targets): for data U made from a known zeta (fr3d_fwd_apply plus
+ * noise), the candidate minimising, per band, the error sum ||zeta~_alpha - zeta~_true||^2 of the
+ * Tikhonov solution (M = 1: evaluated in closed form per frequency class, no solve).  X, T, Y: device [B][n_in] / [B][n_out] float; grad: device [n_params] float;
+ * loss: device float; params: HOST [n_params] float.  A network serves one stream at a time. */
+int fr3d_mlp_create(int n_in, int n_hidden, int n_out, unsigned long long seed, fr3d_mlp** out);
+                          /* 1 <= n_in, n_out <= FR3D_MAX_BANDS, 1 <= n_hidden <= 96; Glorot-uniform
+                             weights from SplitMix64(seed), zero biases; synchronous */
+void fr3d_mlp_destroy(fr3d_mlp* net);
+int fr3d_mlp_query(const fr3d_mlp* net, int* n_in, int* n_hidden, int* n_out, int* n_params);
+int fr3d_mlp_get_params(fr3d_mlp* net, float* params);        /* synchronous */
+int fr3d_mlp_set_params(fr3d_mlp* net, const float* params);  /* synchronous; resets the Adam state */
+int fr3d_mlp_forward(fr3d_mlp* net, const float* X, int B, float* Y, void* stream);
+/* loss (if non-NULL) and the gradient of the loss (copied to grad if non-NULL) for one batch */
+int fr3d_mlp_gradient(fr3d_mlp* net, const float* X, const float* T, int B, float* grad, float* loss,
+                      void* stream);
+/* gradient + one Adam step with learning rate lr */
+int fr3d_mlp_train_step(fr3d_mlp* net, const float* X, const float* T, int B, float lr, float* loss,
+                        void* stream);
+/* the network input x_b = f_b / 4 of data U (device [Q][1][n][n] float, M = 1) into feat (device
+ * float[n_bands]) */
+int fr3d_band_features(fr3d_handle* h, const float* U, int Q, int n_bands, double delta, float* feat,
+                       void* stream);
+/* per-band error-optimal candidate for data U (device [Q][1][n][n] float, M = 1) made from the known
+ * zeta_true (device [Q][M'][n][n] float): idx (device int[n_bands]); target (device float[n_bands] or
+ * NULL): y_b of the chosen candidate; err (device double[n_bands][n_alpha] or NULL): the error curves
+ * E_b(alpha_k) = sum over the frequencies of band b, all q and all depths of |zeta~_alpha - zeta~_true|^2
+ * (unnormalised spectra) */
+int fr3d_band_alpha_targets(fr3d_handle* h, const float* U, const float* zeta_true, int Q,
+                            const double* alphas, int n_alpha, int n_bands, int* idx, float* target,
+                            double* err, void* stream);
 
 /* Number of kernel launches the last call on this handle enqueued (cache rebuilds excluded). */
 int fr3d_last_launch_count(fr3d_handle* h);

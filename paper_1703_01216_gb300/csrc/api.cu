@@ -208,6 +208,11 @@ int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
   } else if (o->alpha_mode == FR3D_ALPHA_GIVEN) {
     FR3D_TRY(check_alphas(o->alphas, o->n_alpha));
     if (!o->alpha_idx) return FR3D_ERR_INVALID_ARG;
+  } else if (o->alpha_mode == FR3D_ALPHA_LEARNED) {
+    FR3D_TRY(check_alphas(o->alphas, o->n_alpha));
+    if (!(o->delta > 0) || !isfinite(o->delta)) return FR3D_ERR_INVALID_ARG;
+    if (o->precision != FR3D_PREC_FP32) return FR3D_ERR_INVALID_ARG;
+    if (!learned_net_fits(o->net, o->n_bands > 1 ? o->n_bands : 1)) return FR3D_ERR_INVALID_ARG;
   } else {
     return FR3D_ERR_INVALID_ARG;
   }
@@ -247,6 +252,19 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
     aidx = idx;
     if constexpr (sizeof(T) == 4) D = H->D32;
     else D = H->D64;
+  } else if (o->alpha_mode == FR3D_ALPHA_LEARNED) {
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    prof_mark(H, kStTable, st);
+    int* idx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
+    if constexpr (sizeof(T) == 4) {
+      FR3D_TRY(learned_alpha(H, Uh, Q * H->M, nb, o->delta, o->alphas, o->n_alpha, o->net, idx, nullptr, o->info, st));
+      D = H->D32;
+    } else {
+      return FR3D_ERR_INVALID_ARG;   // excluded by check_invert_args
+    }
+    prof_mark(H, kStAlpha, st);
+    launches += 1;
+    aidx = idx;
   } else if (o->alpha_mode == FR3D_ALPHA_GIVEN) {
     FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
     prof_mark(H, kStTable, st);
@@ -313,6 +331,7 @@ int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** U
   if (o->output == FR3D_OUT_XI) FR3D_TRY(ensure_wtab(H, o->sources, st));
   const int nb = o->n_bands > 1 ? o->n_bands : 1;
   if (nb > 1) FR3D_TRY(ensure_bands(H, nb, nullptr));
+  if (o->alpha_mode == FR3D_ALPHA_LEARNED) return FR3D_ERR_INVALID_ARG;   // not in batched plans
   if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY || o->alpha_mode == FR3D_ALPHA_GIVEN) {
     FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
     FR3D_TRY(ensure_partials(H));

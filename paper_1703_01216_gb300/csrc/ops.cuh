@@ -52,6 +52,12 @@ int ensure_partials(Handle* H);
 // band of every frequency class for nb radial bands, and the number of grid frequencies per band
 int ensure_bands(Handle* H, int nb, std::vector<double>* count);
 
+// learned per-band alpha (learned.cu): one launch computing the band features (to feat, if given)
+// and, with a network, the per-band candidate indices (to aidx); info gets the INFO bits
+bool learned_net_fits(const fr3d_mlp* net, int nb);
+int learned_alpha(Handle* H, const float2* Uh, int nplanes, int nb, double delta, const double* alphas, int na,
+                  const fr3d_mlp* net, int* aidx, float* feat, int* info, cudaStream_t st);
+
 // precision-independent table builders (alpha tables, fixed alpha)
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st);
 int fixed_table(Handle* H, double alpha, cudaStream_t st);

@@ -79,7 +79,8 @@ int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) 
 
 int ensure_partials(Handle* H) {
   const int blocks = (H->C + 63) / 64;
-  const int need = blocks * FR3D_MAX_ALPHAS * FR3D_MAX_BANDS;
+  // alpha rule: [blocks][bands][alphas]; learned rule: at most 2 * 152 blocks of FR3D_MAX_BANDS sums
+  const int need = std::max(blocks * FR3D_MAX_ALPHAS * FR3D_MAX_BANDS, 2 * 152 * FR3D_MAX_BANDS);
   if (H->partial_cap >= need) return FR3D_OK;
   if (H->partials) cudaFree(H->partials);
   H->partials = nullptr;

@@ -18,10 +18,11 @@ LIB_PATH = os.path.join(HERE, "lib", "libfr3d.so")
 
 OK = 0
 PREC_FP32, PREC_FP64 = 0, 1
-ALPHA_FIXED, ALPHA_DISCREPANCY, ALPHA_GIVEN = 0, 1, 2
+ALPHA_FIXED, ALPHA_DISCREPANCY, ALPHA_GIVEN, ALPHA_LEARNED = 0, 1, 2, 3
 MAX_BANDS = 16
 OUT_ZETA, OUT_XI = 0, 1
-INFO_ALPHA_NONE_SATISFIES, INFO_ALPHA_ALL_SATISFY, INFO_NONFINITE = 1, 2, 4
+INFO_ALPHA_NONE_SATISFIES, INFO_ALPHA_ALL_SATISFY, INFO_NONFINITE, INFO_LEARNED_OUT_OF_RANGE = 1, 2, 4, 8
+MAX_HIDDEN = 96
 K_DZ_INV_R = 0
 MAX_ALPHAS = 128
 MAX_SOURCE_POINTS = 256
@@ -43,7 +44,7 @@ class InvertOpts(ct.Structure):
     _fields_ = [("alpha_mode", ct.c_int), ("alpha", ct.c_double), ("alphas", _dp), ("n_alpha", ct.c_int),
                 ("delta", ct.c_double), ("tau", ct.c_double), ("output", ct.c_int), ("precision", ct.c_int),
                 ("sources", ct.POINTER(Sources)), ("alpha_idx", ct.c_void_p), ("residuals", ct.c_void_p),
-                ("info", ct.c_void_p), ("n_bands", ct.c_int)]
+                ("info", ct.c_void_p), ("n_bands", ct.c_int), ("net", ct.c_void_p)]
 
 
 class Instance(ct.Structure):
@@ -65,7 +66,10 @@ EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", 
            "fr3d_zeta_from_xi", "fr3d_choose_alpha", "fr3d_invert", "fr3d_invert_host",
            "fr3d_last_launch_count", "fr3d_profile_enable", "fr3d_profile_read", "fr3d_status_string",
            "fr3d_batch_create", "fr3d_batch_run", "fr3d_batch_launch_count", "fr3d_batch_destroy",
-           "fr3d_invert_batched")
+           "fr3d_invert_batched",
+           "fr3d_mlp_create", "fr3d_mlp_destroy", "fr3d_mlp_query", "fr3d_mlp_get_params", "fr3d_mlp_set_params",
+           "fr3d_mlp_forward", "fr3d_mlp_gradient", "fr3d_mlp_train_step", "fr3d_band_features",
+           "fr3d_band_alpha_targets")
 
 
 def load(path: str | None = None):
@@ -97,10 +101,21 @@ def load(path: str | None = None):
     lib.fr3d_batch_destroy.argtypes = [vp]
     lib.fr3d_batch_destroy.restype = None
     lib.fr3d_invert_batched.argtypes = [ct.POINTER(Instance), i, vp]
+    lib.fr3d_mlp_create.argtypes = [i, i, i, ct.c_ulonglong, ct.POINTER(vp)]
+    lib.fr3d_mlp_destroy.argtypes = [vp]
+    lib.fr3d_mlp_destroy.restype = None
+    lib.fr3d_mlp_query.argtypes = [vp, ct.POINTER(i), ct.POINTER(i), ct.POINTER(i), ct.POINTER(i)]
+    lib.fr3d_mlp_get_params.argtypes = [vp, vp]
+    lib.fr3d_mlp_set_params.argtypes = [vp, vp]
+    lib.fr3d_mlp_forward.argtypes = [vp, vp, i, vp, vp]
+    lib.fr3d_mlp_gradient.argtypes = [vp, vp, vp, i, vp, vp, vp]
+    lib.fr3d_mlp_train_step.argtypes = [vp, vp, vp, i, ct.c_float, vp, vp]
+    lib.fr3d_band_features.argtypes = [vp, vp, i, i, d, vp, vp]
+    lib.fr3d_band_alpha_targets.argtypes = [vp, vp, vp, i, _dp, i, i, vp, vp, vp, vp]
     lib.fr3d_status_string.argtypes = [i]
     lib.fr3d_status_string.restype = ct.c_char_p
     for name in EXPORTS:
-        if name not in ("fr3d_handle_destroy", "fr3d_status_string", "fr3d_batch_destroy"):
+        if name not in ("fr3d_handle_destroy", "fr3d_status_string", "fr3d_batch_destroy", "fr3d_mlp_destroy"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -215,15 +230,17 @@ class Opts:
     """Builds fr3d_invert_opts and keeps its host arrays alive."""
 
     def __init__(self, *, alpha=None, alphas=None, delta=0.0, tau=1.1, output=OUT_XI, precision=PREC_FP32,
-                 points=None, A0=1.0, alpha_idx=None, residuals=None, info=None, n_bands=1, given=False):
+                 points=None, A0=1.0, alpha_idx=None, residuals=None, info=None, n_bands=1, given=False, net=None):
         o = InvertOpts()
+        self._net = net
         if alpha is not None:
             o.alpha_mode, o.alpha = ALPHA_FIXED, float(alpha)
             self._a = None
         else:
             self._a, ap = _f64(alphas)
-            o.alpha_mode = ALPHA_GIVEN if given else ALPHA_DISCREPANCY
+            o.alpha_mode = ALPHA_LEARNED if net is not None else (ALPHA_GIVEN if given else ALPHA_DISCREPANCY)
             o.alphas, o.n_alpha = ap, self._a.size
+            o.net = net.ptr if net is not None else None
         o.n_bands = int(n_bands)
         o.delta, o.tau, o.output, o.precision = float(delta), float(tau), int(output), int(precision)
         if points is not None:
@@ -263,6 +280,67 @@ def profile_read(handle: Handle, cap: int = 96):
     ms = (ct.c_float * cap)()
     n = _check(load().fr3d_profile_read(handle.ptr, kinds, ms, cap), "fr3d_profile_read")
     return [(STAGE_NAMES[kinds[i]], float(ms[i])) for i in range(n)]
+
+
+class Mlp:
+    """fr3d_mlp: the per-band alpha network (weights on the device)."""
+
+    def __init__(self, n_in: int, n_hidden: int, n_out: int, seed: int = 0):
+        p = ct.c_void_p()
+        _check(load().fr3d_mlp_create(int(n_in), int(n_hidden), int(n_out), int(seed), ct.byref(p)),
+               "fr3d_mlp_create")
+        self.ptr = p
+        self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
+        npar = ct.c_int()
+        _check(load().fr3d_mlp_query(self.ptr, None, None, None, ct.byref(npar)), "fr3d_mlp_query")
+        self.n_params = npar.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(load().fr3d_mlp_get_params(self.ptr, _ptr(out)), "fr3d_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(np.asarray(params, np.float32))
+        if a.size != self.n_params:
+            raise ValueError("wrong parameter count")
+        _check(load().fr3d_mlp_set_params(self.ptr, _ptr(a)), "fr3d_mlp_set_params")
+
+    def forward(self, X, Y, stream=None):
+        _check(load().fr3d_mlp_forward(self.ptr, _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)),
+               "fr3d_mlp_forward")
+
+    def gradient(self, X, T, grad=None, loss=None, stream=None):
+        _check(load().fr3d_mlp_gradient(self.ptr, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grad), _ptr(loss),
+                                        _stream(stream)), "fr3d_mlp_gradient")
+
+    def train_step(self, X, T, lr: float, loss=None, stream=None):
+        _check(load().fr3d_mlp_train_step(self.ptr, _ptr(X), _ptr(T), int(X.shape[0]), float(lr), _ptr(loss),
+                                          _stream(stream)), "fr3d_mlp_train_step")
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().fr3d_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def band_features(handle: Handle, U, Q: int, n_bands: int, delta: float, feat, stream=None):
+    _check(load().fr3d_band_features(handle.ptr, _ptr(U), int(Q), int(n_bands), float(delta), _ptr(feat),
+                                     _stream(stream)), "fr3d_band_features")
+
+
+def band_alpha_targets(handle: Handle, U, zeta_true, Q: int, alphas, n_bands: int, idx, target=None, err=None,
+                       stream=None):
+    a, ap = _f64(alphas)
+    _check(load().fr3d_band_alpha_targets(handle.ptr, _ptr(U), _ptr(zeta_true), int(Q), ap, a.size, int(n_bands),
+                                          _ptr(idx), _ptr(target), _ptr(err), _stream(stream)),
+           "fr3d_band_alpha_targets")
 
 
 class Batch:

@@ -1,0 +1,226 @@
+"""GPU parity and gain of the learned per-band alpha rule, through the C ABI, against the FP64 oracle.
+
+Tolerances: band features 2e-5 absolute in log10 (FP32 spectra, FP64 sums); error curves 1e-5
+relative plus a floor of 1e-12 of the total zeta energy (FP32 spectra of the data and of zeta, FP64
+sums); network output 2e-5 and gradient 1e-4
+relative (BF16 weights on both sides, FP32 arithmetic against FP64); Adam step 1e-6 absolute;
+inversion with the learned indices 1e-4 relative (the fixed-alpha reconstruction bound).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1703_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1703_01216_gb300 import build, fr3d
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    build.build()
+    fr3d.load()
+    return fr3d
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def gpu_data(F, w):
+    """U_clean = A (xi V0_q) and U = U_clean + relative noise, made by the library (FP32)."""
+    H = F.kernel_transform(w.n, w.x0, w.h, w.zr, w.zy, w.nu)
+    zeta = torch.empty((w.Q, w.Mp, w.n, w.n), device="cuda")
+    F.zeta_from_xi(H, dev(w.xi_true), w.sources, zeta)
+    Uc = torch.empty((w.Q, 1, w.n, w.n), device="cuda")
+    F.fwd_apply(H, zeta, w.Q, Uc)
+    nz = dev(w.noise)
+    nz *= w.noise_level * Uc.norm() / nz.norm()
+    return H, Uc + nz, Uc, float(nz.norm()), zeta
+
+
+# ------------------------------------------------------------------ features and targets
+@pytest.mark.parametrize("n,mp,q,nb", [(32, 8, 1, 4), (64, 16, 2, 8), (48, 6, 3, 1)])
+def test_band_features_match_oracle(F, n, mp, q, nb):
+    w = I.make_workload(n, mp, q=q, n_incl=3, noise_level=0.02, seed=500 + n)
+    H, U, _, delta, _ = gpu_data(F, w)
+    x = torch.empty(nb, device="cuda")
+    F.band_features(H, U, q, nb, delta, x)
+    ref = O.band_features(host(U), nb, delta)
+    assert np.max(np.abs(4.0 * host(x) - ref)) <= 2e-5
+
+
+@pytest.mark.parametrize("n,mp,q,nb", [(32, 8, 1, 4), (48, 12, 2, 6)])
+def test_band_targets_match_explicit_error_curves(F, n, mp, q, nb):
+    """GPU curves (closed form per frequency class) equal the oracle's explicit per-frequency
+    Tikhonov errors; the chosen candidate is a minimiser of the oracle's curve."""
+    w = I.make_workload(n, mp, q=q, n_incl=4, noise_level=0.02, n_alpha=16, seed=600 + n)
+    H, U, _, _, zeta = gpu_data(F, w)
+    idx = torch.zeros(nb, dtype=torch.int32, device="cuda")
+    tgt = torch.zeros(nb, device="cuda")
+    err = torch.zeros((nb, w.alphas.size), dtype=torch.float64, device="cuda")
+    F.band_alpha_targets(H, U, zeta, q, w.alphas, nb, idx, tgt, err)
+    A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu)
+    E = O.band_error_curves(A, host(U), host(zeta), w.alphas, nb)
+    # FP32 spectra carry rounding of ~1e-7 of each plane's largest coefficient, i.e. an error energy
+    # of ~1e-14 of the total: bands holding almost no energy get an absolute floor of 1e-12 of it
+    floor = 1e-12 * E[:, -1].sum()
+    assert np.all(np.abs(host(err) - E) <= 1e-5 * E + floor)
+    got = idx.cpu().numpy()
+    for b in range(nb):
+        assert E[b, got[b]] <= E[b].min() * (1 + 1e-5) + floor
+    assert np.allclose(host(tgt), O.log_alpha_target(w.alphas, got), atol=1e-6)
+
+
+# ------------------------------------------------------------------ network kernels
+@pytest.mark.parametrize("nin,nh,nout,B", [(8, 64, 8, 37), (3, 5, 2, 4), (16, 96, 16, 300)])
+def test_mlp_forward_and_gradient_match_oracle(F, nin, nh, nout, B):
+    net = F.Mlp(nin, nh, nout, seed=nin * 100 + nh)
+    rng = np.random.default_rng(nin + nh)
+    p = rng.standard_normal(net.n_params).astype(np.float32) * 0.5
+    net.set_params(p)
+    pb = O.bf16_round(p)
+    X = rng.standard_normal((B, nin))
+    T = rng.standard_normal((B, nout))
+    Y = torch.empty((B, nout), device="cuda")
+    net.forward(dev(X), Y)
+    ref, _ = O.mlp_forward(pb, X, nin, nh, nout)
+    assert rel(host(Y), ref) <= 2e-5
+    g = torch.empty(net.n_params, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    net.gradient(dev(X), dev(T), g, loss)
+    lref, gref = O.mlp_loss_grad(pb, X, T, nin, nh, nout)
+    assert abs(float(loss) - lref) <= 1e-5 * lref
+    assert rel(host(g), gref) <= 1e-4
+    net.close()
+
+
+def test_adam_step_matches_oracle(F):
+    nin, nh, nout, B = 8, 32, 8, 64
+    net = F.Mlp(nin, nh, nout, seed=3)
+    p0 = net.get_params()
+    rng = np.random.default_rng(9)
+    X, T = rng.standard_normal((B, nin)), rng.standard_normal((B, nout))
+    lr = 1e-3
+    for step in (1, 2):
+        p_before = net.get_params()
+        _, g = O.mlp_loss_grad(O.bf16_round(p_before), X, T, nin, nh, nout)
+        net.train_step(dev(X), dev(T), lr)
+        p_after = net.get_params()
+        if step == 1:
+            m, v = np.zeros_like(g), np.zeros_like(g)
+        pr, m, v = O.adam_step(p_before.astype(np.float64), m, v, g, step, lr)
+        big = np.abs(g) > 1e-3 * np.abs(g).max()
+        assert np.max(np.abs(p_after - pr)[big]) <= 1e-6
+    # the BF16 copy follows the master weights: the forward pass sees bf16(master)
+    Y = torch.empty((B, nout), device="cuda")
+    net.forward(dev(X), Y)
+    ref, _ = O.mlp_forward(O.bf16_round(net.get_params()), X, nin, nh, nout)
+    assert rel(host(Y), ref) <= 2e-5
+    assert not np.array_equal(p0, net.get_params())
+    net.close()
+
+
+# ------------------------------------------------------------------ learned inversion
+def _check_index(got, la, lg):
+    """got must be the nearest candidate to la, or tie with it within the FP32 output error."""
+    d = np.abs(lg - la)
+    assert d[got] <= d.min() + 1e-4
+
+
+@pytest.mark.parametrize("n,mp,q,nb", [(32, 8, 1, 4), (64, 10, 2, 8)])
+def test_learned_invert_matches_oracle(F, n, mp, q, nb):
+    w = I.make_workload(n, mp, q=q, n_incl=3, noise_level=0.02, n_alpha=16, seed=700 + n)
+    H, U, _, delta, _ = gpu_data(F, w)
+    net = F.Mlp(nb, 32, nb, seed=11)
+    rng = np.random.default_rng(n)
+    o = O.mlp_offsets(nb, 32, nb)
+    p = (rng.standard_normal(net.n_params) * 0.3).astype(np.float32)
+    p[o["b3"]:] = rng.uniform(-0.8, 0.8, nb)       # predictions inside the candidate range
+    net.set_params(p)
+    idx = torch.full((nb,), -1, dtype=torch.int32, device="cuda")
+    info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    xi = torch.empty((mp, n, n), device="cuda")
+    F.invert(H, U, q, xi, F.Opts(alphas=w.alphas, delta=delta, points=w.sources, alpha_idx=idx, info=info,
+                                 n_bands=nb, net=net))
+    feat = O.band_features(host(U), nb, delta)
+    y, la, ref_idx = O.learned_alpha_index(O.bf16_round(p), feat, w.alphas, 32)
+    got = [int(v) for v in idx.cpu().numpy()]
+    lg = np.log10(w.alphas)
+    for b in range(nb):
+        _check_index(got[b], la[b], lg)
+    out_of_range = np.any((la < lg[0] - 0.5) | (la > lg[-1] + 0.5))
+    assert int(info.item()) == (F.INFO_LEARNED_OUT_OF_RANGE if out_of_range else 0)
+    # the same indices given explicitly reproduce the result bit for bit, and the oracle agrees
+    xg = torch.empty_like(xi)
+    F.invert(H, U, q, xg, F.Opts(alphas=w.alphas, points=w.sources, alpha_idx=idx, n_bands=nb, given=True))
+    assert torch.equal(xg, xi)
+    ref = O.invert(host(U), n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, sources=w.sources, n_bands=nb,
+                   band_alpha_index=got)
+    assert rel(host(xi), ref["xi"]) <= 1e-4
+    # a prediction far outside the grid takes the nearest end and raises the flag
+    p[o["b3"]:] = 3.0
+    net.set_params(p)
+    F.invert(H, U, q, xi, F.Opts(alphas=w.alphas, delta=delta, points=w.sources, alpha_idx=idx, info=info,
+                                 n_bands=nb, net=net))
+    assert list(idx.cpu().numpy()) == [w.alphas.size - 1] * nb
+    assert int(info.item()) == F.INFO_LEARNED_OUT_OF_RANGE
+    net.close()
+
+
+def test_learned_rejects_bad_arguments(F):
+    w = I.make_workload(32, 4, q=1, seed=1)
+    H, U, _, delta, _ = gpu_data(F, w)
+    xi = torch.empty((4, 32, 32), device="cuda")
+    net = F.Mlp(4, 8, 4)
+    for kw in (dict(n_bands=3), dict(n_bands=4, delta=0.0), dict(n_bands=4, precision=F.PREC_FP64)):
+        kw.setdefault("delta", delta)
+        with pytest.raises(F.Fr3dError):
+            F.invert(H, U, 1, xi, F.Opts(alphas=w.alphas, points=w.sources, net=net, **kw))
+    with pytest.raises(F.Fr3dError):
+        F.Mlp(4, 97, 4)
+    net.close()
+
+
+# ------------------------------------------------------------------ gain over the discrepancy rule
+def test_learned_rule_beats_discrepancy_on_held_out_seeds(F):
+    """Train on pairs made by the library's own forward operator (128^2 x 32, one source, 1-12
+    inclusions, 0.5-5 % noise), then on held-out seeds compare the relative L2 error of xi against
+    the truth: learned per-band alpha versus the discrepancy principle (the paper's rule)."""
+    from paper_1703_01216_gb300 import learned as Lm
+    n, mp, nb = 128, 32, 8
+    proto = I.make_workload(n, mp, q=1, n_alpha=32, seed=0)
+    H = F.kernel_transform(n, proto.x0, proto.h, proto.zr, proto.zy, proto.nu)
+    pairs = Lm.make_pairs(H, n, proto.x0, proto.h, proto.zr, proto.sources, proto.alphas, nb, 768, seed=10_000,
+                          device="cuda")
+    net = F.Mlp(nb, 64, nb, seed=1)
+    Lm.train(net, pairs, steps=3000, batch=256, lr=3e-3, lr_final=3e-4, seed=2)
+    e_plain, e_learned = [], []
+    for i in range(12):
+        rng = np.random.default_rng(90_000 + i)
+        w = I.make_workload(n, mp, q=1, n_incl=int(rng.integers(1, 13)), kinds=("gauss", "ellipsoid"),
+                            noise_level=float(rng.uniform(0.005, 0.05)), n_alpha=32, seed=90_000 + i)
+        H2, U, _, delta, _ = gpu_data(F, w)
+        xi_p = torch.empty((mp, n, n), device="cuda")
+        xi_l = torch.empty((mp, n, n), device="cuda")
+        F.invert(H2, U, 1, xi_p, F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources))
+        F.invert(H2, U, 1, xi_l, F.Opts(alphas=w.alphas, delta=delta, points=w.sources, n_bands=nb, net=net))
+        e_plain.append(rel(host(xi_p), w.xi_true))
+        e_learned.append(rel(host(xi_l), w.xi_true))
+    print("held-out rel-L2 of xi: discrepancy", np.mean(e_plain), "learned", np.mean(e_learned))
+    assert np.mean(e_learned) <= np.mean(e_plain)
+    net.close()
