@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fr3d", choices=["fr3d", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-alpha leg")
     ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
@@ -343,6 +344,8 @@ def run_fr3d(args):
     }
     clocks = clk.summary()
     result["clocks"] = clocks
+    if not args.no_learned:
+        result["learned"] = bench_learned(args, dev, flush, w, H, U, delta, rel_truth, dist)
     if rank == 0 and not args.no_batch:
         result["batched"] = bench_batched(args, dev, flush)
 
@@ -358,6 +361,99 @@ def run_fr3d(args):
         print(json.dumps(result))
     if dist:
         dist.destroy_process_group()
+
+
+def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, pairs=1024, train_steps=3000):
+    """The learned per-band alpha rule on the same workload: a network trained on pairs made by the
+    library's forward operator at this geometry (seeds disjoint from the workload's), then the
+    inversion with FR3D_ALPHA_LEARNED timed exactly like the plain one (one CUDA graph replay per
+    step, L2 flushed before each), with its relative L2 error against the true xi beside the plain
+    discrepancy-principle error."""
+    import torch
+    from paper_1703_01216_gb300 import fr3d
+    from paper_1703_01216_gb300 import learned as Lm
+    n, Mp, Q = w.n, w.Mp, w.Q
+    t0 = time.perf_counter()
+    Ht = fr3d.kernel_transform(n, w.x0, w.h, w.zr, w.zy, w.nu)
+    ps = Lm.make_pairs(Ht, n, w.x0, w.h, w.zr, w.sources, w.alphas, n_bands, pairs, seed=20_000, device=dev)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = fr3d.Mlp(n_bands, 64, n_bands, seed=1)
+    t0 = time.perf_counter()
+    hist = Lm.train(net, ps, steps=train_steps, batch=256, lr=3e-3, lr_final=3e-4, seed=2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    Ht.close()
+    out = torch.empty((Mp, n, n), device=dev)
+    idx = torch.zeros(n_bands, dtype=torch.int32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    opts = fr3d.Opts(alphas=w.alphas, delta=delta, points=w.sources, alpha_idx=idx, info=info, n_bands=n_bands,
+                     net=net)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        flush.fill_(1.0)
+        fr3d.invert(H, U, Q, out, opts)
+    torch.cuda.synchronize()
+    fr3d.profile_enable(H, True)
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(st)
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            fr3d.invert(H, U, Q, out, opts)
+    st.wait_stream(cap)
+    launches_per_step = fr3d.last_launch_count(H)
+    for _ in range(3):
+        flush.fill_(1.0)
+        graph.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = {}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(1.0)
+        ev[k][0].record(st)
+        graph.replay()
+        ev[k][1].record(st)
+        for name, ms in fr3d.profile_read(H):
+            if name != "table":
+                stage_ms[name] = stage_ms.get(name, 0.0) + ms
+    torch.cuda.synchronize()
+    fr3d.profile_enable(H, False)
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    world = 1
+    if dist:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        world = dist.get_world_size()
+    xi_true = torch.tensor(w.xi_true, device=dev)
+    rel = float((out.double() - xi_true).norm() / xi_true.norm())
+    # the ceiling of a per-band rule: the error-optimal candidate of every band (needs the true zeta)
+    zeta = torch.empty((Q, Mp, n, n), device=dev)
+    fr3d.zeta_from_xi(H, xi_true.float(), w.sources, zeta)
+    best = torch.zeros(n_bands, dtype=torch.int32, device=dev)
+    fr3d.band_alpha_targets(H, U, zeta, Q, w.alphas, n_bands, best)
+    del zeta
+    fr3d.invert(H, U, Q, out, fr3d.Opts(alphas=w.alphas, points=w.sources, alpha_idx=best, n_bands=n_bands,
+                                        given=True))
+    rel_best = float((out.double() - xi_true).norm() / xi_true.norm())
+    res = {"value": n * n * Mp * world * args.steps / total_s, "unit": "voxels/s",
+           "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
+           "band_optimal_rel_l2_vs_truth": round(rel_best, 4),
+           "band_optimal_alpha_index": [int(v) for v in best.cpu().numpy()],
+           "ms_per_step": 1e3 * total_s / args.steps, "gpu_launches": launches_per_step * args.steps,
+           "rel_l2_vs_truth": round(rel, 4), "plain_rel_l2_vs_truth": round(plain_rel, 4),
+           "alpha_index_per_band": [int(v) for v in idx.cpu().numpy()], "info": int(info.item()),
+           "n_bands": n_bands, "network": f"{n_bands}-64-64-{n_bands} tanh MLP, BF16 weights",
+           "train_pairs": pairs, "train_steps": train_steps, "pairs_s": round(t_pairs, 2),
+           "train_s": round(t_train, 2), "final_train_loss": round(hist[-1], 5),
+           "pair_recipe": "synthetic inclusions (1-12, Gaussian/ellipsoid), 0.5-5% noise, same geometry and "
+                          "sources; seeds 20000+ (workload seed differs)"}
+    net.close()
+    return res
 
 
 def bench_batched(args, dev, flush, count=64):

@@ -261,7 +261,8 @@ int fr3d_last_launch_count(fr3d_handle* h);
  * and writes, per launch interval i < min(cap, count), its stage kind and its duration in ms;
  * it returns the count.  Kinds: 0 data row pass, 1 data column pass, 2 alpha rule, 3 solve +
  * inverse column pass, 4 inverse row pass (+ xi), 5 table rebuild, 6 forward contraction,
- * 7 inverse column pass, 8 other, 9 fused solve + inverse DFT + combination. */
+ * 7 inverse column pass, 8 other, 9 fused solve + inverse DFT + combination, 10 per-band selection of
+ * the solve weights (n_bands > 1). */
 int fr3d_profile_enable(fr3d_handle* h, int enable);
 int fr3d_profile_read(fr3d_handle* h, int* kinds, float* ms, int cap);
 

@@ -29,7 +29,8 @@ struct AlphaInst {
   int nplanes, na, nb, bstart, nblk;
 };
 
-__global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst, long ps, int n,
+// Each instance owns a whole number of clusters of blocks (alpha_blocks), so no cluster spans two.
+__global__ void __cluster_dims__(kAlphaCluster, 1, 1) __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst, long ps, int n,
                                                        int Cn, double inv_n2) {
   int i = 0;
   while (i + 1 < ninst && inst[i + 1].bstart <= (int)blockIdx.x) ++i;
@@ -159,7 +160,7 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
         a.nplanes = I.Q;
         a.na = I.opts->n_alpha;
         a.bstart = g.nalpha_blk;
-        a.nblk = (H->C + kAlphaCPB - 1) / kAlphaCPB;
+        a.nblk = alpha_blocks(H->C);
         g.nalpha_blk += a.nblk;
         g.max_na = std::max(g.max_na, a.na);
         alph.push_back(a);

@@ -14,7 +14,7 @@
 //              with P_c = sum wt |U~|^2, X_c = sum wt Re(conj(U~) a^T zeta~_true), Z_c = sum wt ||zeta~_true||^2.
 // Inside fr3d_invert (FR3D_ALPHA_LEARNED) the rule is one kernel in place of the alpha sweep: band
 // power sums (deterministic block partials, the last block finishes), features, network, nearest
-// candidate per band.
+// candidate per band, all in FP32.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -68,7 +68,8 @@ __host__ __device__ inline Off offsets(int nin, int nh, int nout) {
 constexpr float kFeatScale = 0.25f;   // x = f / 4
 constexpr float kLogShift = 4.5f;     // y = (log10 alpha + 4.5) / 3.5
 constexpr float kLogScale = 3.5f;
-constexpr int kMaxHidden = 96;        // the weights of the largest network fit the reduction buffer
+constexpr int kMaxHidden = 96;        // widest hidden layer of a network
+constexpr int kMaxParams = FR3D_MAX_BANDS * kMaxHidden * 2 + kMaxHidden * kMaxHidden + 2 * kMaxHidden + FR3D_MAX_BANDS;
 constexpr int kLearnedThreads = 256;
 
 __device__ inline float bf(const __nv_bfloat16* w, int i) { return __bfloat162float(w[i]); }
@@ -210,10 +211,10 @@ uint64_t splitmix64(uint64_t& s) {
 
 // ------------------------------------------------------------------ band statistics
 struct BandConst {
-  double count[FR3D_MAX_BANDS];   // grid frequencies per band
+  float lc[FR3D_MAX_BANDS];       // log10(count_b delta^2), formed on the host in FP64
 };
 struct AlphaLog {
-  double lg[FR3D_MAX_ALPHAS];     // log10 of the candidates
+  float lg[FR3D_MAX_ALPHAS];      // log10 of the candidates
 };
 
 // band of the half-spectrum bin (kx, ky)
@@ -221,63 +222,110 @@ __device__ __forceinline__ int bin_band(const unsigned char* __restrict__ cband,
   return nb > 1 ? (int)__ldg(cband + class_of(kx, ky, n)) : 0;
 }
 
-// red[b][0] = sum over the block's threads of red[b][t] (fixed order)
-__device__ void tree_reduce(double (*red)[kLearnedThreads], int nb, int tid) {
-  for (int s = kLearnedThreads / 2; s > 0; s >>= 1) {
-    if (tid < s)
-      for (int b = 0; b < nb; ++b) red[b][tid] += red[b][tid + s];
-    __syncthreads();
+// sum over the block's threads of red[b][t] for every band b < nb, into tot[b] (fixed order: a
+// butterfly within each warp, then the warp totals in warp order); ends with a barrier
+__device__ void block_band_sum(float (*red)[kLearnedThreads], float (*wsum)[kLearnedThreads / 32], int nb,
+                               float* tot, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  __syncthreads();
+  for (int b = 0; b < nb; ++b) {
+    float v = red[b][tid];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    if (lane == 0) wsum[b][warp] = v;
   }
+  __syncthreads();
+  if (tid < nb) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < kLearnedThreads / 32; ++w) s += wsum[tid][w];
+    tot[tid] = s;
+  }
+  __syncthreads();
+}
+
+// largest power of two <= v (v >= 1), capped at 32: lanes that share one output of a layer
+__device__ __forceinline__ int lanes_per_output(int v) {
+  int g = 1;
+  while (g * 2 <= v && g < 32) g *= 2;
+  return g;
+}
+
+// out[u] = act(b[u] + sum_i W[u][i] in[i]) for u < nout with G = lanes_per_output(256 / nout) adjacent
+// lanes per output (a butterfly over the G lanes finishes each sum); every thread reaches the barrier
+__device__ void dense_layer(const __nv_bfloat16* w, int wo, int bo, const float* in, int nin, float* out, int nout,
+                            bool act, int tid) {
+  const int G = lanes_per_output(kLearnedThreads / nout);
+  const int u = tid / G, g = tid % G;
+  float a = 0.f;
+  if (u < nout)
+    for (int i = g; i < nin; i += G) a = fmaf(bf(w, wo + u * nin + i), in[i], a);
+  for (int m = G / 2; m > 0; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
+  if (u < nout && g == 0) {
+    a += bf(w, bo + u);
+    out[u] = act ? tanhf(a) : a;
+  }
+  __syncthreads();
 }
 
 // Band power sums of the half spectrum Uh (nplanes planes of (n/2+1) x n bins, weights 1 on the kx = 0
 // and kx = n/2 rows, 2 elsewhere), block partials, and in the last block: the network input x_b = f_b / 4
-// (to feat, if given), and with a network the per-band candidate indices.  info (if given) receives FR3D_INFO_NONFINITE and
-// FR3D_INFO_LEARNED_OUT_OF_RANGE bits.
+// (to feat, if given), and with a network the per-band candidate indices.  info (if given) receives
+// FR3D_INFO_NONFINITE and FR3D_INFO_LEARNED_OUT_OF_RANGE bits.
+// Everything is FP32: every sum is pairwise (a few bins per thread, then butterflies over lanes, warps
+// and blocks), so its relative error stays near 1e-6, far below what a log10 feature resolves, and the
+// serial tail of the last block runs on the FP32 pipe (FP64 is a small fraction of it on this GPU).
 __global__ void __launch_bounds__(kLearnedThreads) k_learned_alpha(
-    const float4* __restrict__ Uh4, long n4, long ps2, int n, const unsigned char* __restrict__ cband, int nb,
-    BandConst bc, double delta2, double* __restrict__ partials, unsigned* __restrict__ counter,
-    float* __restrict__ feat, const __nv_bfloat16* __restrict__ w, int nh, AlphaLog al, int na,
-    int* __restrict__ aidx, int* __restrict__ info) {
-  __shared__ union {
-    double red[FR3D_MAX_BANDS][kLearnedThreads];
-    __nv_bfloat16 w[FR3D_MAX_BANDS * kLearnedThreads * 4];
+    const float4* __restrict__ Uh4, int n4, int ps2, int n, const unsigned char* __restrict__ cband, int nb,
+    BandConst bc, float* __restrict__ partials, unsigned* __restrict__ counter, float* __restrict__ feat,
+    const __nv_bfloat16* __restrict__ w, int nh, AlphaLog al, int na, int* __restrict__ aidx,
+    int* __restrict__ info) {
+  __shared__ __align__(16) union {
+    float red[FR3D_MAX_BANDS][kLearnedThreads];
+    __nv_bfloat16 w[kMaxParams];
+    uint4 w16[(kMaxParams + 7) / 8];
   } sm;
-  __shared__ float x[FR3D_MAX_BANDS], h1[kMaxHidden], h2[kMaxHidden];
+  __shared__ float wsum[FR3D_MAX_BANDS][kLearnedThreads / 32];
+  __shared__ float tot[FR3D_MAX_BANDS], x[FR3D_MAX_BANDS], h1[kMaxHidden], h2[kMaxHidden], y[FR3D_MAX_BANDS];
   __shared__ int flags;
   __shared__ bool last;
-  const int tid = threadIdx.x;
-  for (int b = 0; b < nb; ++b) sm.red[b][tid] = 0.0;
-  for (long e4 = (long)blockIdx.x * kLearnedThreads + tid; e4 < n4; e4 += (long)gridDim.x * kLearnedThreads) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int b = 0; b < nb; ++b) sm.red[b][tid] = 0.f;
+  for (int e4 = blockIdx.x * kLearnedThreads + tid; e4 < n4; e4 += gridDim.x * kLearnedThreads) {
     const float4 u = __ldg(Uh4 + e4);
-    const int e = (int)(e4 % ps2) * 2;            // bin of u.x, u.y; u.z, u.w is bin e + 1 (same row)
+    const int e = (e4 % ps2) * 2;                 // bin of u.x, u.y; u.z, u.w is bin e + 1 (same row)
     const int kx = e / n, ky = e % n;
-    const double wt = (kx == 0 || 2 * kx == n) ? 1.0 : 2.0;
-    sm.red[bin_band(cband, nb, kx, ky, n)][tid] += wt * ((double)u.x * u.x + (double)u.y * u.y);
-    sm.red[bin_band(cband, nb, kx, ky + 1, n)][tid] += wt * ((double)u.z * u.z + (double)u.w * u.w);
+    const float wt = (kx == 0 || 2 * kx == n) ? 1.f : 2.f;
+    sm.red[bin_band(cband, nb, kx, ky, n)][tid] += wt * fmaf(u.x, u.x, u.y * u.y);
+    sm.red[bin_band(cband, nb, kx, ky + 1, n)][tid] += wt * fmaf(u.z, u.z, u.w * u.w);
   }
-  __syncthreads();
-  tree_reduce(sm.red, nb, tid);
-  if (tid < nb) partials[(long)blockIdx.x * nb + tid] = sm.red[tid][0];
+  block_band_sum(sm.red, wsum, nb, tot, tid);
+  if (tid < nb) partials[blockIdx.x * nb + tid] = tot[tid];
   __threadfence();
   __syncthreads();
   if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int b = 0; b < nb; ++b) {
-    double s = 0.0;
-    for (int blk = tid; blk < (int)gridDim.x; blk += kLearnedThreads) s += __ldcg(partials + (long)blk * nb + b);
-    sm.red[b][tid] = s;
+  {
+    // the partials of blocks tid and tid + 256 (the grid has at most 2 * 256 blocks), all loads in flight
+    float v0[FR3D_MAX_BANDS], v1[FR3D_MAX_BANDS];
+    const int g = (int)gridDim.x;
+#pragma unroll
+    for (int b = 0; b < FR3D_MAX_BANDS; ++b) {
+      v0[b] = (b < nb && tid < g) ? __ldcg(partials + tid * nb + b) : 0.f;
+      v1[b] = (b < nb && tid + kLearnedThreads < g) ? __ldcg(partials + (tid + kLearnedThreads) * nb + b) : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < FR3D_MAX_BANDS; ++b)
+      if (b < nb) sm.red[b][tid] = v0[b] + v1[b];
   }
   if (tid == 0) flags = 0;
-  __syncthreads();
-  tree_reduce(sm.red, nb, tid);
+  block_band_sum(sm.red, wsum, nb, tot, tid);
   if (tid < nb) {
-    const double s = sm.red[tid][0];
+    const float s = tot[tid];
     if (!isfinite(s)) atomicOr(&flags, FR3D_INFO_NONFINITE);
-    const float f = (float)log10(fmax(s, 1e-300) / (bc.count[tid] * delta2));
-    x[tid] = f * kFeatScale;
+    x[tid] = (log10f(fmaxf(s, 1e-37f)) - bc.lc[tid]) * kFeatScale;
     if (feat) feat[tid] = x[tid];
   }
   if (tid == 0) *counter = 0u;
@@ -286,47 +334,56 @@ __global__ void __launch_bounds__(kLearnedThreads) k_learned_alpha(
     if (tid == 0 && info) *info = flags;
     return;
   }
-  // network: weights staged in shared memory (over the reduction buffer)
+  // network: weights staged in shared memory (over the reduction buffer), then three layers
   const Off o = offsets(nb, nh, nb);
-  for (int i = tid; i < o.np; i += kLearnedThreads) sm.w[i] = w[i];
-  __syncthreads();
-  // row u of a weight matrix is read starting at column u (mod width): no shared-memory bank conflicts
-  if (tid < nh) {
-    float a = bf(sm.w, o.b1 + tid);
-    for (int j = 0; j < nb; ++j) {
-      const int i = (j + tid) % nb;
-      a = fmaf(bf(sm.w, o.w1 + tid * nb + i), x[i], a);
+  {
+    // 16-byte pieces, all loads of a thread in flight before the stores (the allocation is 256-byte
+    // aligned; the last partial piece is copied element by element)
+    constexpr int kPer = ((kMaxParams + 7) / 8 + kLearnedThreads - 1) / kLearnedThreads;
+    const int n16 = o.np / 8;
+    const uint4* w16 = reinterpret_cast<const uint4*>(w);
+    uint4 v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + i * kLearnedThreads;
+      if (e < n16) v[i] = __ldg(w16 + e);
     }
-    h1[tid] = tanhf(a);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + i * kLearnedThreads;
+      if (e < n16) sm.w16[e] = v[i];
+    }
+    for (int i = n16 * 8 + tid; i < o.np; i += kLearnedThreads) sm.w[i] = w[i];
   }
   __syncthreads();
-  if (tid < nh) {
-    float a = bf(sm.w, o.b2 + tid);
-    for (int j = 0; j < nh; ++j) {
-      const int i = (j + tid) % nh;
-      a = fmaf(bf(sm.w, o.w2 + tid * nh + i), h1[i], a);
-    }
-    h2[tid] = tanhf(a);
-  }
-  __syncthreads();
-  if (tid < nb) {
-    float a = bf(sm.w, o.b3 + tid);
-    for (int j = 0; j < nh; ++j) {
-      const int i = (j + tid) % nh;
-      a = fmaf(bf(sm.w, o.w3 + tid * nh + i), h2[i], a);
-    }
-    const double la = (double)a * kLogScale - kLogShift;
-    int best = 0;
-    double bd = fabs(al.lg[0] - la);
-    for (int k = 1; k < na; ++k) {
-      const double d = fabs(al.lg[k] - la);
+  dense_layer(sm.w, o.w1, o.b1, x, nb, h1, nh, true, tid);
+  dense_layer(sm.w, o.w2, o.b2, h1, nh, h2, nh, true, tid);
+  dense_layer(sm.w, o.w3, o.b3, h2, nh, y, nb, false, tid);
+  // nearest candidate in log10 alpha, one warp per band (ties: the smaller index)
+  for (int b = warp; b < nb; b += kLearnedThreads / 32) {
+    const float la = y[b] * kLogScale - kLogShift;
+    float bd = 3.4e38f;
+    int best = 0x7fffffff;
+    for (int k = lane; k < na; k += 32) {
+      const float d = fabsf(al.lg[k] - la);
       if (d < bd) {
         bd = d;
         best = k;
       }
     }
-    aidx[tid] = best;
-    if (!(la >= al.lg[0] - 0.5 && la <= al.lg[na - 1] + 0.5)) atomicOr(&flags, FR3D_INFO_LEARNED_OUT_OF_RANGE);
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, bd, m);
+      const int ok = __shfl_xor_sync(0xffffffffu, best, m);
+      if (od < bd || (od == bd && ok < best)) {
+        bd = od;
+        best = ok;
+      }
+    }
+    if (lane == 0) {
+      aidx[b] = best;
+      if (!(la >= al.lg[0] - 0.5f && la <= al.lg[na - 1] + 0.5f)) atomicOr(&flags, FR3D_INFO_LEARNED_OUT_OF_RANGE);
+    }
   }
   __syncthreads();
   if (tid == 0 && info) *info = flags;
@@ -455,16 +512,18 @@ int learned_alpha(Handle* H, const float2* Uh, int nplanes, int nb, double delta
   FR3D_TRY(ensure_bands(H, nb, &count));
   FR3D_TRY(ensure_partials(H));
   BandConst bc;
-  for (int b = 0; b < nb; ++b) bc.count[b] = count[b];
+  for (int b = 0; b < nb; ++b) bc.lc[b] = (float)log10(count[b] * delta * delta);
   AlphaLog al;
-  for (int k = 0; k < na; ++k) al.lg[k] = log10(alphas[k]);
+  for (int k = 0; k < na; ++k) al.lg[k] = (float)log10(alphas[k]);
   const long ps2 = (long)(H->n / 2 + 1) * H->n / 2;
   const long n4 = ps2 * nplanes;
+  if (n4 > 0x7fffffffL) return FR3D_ERR_UNSUPPORTED_SIZE;
   long blocks = (n4 + 2 * kLearnedThreads - 1) / (2 * kLearnedThreads);
-  blocks = std::max(1L, std::min(blocks, 2L * 152));
+  blocks = std::max(1L, std::min(blocks, 2L * 152));   // at most 2 * kLearnedThreads (the last block's loads)
   k_learned_alpha<<<(int)blocks, kLearnedThreads, 0, st>>>(
-      reinterpret_cast<const float4*>(Uh), n4, ps2, H->n, H->cband, nb, bc, delta * delta, H->partials, H->counter,
-      feat, net ? net->m.w : nullptr, net ? net->m.nh : 0, al, na, aidx, info);
+      reinterpret_cast<const float4*>(Uh), (int)n4, (int)ps2, H->n, H->cband, nb, bc,
+      reinterpret_cast<float*>(H->partials), H->counter, feat, net ? net->m.w : nullptr, net ? net->m.nh : 0, al,
+      na, aidx, info);
   FR3D_CUDA_TRY(cudaGetLastError());
   return FR3D_OK;
 }

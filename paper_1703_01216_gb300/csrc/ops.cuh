@@ -58,6 +58,9 @@ bool learned_net_fits(const fr3d_mlp* net, int nb);
 int learned_alpha(Handle* H, const float2* Uh, int nplanes, int nb, double delta, const double* alphas, int na,
                   const fr3d_mlp* net, int* aidx, float* feat, int* info, cudaStream_t st);
 
+// per-band calls: the solve-weight table of every bin's band alpha (Dd32 rows selected by aidx) into dsel32
+int band_select_f32(Handle* H, const int* aidx, cudaStream_t st);
+
 // precision-independent table builders (alpha tables, fixed alpha)
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st);
 int fixed_table(Handle* H, double alpha, cudaStream_t st);

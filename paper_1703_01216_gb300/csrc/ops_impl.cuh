@@ -1,6 +1,8 @@
 // Per-precision kernel launchers (included once per precision by ops_f32.cu / ops_f64.cu).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "fft2d.cuh"
@@ -233,16 +235,26 @@ __device__ __forceinline__ double sq_abs(double2 v) { return fma(v.x, v.x, v.y *
 
 constexpr int kAlphaCPB = 64;  // classes per block
 constexpr int kAlphaSplit = 4; // threads per class in the power gather
+constexpr int kAlphaCluster = 8; // blocks per cluster (the grid is padded to a multiple)
 
 // Per band b of frequency classes (one band: the whole spectrum),
 //   r_b^2(alpha_k) = n^-2 sum_{c in b} Ft[c][k] P[c]  (Parseval; M = 1 closed form of the residual),
 // with P[c] the data power of class c: every stored half-spectrum bin of the class, weighted 1 on
 // the kx = 0 and kx = n/2 columns and 2 elsewhere (their mirror bins are not stored), summed over
 // planes.  The discrepancy rule picks, per band, the largest alpha_k with r_b^2 <= thr2.t[b].
-// Deterministic: fixed-order partial sums per block, reduced by the last block to finish.
+// Deterministic: fixed-order partial sums per block, per cluster of kAlphaCluster blocks (through
+// distributed shared memory), and over clusters by the last block to finish.  FP64 runs at a small
+// fraction of the FP32 rate on this GPU, so the serial parts avoid FP64 chains: the choice is a warp
+// ballot per band rather than a loop over candidates.
 struct BandThr {
   double t[FR3D_MAX_BANDS];
 };
+
+// blocks of the alpha rule for Cn classes: one per kAlphaCPB classes, padded to whole clusters
+inline int alpha_blocks(int Cn) {
+  const int b = (Cn + kAlphaCPB - 1) / kAlphaCPB;
+  return (b + kAlphaCluster - 1) / kAlphaCluster * kAlphaCluster;
+}
 
 template <typename C>
 __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
@@ -251,16 +263,23 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
                                                   double* __restrict__ partials, unsigned* __restrict__ counter,
                                                   int* __restrict__ aidx, double* __restrict__ res_out,
                                                   int* __restrict__ info, int blk, int nblk) {
+  // Accumulation types: the class power P[c] is summed in the data's precision (at most 4 nplanes
+  // positive terms); the residual sums F[c][k] P[c] over classes and blocks are FP64.
+  using A = typename std::conditional<std::is_same<C, float2>::value, float, double>::type;
+  namespace cg = cooperative_groups;
   __shared__ double sP[kAlphaCPB];
   __shared__ unsigned char sB[kAlphaCPB];
   __shared__ int present[FR3D_MAX_BANDS];
   __shared__ double red[256];
+  __shared__ double sPart[FR3D_MAX_BANDS * FR3D_MAX_ALPHAS];   // this block's sums; later the r^2 curves
+  __shared__ int flg[FR3D_MAX_BANDS];
   __shared__ bool last;
   extern __shared__ double sF[];             // [kAlphaCPB][na] slab of Ft for this block's classes
   const int tid = threadIdx.x;
   const int c0 = blk * kAlphaCPB;
-  const int nF = min(kAlphaCPB, Cn - c0) * na;
+  const int nF = max(0, min(kAlphaCPB, Cn - c0)) * na;
   const double* slab = Ft + (long)c0 * na;
+  const int O = nb * na;
   if (tid < FR3D_MAX_BANDS) present[tid] = 0;
   // one round of global loads: this thread's share of the class powers and of the filter slab
   const int cl = tid / kAlphaSplit, sub = tid % kAlphaSplit, c = c0 + cl;
@@ -282,20 +301,24 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
     const int e = tid + i * 256;
     f[i] = e < nF ? __ldg(slab + e) : 0.0;
   }
-  double acc = 0.0;
+  A acc = 0;
   for (int pl0 = sub; pl0 < nplanes; pl0 += 2 * kAlphaSplit) {
-    double s[4][2];
+    A s[4][2];
 #pragma unroll
     for (int mi = 0; mi < 4; ++mi)
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int pl = pl0 + u * kAlphaSplit;
-        s[mi][u] = (mi < nm && pl < nplanes) ? sq_abs(__ldg(Uh + pl * ps + (long)kxs[mi] * n + kys[mi])) : 0.0;
+        const C v = (mi < nm && pl < nplanes) ? __ldg(Uh + pl * ps + (long)kxs[mi] * n + kys[mi]) : C{0, 0};
+        s[mi][u] = v.x * v.x + v.y * v.y;
       }
 #pragma unroll
     for (int mi = 0; mi < 4; ++mi)
-      if (mi < nm) acc = fma((kxs[mi] == 0 || 2 * kxs[mi] == n) ? 1.0 : 2.0, s[mi][0] + s[mi][1], acc);
+      if (mi < nm) acc += ((kxs[mi] == 0 || 2 * kxs[mi] == n) ? A(1) : A(2)) * (s[mi][0] + s[mi][1]);
   }
+  // the kAlphaSplit threads of a class are adjacent lanes: combine them in a fixed order
+#pragma unroll
+  for (int m = 1; m < kAlphaSplit; m <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     const int e = tid + i * 256;
@@ -303,27 +326,22 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
   }
   // slabs longer than 16 loads per thread (more than 64 candidates) finish here
   for (int e = tid + 16 * 256; e < nF; e += 256) sF[e] = __ldg(slab + e);
-  red[tid] = acc;
-  __syncthreads();
-  if (tid < kAlphaCPB) {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < kAlphaSplit; ++k) s += red[tid * kAlphaSplit + k];
-    sP[tid] = s;
-    const int b = (c0 + tid < Cn && nb > 1) ? (int)cband[c0 + tid] : 0;
-    sB[tid] = (unsigned char)b;
-    if (c0 + tid < Cn) present[b] = 1;
+  if (sub == 0) {
+    sP[cl] = (double)acc;
+    const int b = (c < Cn && nb > 1) ? (int)cband[c] : 0;
+    sB[cl] = (unsigned char)b;
+    if (c < Cn) present[b] = 1;
   }
   __syncthreads();
+  // per band: this block's sums of F[c][k] P[c] (S threads per candidate, fixed order)
   const int S = 256 / na;
   for (int b = 0; b < nb; ++b) {
     if (present[b]) {
       if (tid < S * na) {
         const int k = tid % na, sb = tid / na;
         double a2 = 0.0;
-        for (int cc = sb; cc < kAlphaCPB; cc += S) {
+        for (int cc = sb; cc < kAlphaCPB; cc += S)
           if (c0 + cc < Cn && sB[cc] == b) a2 = fma(sF[cc * na + k], sP[cc], a2);
-        }
         red[tid] = a2;
       }
       __syncthreads();
@@ -332,56 +350,64 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
       double s = 0.0;
       if (present[b])
         for (int sb = 0; sb < S; ++sb) s += red[sb * na + tid];
-      partials[((long)blk * nb + b) * na + tid] = s;
+      sPart[b * na + tid] = s;
     }
     __syncthreads();
   }
+  // cluster of kAlphaCluster consecutive blocks: block r adds output o = r, r + CL, ... over the
+  // cluster's blocks (distributed shared memory, rank order) and stores the cluster's partial
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster.sync();
+  {
+    const int r = (int)cluster.block_rank();
+    const int cid = blk / kAlphaCluster;
+    for (int o = r + tid * kAlphaCluster; o < O; o += 256 * kAlphaCluster) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < kAlphaCluster; ++q) s += *cluster.map_shared_rank(sPart + o, (unsigned)q);
+      partials[(long)cid * O + o] = s;
+    }
+  }
+  cluster.sync();                            // no block leaves while its shared memory is read
   __threadfence();
   __syncthreads();
   if (tid == 0) last = atomicAdd(counter, 1u) == (unsigned)(nblk - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  __shared__ double r2[FR3D_MAX_BANDS * FR3D_MAX_ALPHAS];
-  // output o = (b, k): T threads per output each sum every T-th block's partial (16 loads in flight
-  // per round), then the T sums are added in a fixed order
-  const int O = nb * na;
-  const int T = O >= 256 ? 1 : 256 / O;
-  for (int o0 = 0; o0 < O; o0 += 256 / T) {
-    const int o = o0 + tid % (256 / T), sb = tid / (256 / T);
+  // the last block: r^2 per (band, candidate) over the cluster partials (8 loads in flight per round)
+  const int ncl = nblk / kAlphaCluster;
+  for (int o = tid; o < O; o += 256) {
     double s = 0.0;
-    if (o < O && sb < T) {
-      for (int b0 = sb; b0 < nblk; b0 += 16 * T) {
-        double v[16];
+    for (int g0 = 0; g0 < ncl; g0 += 8) {
+      double v[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int bb = b0 + i * T;
-          v[i] = bb < nblk ? __ldcg(partials + (long)bb * O + o) : 0.0;
-        }
+      for (int i = 0; i < 8; ++i) v[i] = g0 + i < ncl ? __ldcg(partials + (long)(g0 + i) * O + o) : 0.0;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) s += v[i];
-      }
+      for (int i = 0; i < 8; ++i) s += v[i];
     }
-    red[tid] = s;
-    __syncthreads();
-    if (tid < 256 / T && o0 + tid < O) {
-      double t = 0.0;
-      for (int sb2 = 0; sb2 < T; ++sb2) t += red[sb2 * (256 / T) + tid];
-      r2[o0 + tid] = t * inv_n2;
-      if (res_out) res_out[o0 + tid] = t * inv_n2;
-    }
-    __syncthreads();
+    s *= inv_n2;
+    sPart[o] = s;
+    if (res_out) res_out[o] = s;
   }
-  __shared__ int flg[FR3D_MAX_BANDS];
-  if (tid < nb) {
-    int best = -1, flags = 0, ok = 0;
-    for (int k = 0; k < na; ++k) {
-      const double v = r2[tid * na + k];
-      if (!isfinite(v)) flags |= FR3D_INFO_NONFINITE;
-      if (v <= thr2.t[tid]) {
-        best = k;
-        ++ok;
+  __syncthreads();
+  // choice per band, one warp per band: ballots of r^2 <= thr over the candidates, largest index wins
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int b = warp; b < nb; b += 8) {
+    int best = -1, ok = 0, flags = 0;
+    for (int k0 = 0; k0 < na; k0 += 32) {
+      const int k = k0 + lane;
+      bool good = false, bad = false;
+      if (k < na) {
+        const double v = sPart[b * na + k];
+        const long long bits = __double_as_longlong(v);
+        bad = ((bits >> 52) & 0x7ff) == 0x7ff;      // Inf or NaN
+        good = v <= thr2.t[b];
       }
+      const unsigned bg = __ballot_sync(0xffffffffu, good);
+      if (__ballot_sync(0xffffffffu, bad)) flags |= FR3D_INFO_NONFINITE;
+      if (bg) best = k0 + 31 - __clz(bg);
+      ok += __popc(bg);
     }
     if (best < 0) {
       best = 0;
@@ -389,8 +415,10 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
     } else if (ok == na) {
       flags |= FR3D_INFO_ALPHA_ALL_SATISFY;
     }
-    aidx[tid] = best;
-    flg[tid] = flags;
+    if (lane == 0) {
+      aidx[b] = best;
+      flg[b] = flags;
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -402,7 +430,7 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
 }
 
 template <typename C>
-__global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
+__global__ void __cluster_dims__(kAlphaCluster, 1, 1) __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
                                                       const double* __restrict__ Ft, int na, BandThr thr2,
                                                       const unsigned char* __restrict__ cband, int nb, double inv_n2,
                                                       double* __restrict__ partials, unsigned* __restrict__ counter,
@@ -415,7 +443,7 @@ __global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, 
 template <typename T>
 int Ops<T>::alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, const double* thr2, int nb, int* aidx,
                          double* residuals, int* info, cudaStream_t st) {
-  const int blocks = (H->C + kAlphaCPB - 1) / kAlphaCPB;
+  const int blocks = alpha_blocks(H->C);
   FR3D_TRY(ensure_partials(H));
   const long ps = (long)(H->n / 2 + 1) * H->n;
   const size_t sm = sizeof(double) * kAlphaCPB * n_alpha;

@@ -44,7 +44,24 @@ __global__ void k_dense_d(const float* __restrict__ D, int na, int Cn, int n, fl
   }
 }
 
+// Dsel[o] = Dd[aidx[band(o)]][o] for every half-spectrum bin o = kx n + ky
+__global__ void k_band_select(const float* __restrict__ Dd, const int* __restrict__ aidx,
+                              const unsigned char* __restrict__ cband, int n, int ps, float* __restrict__ Dsel) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= ps) return;
+  const int b = cband[class_of(o / n, o % n, n)];
+  Dsel[o] = __ldg(Dd + (long)__ldg(aidx + b) * ps + o);
+}
+
 }  // namespace
+
+int band_select_f32(Handle* H, const int* aidx, cudaStream_t st) {
+  const int ps = (H->n / 2 + 1) * H->n;
+  if (!H->dsel32) FR3D_CUDA_TRY(cudaMalloc(&H->dsel32, sizeof(float) * ps));
+  k_band_select<<<(ps + 255) / 256, 256, 0, st>>>(H->Dd32, aidx, H->cband, H->n, ps, H->dsel32);
+  FR3D_CUDA_TRY(cudaGetLastError());
+  return FR3D_OK;
+}
 
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) {
   if ((int)H->alpha_key.size() == n_alpha && memcmp(H->alpha_key.data(), alphas, n_alpha * sizeof(double)) == 0)

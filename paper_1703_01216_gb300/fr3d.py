@@ -267,7 +267,7 @@ def last_launch_count(handle: Handle) -> int:
 
 
 STAGE_NAMES = ("row_r2c", "col_fwd", "alpha", "col_solve", "row_c2r", "table", "contract", "col_inv", "other",
-               "inv_fused")
+               "inv_fused", "band_select")
 
 
 def profile_enable(handle: Handle, enable: bool = True):

@@ -1,6 +1,6 @@
 """GPU parity and gain of the learned per-band alpha rule, through the C ABI, against the FP64 oracle.
 
-Tolerances: band features 2e-5 absolute in log10 (FP32 spectra, FP64 sums); error curves 1e-5
+Tolerances: band features 2e-5 absolute in log10 (FP32 spectra and pairwise FP32 sums); error curves 1e-5
 relative plus a floor of 1e-12 of the total zeta energy (FP32 spectra of the data and of zeta, FP64
 sums); network output 2e-5 and gradient 1e-4
 relative (BF16 weights on both sides, FP32 arithmetic against FP64); Adam step 1e-6 absolute;
