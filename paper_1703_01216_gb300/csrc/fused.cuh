@@ -31,26 +31,30 @@ namespace fr3d {
 
 namespace cg = cooperative_groups;
 
-// Split cluster barrier: arrive without ordering memory (the caller's reads of peer shared memory
-// have completed: their values were consumed) and wait later.
+// Split cluster barrier: arrive without ordering memory and wait later.  The caller arrives only after
+// it has consumed every value it read from peer shared memory, so those reads are complete.
 __device__ __forceinline__ void cluster_arrive_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 
+// CL: CTAs per cluster (above 8 a non-portable cluster size), NT: threads, RB: rows per row batch,
+// MINB: resident CTAs per SM that the register budget is sized for; GACC: accumulate xi in the output
+// array (L2-resident read-modify-write) instead of shared memory
+struct FusedCfgBase {
+  static constexpr bool GACC = false;
+};
 template <int N> struct FusedCfg;
-// CL: CTAs per cluster, NT: threads, RB: rows per row batch, MINB: resident CTAs per SM that the
-// register budget is sized for
-template <> struct FusedCfg<16> { static constexpr int CL = 1, NT = 128, RB = 16, MINB = 4; };
-template <> struct FusedCfg<24> { static constexpr int CL = 1, NT = 96, RB = 24, MINB = 4; };
-template <> struct FusedCfg<32> { static constexpr int CL = 1, NT = 128, RB = 32, MINB = 4; };
-template <> struct FusedCfg<48> { static constexpr int CL = 1, NT = 128, RB = 48, MINB = 3; };
-template <> struct FusedCfg<64> { static constexpr int CL = 2, NT = 256, RB = 32, MINB = 2; };
-template <> struct FusedCfg<96> { static constexpr int CL = 2, NT = 256, RB = 48, MINB = 2; };
-template <> struct FusedCfg<128> { static constexpr int CL = 4, NT = 256, RB = 32, MINB = 2; };
-template <> struct FusedCfg<192> { static constexpr int CL = 4, NT = 256, RB = 16, MINB = 2; };
-template <> struct FusedCfg<256> { static constexpr int CL = 8, NT = 256, RB = 16, MINB = 2; };
-template <> struct FusedCfg<384> { static constexpr int CL = 8, NT = 512, RB = 16, MINB = 1; };
+template <> struct FusedCfg<16> : FusedCfgBase { static constexpr int CL = 1, NT = 128, RB = 16, MINB = 4; };
+template <> struct FusedCfg<24> : FusedCfgBase { static constexpr int CL = 1, NT = 96, RB = 24, MINB = 4; };
+template <> struct FusedCfg<32> : FusedCfgBase { static constexpr int CL = 1, NT = 128, RB = 32, MINB = 4; };
+template <> struct FusedCfg<48> : FusedCfgBase { static constexpr int CL = 1, NT = 128, RB = 48, MINB = 3; };
+template <> struct FusedCfg<64> : FusedCfgBase { static constexpr int CL = 2, NT = 256, RB = 32, MINB = 2; };
+template <> struct FusedCfg<96> : FusedCfgBase { static constexpr int CL = 2, NT = 256, RB = 48, MINB = 2; };
+template <> struct FusedCfg<128> : FusedCfgBase { static constexpr int CL = 4, NT = 256, RB = 32, MINB = 2; };
+template <> struct FusedCfg<192> : FusedCfgBase { static constexpr int CL = 4, NT = 256, RB = 16, MINB = 2; };
+template <> struct FusedCfg<256> : FusedCfgBase { static constexpr int CL = 8, NT = 256, RB = 16, MINB = 2; };
+template <> struct FusedCfg<384> : FusedCfgBase { static constexpr int CL = 8, NT = 512, RB = 16, MINB = 1; };
 
 template <int N> struct FusedGeom {
   using Cf = FusedCfg<N>;
@@ -68,7 +72,7 @@ template <int N> struct FusedGeom {
   static constexpr int PTC = passtw_size<N>(), PTR = passtw_size<L>();
   static constexpr size_t smem_zeta = sizeof(float2) * ((size_t)CPC * SSC + (size_t)RB * SSR + N + PTC + PTR) +
                                       sizeof(float) * (size_t)(CPC + 1) * N;
-  static constexpr size_t smem_xi = smem_zeta + sizeof(float) * (size_t)NRW * N;
+  static constexpr size_t smem_xi = smem_zeta + (Cf::GACC ? 0 : sizeof(float) * (size_t)NRW * N);
   static_assert(L % CL == 0, "column split");
   static_assert(NRW % RB == 0, "row batches");
   static_assert((RB * L) % NT == 0, "outputs per thread");
@@ -216,8 +220,6 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
           xb[i] = xat(L - k, y);
         }
       }
-      if constexpr (CL > 1)
-        if (b == NB - 1) cluster_arrive_relaxed();   // last reads of peer columns for this q
 #pragma unroll
       for (int i = 0; i < SIT; ++i) {
         const int e = tid + i * NT;
@@ -234,15 +236,22 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
           }
         }
       }
+      // every value read from the peers' columns for this q has been consumed above (the loads are
+      // complete), so the arrival needs no memory ordering; the peers wait on it before they overwrite
+      // their columns (next q) or exit
+      if constexpr (CL > 1)
+        if (b == NB - 1) cluster_arrive_relaxed();
       __syncthreads();
       fft_smem<L, true, RB, NT>(rowbuf, SSR, ptr, tid);
       if constexpr (MODE == 1) {
+        float2* acb = accs + b * RB * L;
+        if constexpr (G::Cf::GACC) acb = reinterpret_cast<float2*>(a.out + ((long)j * N + y0 + b * RB) * N);
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
           const int e = tid + i * NT;
           const int row = e / L, mm = e % L;
           const float2 v = rowbuf[row * SSR + pidx<float2>(mm)];
-          float2* ac = accs + b * RB * L + e;
+          float2* ac = acb + e;
           const float2 prev = q == 0 ? make_float2(0.f, 0.f) : *ac;
           *ac = make_float2(fmaf(wv[i].x, v.x, prev.x), fmaf(wv[i].y, v.y, prev.y));
         }
@@ -260,7 +269,7 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   }
   // no CTA leaves while a peer may still read its shared memory
   if constexpr (CL > 1) cluster_wait();
-  if constexpr (MODE == 1) {
+  if constexpr (MODE == 1 && !G::Cf::GACC) {
     // xi of the owned rows; the last barrier of the q loop ordered every accumulator write first
     float2* ov = reinterpret_cast<float2*>(a.out + ((long)j * N + y0) * N);
 #pragma unroll 4
@@ -268,15 +277,15 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   }
 }
 
+// Both kernels are launched with a cluster dimension of FusedCfg<N>::CL (launch_clustered).
 template <int N, int MODE>
-__global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
-    k_inv_fused(FusedArgs a) {
+__global__ void __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB) k_inv_fused(FusedArgs a) {
   inv_fused_body<N, MODE>(a, (int)blockIdx.x / FusedCfg<N>::CL);
 }
 
 // Batched instances of one grid size n: cluster c handles depth map[c].y of instance map[c].x.
 template <int N, int MODE>
-__global__ void __cluster_dims__(FusedCfg<N>::CL, 1, 1) __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
+__global__ void __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
     k_inv_fused_batched(const FusedArgs* __restrict__ inst, const int2* __restrict__ map) {
   const int2 m = map[blockIdx.x / FusedCfg<N>::CL];
   const FusedArgs a = inst[m.x];

@@ -24,14 +24,39 @@ __global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, d
 
 namespace {
 
+// Launch `kern` on `clusters` clusters of CL CTAs (a runtime cluster dimension; sizes above the
+// portable 8 are allowed once per kernel, on the first launch, which happens outside any capture).
+template <int CL, class K, class... Args>
+int launch_clustered(K kern, int clusters, int nt, size_t sm, cudaStream_t st, Args... args) {
+  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(kern), sm));
+  if constexpr (CL > 8) {
+    static bool allowed = false;
+    if (!allowed) {
+      FR3D_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      allowed = true;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * CL);
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FR3D_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args...));
+  return FR3D_OK;
+}
+
 template <int N, int MODE>
 int launch_fused(const Handle* H, const FusedArgs& a, int nj, cudaStream_t st) {
   using G = FusedGeom<N>;
-  auto kern = k_inv_fused<N, MODE>;
   constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;
-  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(kern), sm));
-  kern<<<nj * G::CL, G::NT, sm, st>>>(a);
-  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+  return launch_clustered<G::CL>(k_inv_fused<N, MODE>, nj, G::NT, sm, st, a);
 }
 
 }  // namespace
@@ -73,11 +98,8 @@ namespace {
 template <int N, int MODE>
 int launch_fused_batched(const FusedArgs* inst, const int2* map, int nclusters, cudaStream_t st) {
   using G = FusedGeom<N>;
-  auto kern = k_inv_fused_batched<N, MODE>;
   constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;
-  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(kern), sm));
-  kern<<<nclusters * G::CL, G::NT, sm, st>>>(inst, map);
-  return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
+  return launch_clustered<G::CL>(k_inv_fused_batched<N, MODE>, nclusters, G::NT, sm, st, inst, map);
 }
 }  // namespace
 
