@@ -240,6 +240,93 @@ __device__ __forceinline__ void stockham_pass(C* buf, int sstride, const C* __re
   __syncthreads();
 }
 
+// Pass 0 (NS = 1, no twiddles) fed from registers: element t of sequence s comes from ld(s, t) (for
+// example a global load) instead of shared memory, so the input never makes a shared-memory round trip.
+// Writes the pass's output to buf and synchronises.
+template <int L, bool INV, int NSEQ, int NTHR, class Ld, typename C>
+__device__ __forceinline__ void first_pass_from(C* buf, int sstride, Ld ld, int tid) {
+  constexpr int R = Plan<L>::radix(0);
+  constexpr int BPS = L / R;
+  constexpr int NB = NSEQ * BPS;
+  constexpr int K = (NB + NTHR - 1) / NTHR;
+  constexpr bool EXACT = (K * NTHR == NB);
+  C v[K][R];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int b = tid + k * NTHR;
+    if (EXACT || b < NB) {
+      const int s = b / BPS, j = b - s * BPS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[k][r] = ld(s, j + r * BPS);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int b = tid + k * NTHR;
+    if (EXACT || b < NB) {
+      const int s = b / BPS, j = b - s * BPS;
+      Dft<R, INV>::run(v[k]);
+      C* base = buf + s * sstride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[pidx<C>(j * R + r)] = v[k][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Geometry of the last pass of an L-point FFT: butterfly b = tid + k NTHR of NSEQ sequences owns the
+// outputs t = j + r NS (r < R) of sequence s = b / BPS, j = b mod BPS.
+template <int L> struct LastPass {
+  static constexpr int NP = Plan<L>::np;
+  static constexpr int R = Plan<L>::radix(NP - 1);
+  static constexpr int BPS = L / R;
+  static constexpr int NS = L / R;
+};
+
+// The last pass of an L-point FFT whose earlier passes are done (data in buf): the outputs go to
+// emit(s, t, value, k, r) instead of back to shared memory, so no barrier follows the reads.
+template <int L, bool INV, int NSEQ, int NTHR, class Em, typename C>
+__device__ __forceinline__ void last_pass_to(const C* buf, int sstride, const C* __restrict__ twp, Em emit, int tid) {
+  using LP = LastPass<L>;
+  constexpr int R = LP::R, BPS = LP::BPS, NS = LP::NS;
+  constexpr int NB = NSEQ * BPS;
+  constexpr int K = (NB + NTHR - 1) / NTHR;
+  constexpr bool EXACT = (K * NTHR == NB);
+  const C* tw = twp + passtw_offset<L>(LP::NP - 1);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int b = tid + k * NTHR;
+    if (EXACT || b < NB) {
+      const int s = b / BPS, j = b - s * BPS;
+      const C* base = buf + s * sstride;
+      C v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C x = base[pidx<C>(j + r * BPS)];
+        if (NS > 1 && r > 0) {
+          C w = tw[(r - 1) * NS + j];
+          if (INV) w = cconj(w);
+          x = cmul(x, w);
+        }
+        v[r] = x;
+      }
+      Dft<R, INV>::run(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) emit(s, j + r * NS, v[r], k, r);
+    }
+  }
+}
+
+// Passes P0 .. P1 - 1 of an L-point FFT (NS = product of the radices before P0).
+template <int L, bool INV, int NSEQ, int NTHR, int P0, int P1, int NS = 1, typename C>
+__device__ __forceinline__ void fft_passes(C* buf, int sstride, const C* __restrict__ twp, int tid) {
+  if constexpr (P0 < P1) {
+    constexpr int R = Plan<L>::radix(P0);
+    stockham_pass<L, R, NS, INV, NSEQ, NTHR>(buf, sstride, twp + passtw_offset<L>(P0), tid);
+    fft_passes<L, INV, NSEQ, NTHR, P0 + 1, P1, NS * R>(buf, sstride, twp, tid);
+  }
+}
+
 // All passes of an L-point FFT on NSEQ sequences (stride sstride); twp = pass tables of length L.
 template <int L, bool INV, int NSEQ, int NTHR, int P = 0, int NS = 1, typename C>
 __device__ __forceinline__ void fft_smem(C* buf, int sstride, const C* __restrict__ twp, int tid) {

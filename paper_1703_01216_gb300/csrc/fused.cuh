@@ -170,43 +170,43 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
     // the peers' reads of this CTA's columns for q - 1 are done (arrive below) before overwriting
     if constexpr (CL > 1)
       if (q > 0) cluster_wait();
-    // ---------------- column phase
-#pragma unroll
-    for (int b0 = 0; b0 < CLD; b0 += CB) {
-      float2 u[CB], un[CB];
-#pragma unroll
-      for (int i = 0; i < CB; ++i) {
-        const int e = tid + (b0 + i) * NT;
-        u[i] = __ldg(Zq + (long)c0 * N + e);
-        if (r == 0 && e < N) un[i] = __ldg(Zq + (long)L * N + e);
+    // ---------------- column phase: U~_q w_j loaded straight into the registers of the first pass of
+    // the inverse column DFTs (no shared-memory round trip for the input)
+    auto ldc = [&](int col, int ky) -> float2 {
+      const int e = col * N + ky;
+      const float2 u = __ldg(Zq + (long)c0 * N + e);
+      const float w = wsm[e];
+      float2 v = make_float2(u.x * w, u.y * w);
+      if (r == 0 && col == 0) {   // packed column 0: add i w(n/2, ky) U~(n/2, ky)
+        const float2 un = __ldg(Zq + (long)L * N + ky);
+        const float wl = wsm[CPC * N + ky];
+        v.x -= un.y * wl;
+        v.y += un.x * wl;
       }
-#pragma unroll
-      for (int i = 0; i < CB; ++i) {
-        const int e = tid + (b0 + i) * NT;
-        const int col = e / N, ky = e % N;
-        const float w = wsm[e];
-        float2 v = make_float2(u[i].x * w, u[i].y * w);
-        if (r == 0 && e < N) {   // packed column 0: add i * w(n/2, ky) U~(n/2, ky)
-          const float wl = wsm[CPC * N + e];
-          v.x -= un[i].y * wl;
-          v.y += un[i].x * wl;
-        }
-        colbuf[col * SSC + pidx<float2>(ky)] = v;
-      }
-    }
-    __syncthreads();
-    fft_smem<N, true, CPC, NT>(colbuf, SSC, ptc, tid);
+      return v;
+    };
+    first_pass_from<N, true, CPC, NT>(colbuf, SSC, ldc, tid);
+    fft_passes<N, true, CPC, NT, 1, Plan<N>::np, Plan<N>::radix(0)>(colbuf, SSC, ptc, tid);
     if constexpr (CL > 1) cg::this_cluster().sync();
     // ---------------- row phase
 #pragma unroll 1
     for (int b = 0; b < NB; ++b) {
-      // combination weights of this batch, requested now so that the HBM latency overlaps the
-      // split and the row transforms
-      float2 wv[EPT];
+      // combination weights of this batch in the layout of the last row pass (butterfly (row, jq) owns
+      // outputs jq + rr NS), requested now so that the HBM latency overlaps the split and the passes
+      using LPr = LastPass<L>;
+      constexpr int KR = (RB * LPr::BPS + NT - 1) / NT;
+      float2 wv[KR][LPr::R];
       if constexpr (MODE == 1) {
         const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + j) * N + y0 + b * RB) * N);
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) wv[i] = __ldg(wq + tid + i * NT);   // [row][mm] pairs of the batch
+        for (int k = 0; k < KR; ++k) {
+          const int bb = tid + k * NT;
+          if ((RB * LPr::BPS) % NT == 0 || bb < RB * LPr::BPS) {
+            const int sr = bb / LPr::BPS, jq = bb % LPr::BPS;
+#pragma unroll
+            for (int rr = 0; rr < LPr::R; ++rr) wv[k][rr] = __ldg(wq + sr * L + jq + rr * LPr::NS);
+          }
+        }
       }
       // Hermitian split Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), pairs (k, L - k)
       constexpr int SIT = (G::NSPL + NT - 1) / NT;
@@ -242,27 +242,20 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
       if constexpr (CL > 1)
         if (b == NB - 1) cluster_arrive_relaxed();
       __syncthreads();
-      fft_smem<L, true, RB, NT>(rowbuf, SSR, ptr, tid);
+      fft_passes<L, true, RB, NT, 0, Plan<L>::np - 1>(rowbuf, SSR, ptr, tid);
       if constexpr (MODE == 1) {
         float2* acb = accs + b * RB * L;
         if constexpr (G::Cf::GACC) acb = reinterpret_cast<float2*>(a.out + ((long)j * N + y0 + b * RB) * N);
-#pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-          const int e = tid + i * NT;
-          const int row = e / L, mm = e % L;
-          const float2 v = rowbuf[row * SSR + pidx<float2>(mm)];
-          float2* ac = acb + e;
+        auto emit = [&](int sr, int t, float2 v, int k, int rr) {
+          float2* ac = acb + sr * L + t;
           const float2 prev = q == 0 ? make_float2(0.f, 0.f) : *ac;
-          *ac = make_float2(fmaf(wv[i].x, v.x, prev.x), fmaf(wv[i].y, v.y, prev.y));
-        }
+          *ac = make_float2(fmaf(wv[k][rr].x, v.x, prev.x), fmaf(wv[k][rr].y, v.y, prev.y));
+        };
+        last_pass_to<L, true, RB, NT>(rowbuf, SSR, ptr, emit, tid);
       } else {
         float2* o = reinterpret_cast<float2*>(a.out + (((long)q * a.Mp + j) * N + y0 + b * RB) * N);
-#pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-          const int e = tid + i * NT;
-          const int row = e / L, mm = e % L;
-          o[e] = rowbuf[row * SSR + pidx<float2>(mm)];
-        }
+        auto emit = [&](int sr, int t, float2 v, int, int) { o[sr * L + t] = v; };
+        last_pass_to<L, true, RB, NT>(rowbuf, SSR, ptr, emit, tid);
       }
       __syncthreads();
     }
