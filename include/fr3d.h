@@ -253,6 +253,21 @@ int fr3d_band_alpha_targets(fr3d_handle* h, const float* U, const float* zeta_tr
                             const double* alphas, int n_alpha, int n_bands, int* idx, float* target,
                             double* err, void* stream);
 
+/* ---- autotuner of the fused inverse (steps 2-4 in one kernel, FP32, M = 1) ----
+ * The fused inverse has tile variants that compute the same bits (variant 0: the built-in table of
+ * cluster size, threads and row-batch height per n with xi accumulated in shared memory; 1: xi
+ * accumulated in the output array with taller row batches where they fit; 2: xi in the output
+ * array, table batches).  Modes: 0 = always variant 0; 1 (default) = on the first fr3d_invert of a
+ * shape (device, n, M', Q, output) made outside a stream capture, time every variant on that
+ * call's own arguments (1 warm-up + 3 timed launches each, synchronising the stream once) and use
+ * the fastest from then on, process-wide; 2 + v = always variant v.  Batched plans use variant 0
+ * unless one is forced.  The paper has no counterpart (it fixes no tiling).
+ * fr3d_autotune_mode(-1) returns the mode; otherwise it sets it and returns the previous one. */
+int fr3d_autotune_mode(int mode);
+/* The variant that the handle's last fused inverse used, and (ms, up to cap entries) the per-launch
+ * times the tuner measured on this handle (0 if it did not tune here).  Returns the variant count. */
+int fr3d_autotune_query(fr3d_handle* h, int* variant, float* ms, int cap);
+
 /* Number of kernel launches the last call on this handle enqueued (cache rebuilds excluded). */
 int fr3d_last_launch_count(fr3d_handle* h);
 

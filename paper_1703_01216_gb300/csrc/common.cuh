@@ -93,6 +93,10 @@ struct Handle {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int last_launches = 0;
+  // fused-inverse tile variant of the last call, and the autotuner's timings (ms) if it ran
+  int fused_var = 0;
+  int fused_tuned = 0;
+  float fused_tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
   // stage profiling: events recorded between consecutive launches of one call
   static constexpr int kMaxEv = 96;
   bool prof_on = false;

@@ -24,6 +24,7 @@
 
 #include <cooperative_groups.h>
 
+#include "common.cuh"
 #include "fft2d.cuh"
 #include "../../include/fr3d.h"
 
@@ -56,8 +57,22 @@ template <> struct FusedCfg<192> : FusedCfgBase { static constexpr int CL = 4, N
 template <> struct FusedCfg<256> : FusedCfgBase { static constexpr int CL = 8, NT = 256, RB = 16, MINB = 2; };
 template <> struct FusedCfg<384> : FusedCfgBase { static constexpr int CL = 8, NT = 512, RB = 16, MINB = 1; };
 
-template <int N> struct FusedGeom {
-  using Cf = FusedCfg<N>;
+// Tile variants of the fused inverse (chosen at run time by the autotuner in fused_f32.cu):
+//   V = 0  the table above;
+//   V = 1  xi accumulated in the output array, row batches twice as tall when they divide the rows;
+//   V = 2  xi accumulated in the output array, row batches as in the table.
+// All variants perform the same arithmetic in the same order: their outputs are bit-identical.
+constexpr int kFusedVariants = 3;
+template <int N, int V> struct FusedCfgV {
+  using B = FusedCfg<N>;
+  static constexpr int CL = B::CL, NT = B::NT, MINB = B::MINB;
+  static constexpr int RB = (V == 1 && (N / CL) % (2 * B::RB) == 0 && (2 * B::RB * (N / 2)) % NT == 0)
+                                ? 2 * B::RB : B::RB;
+  static constexpr bool GACC = V == 0 ? B::GACC : true;
+};
+
+template <int N, int V = 0> struct FusedGeom {
+  using Cf = FusedCfgV<N, V>;
   static constexpr int CL = Cf::CL, NT = Cf::NT, RB = Cf::RB;
   static constexpr int L = N / 2;
   static constexpr int CPC = L / CL;                   // packed columns per CTA
@@ -92,9 +107,9 @@ struct FusedArgs {
   int Q, j0, Mp;
 };
 
-template <int N, int MODE>
+template <int N, int MODE, int V>
 __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
-  using G = FusedGeom<N>;
+  using G = FusedGeom<N, V>;
   constexpr int CL = G::CL, NT = G::NT, RB = G::RB, L = G::L;
   constexpr int CPC = G::CPC, NRW = G::NRW, NB = G::NB, SSC = G::SSC, SSR = G::SSR, EPT = G::EPT;
   constexpr int CLD = CPC * N / NT;           // column elements per thread
@@ -271,18 +286,87 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
 }
 
 // Both kernels are launched with a cluster dimension of FusedCfg<N>::CL (launch_clustered).
-template <int N, int MODE>
+template <int N, int MODE, int V>
 __global__ void __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB) k_inv_fused(FusedArgs a) {
-  inv_fused_body<N, MODE>(a, (int)blockIdx.x / FusedCfg<N>::CL);
+  inv_fused_body<N, MODE, V>(a, (int)blockIdx.x / FusedCfg<N>::CL);
 }
 
 // Batched instances of one grid size n: cluster c handles depth map[c].y of instance map[c].x.
-template <int N, int MODE>
+template <int N, int MODE, int V>
 __global__ void __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
     k_inv_fused_batched(const FusedArgs* __restrict__ inst, const int2* __restrict__ map) {
   const int2 m = map[blockIdx.x / FusedCfg<N>::CL];
   const FusedArgs a = inst[m.x];
-  inv_fused_body<N, MODE>(a, m.y);
+  inv_fused_body<N, MODE, V>(a, m.y);
 }
+
+// Launch `kern` on `clusters` clusters of CL CTAs (a runtime cluster dimension; sizes above the
+// portable 8 are allowed once per kernel, on the first launch, which happens outside any capture).
+template <int CL, class K, class... Args>
+int launch_clustered(K kern, int clusters, int nt, size_t sm, cudaStream_t st, Args... args) {
+  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(kern), sm));
+  if constexpr (CL > 8) {
+    static bool allowed = false;
+    if (!allowed) {
+      FR3D_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      allowed = true;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * CL);
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FR3D_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args...));
+  return FR3D_OK;
+}
+
+// Launchers of variant V for every supported n (defined in fused_v<V>.cu).
+template <int V> int fused_launch(int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st);
+template <int V>
+int fused_launch_batched(int n, bool xi, const FusedArgs* inst, const int2* map, int nclusters, cudaStream_t st);
+
+// Definitions shared by the fused_v<V>.cu files.
+#define FR3D_FUSED_VARIANT(V)                                                                                   \
+  template <int N, int MODE>                                                                                    \
+  static int launch_one_##V(const FusedArgs& a, int nj, cudaStream_t st) {                                      \
+    using G = FusedGeom<N, V>;                                                                                  \
+    constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;                                                \
+    return launch_clustered<G::CL>(k_inv_fused<N, MODE, V>, nj, G::NT, sm, st, a);                              \
+  }                                                                                                             \
+  template <int N, int MODE>                                                                                    \
+  static int launch_batched_##V(const FusedArgs* inst, const int2* map, int ncl, cudaStream_t st) {             \
+    using G = FusedGeom<N, V>;                                                                                  \
+    constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;                                                \
+    return launch_clustered<G::CL>(k_inv_fused_batched<N, MODE, V>, ncl, G::NT, sm, st, inst, map);             \
+  }                                                                                                             \
+  template <>                                                                                                   \
+  int fused_launch<V>(int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st) {                            \
+    switch (n) {                                                                                                \
+      FR3D_FUSED_CASES(launch_one_##V, (a, nj, st))                                                             \
+    }                                                                                                           \
+    return FR3D_ERR_UNSUPPORTED_SIZE;                                                                           \
+  }                                                                                                             \
+  template <>                                                                                                   \
+  int fused_launch_batched<V>(int n, bool xi, const FusedArgs* inst, const int2* map, int ncl, cudaStream_t st) { \
+    switch (n) {                                                                                                \
+      FR3D_FUSED_CASES(launch_batched_##V, (inst, map, ncl, st))                                                \
+    }                                                                                                           \
+    return FR3D_ERR_UNSUPPORTED_SIZE;                                                                           \
+  }
+#define FR3D_FUSED_CASE(F, ARGS, N) \
+  case N: return xi ? F<N, 1> ARGS : F<N, 0> ARGS;
+#define FR3D_FUSED_CASES(F, ARGS)                                                                 \
+  FR3D_FUSED_CASE(F, ARGS, 16) FR3D_FUSED_CASE(F, ARGS, 24) FR3D_FUSED_CASE(F, ARGS, 32)         \
+  FR3D_FUSED_CASE(F, ARGS, 48) FR3D_FUSED_CASE(F, ARGS, 64) FR3D_FUSED_CASE(F, ARGS, 96)         \
+  FR3D_FUSED_CASE(F, ARGS, 128) FR3D_FUSED_CASE(F, ARGS, 192) FR3D_FUSED_CASE(F, ARGS, 256)      \
+  FR3D_FUSED_CASE(F, ARGS, 384)
 
 }  // namespace fr3d

@@ -1,4 +1,9 @@
-// Launchers of the fused inverse (fused.cuh) and of the 1 / sum_q V0_q^2 table.
+// Launchers of the fused inverse (fused.cuh), its tile-variant autotuner, and the combination table.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "fused.cuh"
 #include "ops.cuh"
 
@@ -24,39 +29,79 @@ __global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, d
 
 namespace {
 
-// Launch `kern` on `clusters` clusters of CL CTAs (a runtime cluster dimension; sizes above the
-// portable 8 are allowed once per kernel, on the first launch, which happens outside any capture).
-template <int CL, class K, class... Args>
-int launch_clustered(K kern, int clusters, int nt, size_t sm, cudaStream_t st, Args... args) {
-  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(kern), sm));
-  if constexpr (CL > 8) {
-    static bool allowed = false;
-    if (!allowed) {
-      FR3D_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      allowed = true;
-    }
+// ---------------- autotuner of the fused inverse's tile variant
+// Mode 0: always variant 0; 1: on the first call for a shape (device, n, depths, Q, output) outside a
+// stream capture, time every variant on the call's own arguments (one warm-up and three timed launches
+// each; all variants produce the same bits) and keep the fastest for later calls; 2 + v: always
+// variant v.  Calls inside a capture use the tuned choice if there is one, else variant 0.
+std::atomic<int> g_tune_mode{1};
+struct TuneKey {
+  int dev, n, nj, Q, xi;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, n, nj, Q, xi) < std::tie(o.dev, o.n, o.nj, o.Q, o.xi);
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(clusters * CL);
-  cfg.blockDim = dim3(nt);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  FR3D_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args...));
-  return FR3D_OK;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+int launch_variant(int v, int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st) {
+  switch (v) {
+    case 0: return fused_launch<0>(n, xi, a, nj, st);
+    case 1: return fused_launch<1>(n, xi, a, nj, st);
+    case 2: return fused_launch<2>(n, xi, a, nj, st);
+  }
+  return FR3D_ERR_INVALID_ARG;
 }
 
-template <int N, int MODE>
-int launch_fused(const Handle* H, const FusedArgs& a, int nj, cudaStream_t st) {
-  using G = FusedGeom<N>;
-  constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;
-  return launch_clustered<G::CL>(k_inv_fused<N, MODE>, nj, G::NT, sm, st, a);
+int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, cudaStream_t st, int* v_out) {
+  const int mode = g_tune_mode.load();
+  if (mode >= 2) {
+    *v_out = std::min(mode - 2, kFusedVariants - 1);
+    return FR3D_OK;
+  }
+  *v_out = 0;
+  if (mode == 0) return FR3D_OK;
+  const TuneKey key{H->dev, H->n, nj, a.Q, xi ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      *v_out = it->second;
+      return FR3D_OK;
+    }
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FR3D_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return FR3D_OK;
+  cudaEvent_t e0, e1;
+  FR3D_CUDA_TRY(cudaEventCreate(&e0));
+  FR3D_CUDA_TRY(cudaEventCreate(&e1));
+  int best = 0, st_ok = FR3D_OK;
+  float best_ms = 3.4e38f;
+  for (int v = 0; v < kFusedVariants && st_ok == FR3D_OK; ++v) {
+    st_ok = launch_variant(v, H->n, xi, a, nj, st);
+    if (st_ok == FR3D_OK && cudaEventRecord(e0, st) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
+    for (int rep = 0; rep < 3 && st_ok == FR3D_OK; ++rep) st_ok = launch_variant(v, H->n, xi, a, nj, st);
+    if (st_ok == FR3D_OK && cudaEventRecord(e1, st) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
+    if (st_ok == FR3D_OK && cudaEventSynchronize(e1) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
+    float ms = 0.f;
+    if (st_ok == FR3D_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
+    if (st_ok != FR3D_OK) break;
+    ms /= 3.f;
+    H->fused_tune_ms[v] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FR3D_TRY(st_ok);
+  H->fused_tuned = 1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = best;
+  *v_out = best;
+  return FR3D_OK;
 }
 
 }  // namespace
@@ -85,33 +130,22 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   a.j0 = j0;
   a.Mp = H->Mp;
   const bool xi = output == FR3D_OUT_XI;
-  switch (H->n) {
-#define X(N) \
-  case N: return xi ? launch_fused<N, 1>(H, a, nj, st) : launch_fused<N, 0>(H, a, nj, st);
-    X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
-#undef X
-  }
-  return FR3D_ERR_UNSUPPORTED_SIZE;
+  int v = 0;
+  FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, nj, xi, st, &v));
+  const_cast<Handle*>(H)->fused_var = v;
+  return launch_variant(v, H->n, xi, a, nj, st);
 }
-
-namespace {
-template <int N, int MODE>
-int launch_fused_batched(const FusedArgs* inst, const int2* map, int nclusters, cudaStream_t st) {
-  using G = FusedGeom<N>;
-  constexpr size_t sm = MODE == 1 ? G::smem_xi : G::smem_zeta;
-  return launch_clustered<G::CL>(k_inv_fused_batched<N, MODE>, nclusters, G::NT, sm, st, inst, map);
-}
-}  // namespace
 
 int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st) {
+  // batched plans use variant 0 unless a variant is forced
+  const int mode = g_tune_mode.load();
+  const int v = mode >= 2 ? std::min(mode - 2, kFusedVariants - 1) : 0;
   const bool xi = output == FR3D_OUT_XI;
-  switch (n) {
-#define X(N) \
-  case N: return xi ? launch_fused_batched<N, 1>(inst, map, nclusters, st) : launch_fused_batched<N, 0>(inst, map, nclusters, st);
-    X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
-#undef X
+  switch (v) {
+    case 1: return fused_launch_batched<1>(n, xi, inst, map, nclusters, st);
+    case 2: return fused_launch_batched<2>(n, xi, inst, map, nclusters, st);
   }
-  return FR3D_ERR_UNSUPPORTED_SIZE;
+  return fused_launch_batched<0>(n, xi, inst, map, nclusters, st);
 }
 
 void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
@@ -142,3 +176,18 @@ int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, dou
 }
 
 }  // namespace fr3d
+
+extern "C" int fr3d_autotune_mode(int mode) {
+  if (mode < -1 || mode > 1 + fr3d::kFusedVariants) return FR3D_ERR_INVALID_ARG;
+  if (mode == -1) return fr3d::g_tune_mode.load();
+  return fr3d::g_tune_mode.exchange(mode);
+}
+
+extern "C" int fr3d_autotune_query(fr3d_handle* h, int* variant, float* ms, int cap) {
+  if (!h) return FR3D_ERR_INVALID_ARG;
+  const fr3d::Handle* H = &h->h;
+  if (variant) *variant = H->fused_var;
+  if (ms)
+    for (int v = 0; v < std::min(cap, fr3d::kFusedVariants); ++v) ms[v] = H->fused_tuned ? H->fused_tune_ms[v] : 0.f;
+  return fr3d::kFusedVariants;
+}

@@ -69,7 +69,7 @@ EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", 
            "fr3d_invert_batched",
            "fr3d_mlp_create", "fr3d_mlp_destroy", "fr3d_mlp_query", "fr3d_mlp_get_params", "fr3d_mlp_set_params",
            "fr3d_mlp_forward", "fr3d_mlp_gradient", "fr3d_mlp_train_step", "fr3d_band_features",
-           "fr3d_band_alpha_targets")
+           "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query")
 
 
 def load(path: str | None = None):
@@ -112,6 +112,8 @@ def load(path: str | None = None):
     lib.fr3d_mlp_train_step.argtypes = [vp, vp, vp, i, ct.c_float, vp, vp]
     lib.fr3d_band_features.argtypes = [vp, vp, i, i, d, vp, vp]
     lib.fr3d_band_alpha_targets.argtypes = [vp, vp, vp, i, _dp, i, i, vp, vp, vp, vp]
+    lib.fr3d_autotune_mode.argtypes = [i]
+    lib.fr3d_autotune_query.argtypes = [vp, ct.POINTER(i), ct.POINTER(ct.c_float), i]
     lib.fr3d_status_string.argtypes = [i]
     lib.fr3d_status_string.restype = ct.c_char_p
     for name in EXPORTS:
@@ -280,6 +282,23 @@ def profile_read(handle: Handle, cap: int = 96):
     ms = (ct.c_float * cap)()
     n = _check(load().fr3d_profile_read(handle.ptr, kinds, ms, cap), "fr3d_profile_read")
     return [(STAGE_NAMES[kinds[i]], float(ms[i])) for i in range(n)]
+
+
+def autotune_mode(mode: int | None = None) -> int:
+    """Set the fused-inverse autotuner mode (0 off, 1 tune per shape, 2 + v force variant v) and return
+    the previous one; with no argument, return the current mode."""
+    r = load().fr3d_autotune_mode(-1 if mode is None else int(mode))
+    _check(r, "fr3d_autotune_mode")
+    return r
+
+
+def autotune_query(handle: Handle):
+    """(variant of the handle's last fused inverse, per-variant tuning times in ms or zeros)."""
+    v = ct.c_int()
+    ms = (ct.c_float * 8)()
+    n = load().fr3d_autotune_query(handle.ptr, ct.byref(v), ms, 8)
+    _check(n, "fr3d_autotune_query")
+    return v.value, [float(ms[k]) for k in range(n)]
 
 
 class Mlp:

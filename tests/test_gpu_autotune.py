@@ -1,0 +1,95 @@
+"""Tile variants of the fused inverse and their autotuner: every variant gives the same bits (single
+calls and batched plans), the oracle agrees, and the tuner times every variant and keeps one."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1703_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1703_01216_gb300 import build, fr3d
+    assert torch.cuda.is_available()
+    build.build()
+    fr3d.load()
+    prev = fr3d.autotune_mode()
+    yield fr3d
+    fr3d.autotune_mode(prev)
+
+
+def _data(F, w):
+    H = F.kernel_transform(w.n, w.x0, w.h, w.zr, w.zy, w.nu)
+    zeta = torch.empty((w.Q, w.Mp, w.n, w.n), device="cuda")
+    F.zeta_from_xi(H, torch.as_tensor(w.xi_true, dtype=torch.float32, device="cuda"), w.sources, zeta)
+    U = torch.empty((w.Q, 1, w.n, w.n), device="cuda")
+    F.fwd_apply(H, zeta, w.Q, U)
+    nz = torch.as_tensor(w.noise, dtype=torch.float32, device="cuda")
+    nz *= w.noise_level * U.norm() / nz.norm()
+    return H, U + nz, float(nz.norm())
+
+
+@pytest.mark.parametrize("n,mp,q", [(32, 6, 2), (64, 5, 3), (128, 4, 2), (192, 3, 1), (256, 4, 3), (384, 2, 1)])
+@pytest.mark.parametrize("output", ["xi", "zeta"])
+def test_variants_are_bit_identical_and_match_oracle(F, n, mp, q, output):
+    w = I.make_workload(n, mp, q=q, n_incl=3, noise_level=0.02, n_alpha=12, seed=40 + n)
+    H, U, delta = _data(F, w)
+    out_kind = F.OUT_XI if output == "xi" else F.OUT_ZETA
+    shape = (mp, n, n) if output == "xi" else (q, mp, n, n)
+    outs = []
+    for v in range(3):
+        F.autotune_mode(2 + v)
+        o = torch.full(shape, float("nan"), device="cuda")
+        F.invert(H, U, q, o, F.Opts(alpha=1e-3, output=out_kind, points=w.sources))
+        assert F.autotune_query(H)[0] == v
+        outs.append(o)
+    for v in (1, 2):
+        assert torch.equal(outs[v], outs[0]), v
+    ref = O.invert(U.double().cpu().numpy(), n, w.x0, w.h, w.zy, w.zr, w.nu, alpha=1e-3, sources=w.sources,
+                   output=output)
+    got = outs[0].double().cpu().numpy()
+    assert np.linalg.norm(got - ref[output]) <= 1e-4 * np.linalg.norm(ref[output])
+
+
+def test_tuner_times_every_variant_and_keeps_the_fastest(F):
+    F.autotune_mode(1)
+    w = I.make_workload(128, 7, q=2, n_incl=2, noise_level=0.02, n_alpha=12, seed=5)
+    H, U, delta = _data(F, w)
+    out = torch.empty((7, 128, 128), device="cuda")
+    F.invert(H, U, 2, out, F.Opts(alphas=w.alphas, delta=delta, points=w.sources))
+    v, ms = F.autotune_query(H)
+    assert len(ms) == 3 and all(t > 0 for t in ms)
+    assert ms[v] == min(ms)
+    # a second handle of the same shape reuses the choice without timing
+    H2 = F.kernel_transform(w.n, w.x0, w.h, w.zr, w.zy, w.nu)
+    o2 = torch.empty_like(out)
+    F.invert(H2, U, 2, o2, F.Opts(alphas=w.alphas, delta=delta, points=w.sources))
+    v2, ms2 = F.autotune_query(H2)
+    assert v2 == v and all(t == 0 for t in ms2)
+    assert torch.equal(o2, out)
+
+
+def test_batched_plan_is_identical_under_every_variant(F):
+    shapes = [(64, 5, 2), (128, 3, 1), (256, 2, 2)]
+    items = []
+    for k, (n, mp, q) in enumerate(shapes):
+        w = I.make_workload(n, mp, q=q, n_incl=2, noise_level=0.02, n_alpha=12, seed=60 + k)
+        H, U, delta = _data(F, w)
+        items.append((H, U, q, F.Opts(alphas=w.alphas, delta=delta, points=w.sources),
+                      torch.empty((mp, n, n), device="cuda")))
+    results = []
+    for v in range(3):
+        F.autotune_mode(2 + v)
+        B = F.Batch(items)
+        B.run()
+        torch.cuda.synchronize()
+        results.append([it[4].clone() for it in items])
+        B.close()
+    for v in (1, 2):
+        for a, b in zip(results[0], results[v]):
+            assert torch.equal(a, b)
+    F.autotune_mode(1)
