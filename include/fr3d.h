@@ -193,7 +193,9 @@ int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_inver
  * its instances (data row pass, data column pass, alpha rule, fused inverse).  fr3d_batch_create
  * builds every table and workspace and uploads the descriptors (it synchronises `stream`); the
  * device pointers and options of the instances are fixed at creation.  fr3d_batch_run only
- * launches kernels (it can be captured in a CUDA graph).  The paper has no batch form: this is
+ * launches kernels (it can be captured in a CUDA graph); with the autotuner on (mode 1, below) its
+ * first call outside a capture also times the fused variants and synchronises `stream`, so make
+ * that call before capturing.  The paper has no batch form: this is
  * Algorithm 1 applied to many independent problems at once. */
 typedef struct fr3d_instance {
   fr3d_handle* handle;            /* geometry and kernel tables (fr3d_kernel_transform) */
@@ -260,8 +262,10 @@ int fr3d_band_alpha_targets(fr3d_handle* h, const float* U, const float* zeta_tr
  * array, table batches).  Modes: 0 = always variant 0; 1 (default) = on the first fr3d_invert of a
  * shape (device, n, M', Q, output) made outside a stream capture, time every variant on that
  * call's own arguments (1 warm-up + 3 timed launches each, synchronising the stream once) and use
- * the fastest from then on, process-wide; 2 + v = always variant v.  Batched plans use variant 0
- * unless one is forced.  The paper has no counterpart (it fixes no tiling).
+ * the fastest from then on, process-wide; 2 + v = always variant v.  A batched plan (mode 1) times
+ * the variants of each grid-size group on its first fr3d_batch_run outside a capture and keeps the
+ * fastest per group (that run's outputs are complete and identical).  The paper has no counterpart
+ * (it fixes no tiling).
  * fr3d_autotune_mode(-1) returns the mode; otherwise it sets it and returns the previous one. */
 int fr3d_autotune_mode(int mode);
 /* The variant that the handle's last fused inverse used, and (ms, up to cap entries) the per-launch
@@ -276,8 +280,7 @@ int fr3d_last_launch_count(fr3d_handle* h);
  * and writes, per launch interval i < min(cap, count), its stage kind and its duration in ms;
  * it returns the count.  Kinds: 0 data row pass, 1 data column pass, 2 alpha rule, 3 solve +
  * inverse column pass, 4 inverse row pass (+ xi), 5 table rebuild, 6 forward contraction,
- * 7 inverse column pass, 8 other, 9 fused solve + inverse DFT + combination, 10 per-band selection of
- * the solve weights (n_bands > 1). */
+ * 7 inverse column pass, 8 other, 9 fused solve + inverse DFT + combination. */
 int fr3d_profile_enable(fr3d_handle* h, int enable);
 int fr3d_profile_read(fr3d_handle* h, int* kinds, float* ms, int cap);
 

@@ -289,15 +289,7 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
         prof_mark(H, kStTable, st);
       }
       const float* Dd = o->alpha_mode == FR3D_ALPHA_FIXED ? H->Ddfix32 : H->Dd32;
-      if (nb > 1) {
-        // per-band alphas: one table of each bin's weight, so the fused kernel reads a single row
-        FR3D_TRY(band_select_f32(H, aidx, st));
-        prof_mark(H, kStBandSelect, st);
-        launches += 1;
-        Dd = H->dsel32;
-        aidx = H->zero_idx;
-      }
-      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, 1, H->wtab, out, Q, 0, H->Mp, o->output, st));
+      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, nb, H->wtab, out, Q, 0, H->Mp, o->output, st));
       prof_mark(H, kStFused, st);
       H->last_launches = launches + 1;
       return FR3D_OK;

@@ -39,7 +39,11 @@ __global__ void __cluster_dims__(kAlphaCluster, 1, 1) __launch_bounds__(256) k_a
                             a.counter, a.aidx, a.res, a.info, (int)blockIdx.x - a.bstart, a.nblk);
 }
 
-int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st);
+int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, int variant,
+                          cudaStream_t st);
+int fused_tune_mode_get();
+int fused_tune_batched(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st,
+                       int* best);
 void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
                     float* out, int Q, FusedArgs* a);
 void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double* thr2);
@@ -52,11 +56,13 @@ struct Group {
   int n = 0;
   const Handle* H0 = nullptr;
   int nplanes = 0, nalpha_inst = 0, nalpha_blk = 0, nclusters = 0, max_na = 0;
+  int var = -1;   // fused-inverse tile variant (-1: not chosen yet)
   size_t off_planes = 0, off_alpha = 0, off_fused = 0, off_map = 0;
 };
 
+// the launches of a group before the fused inverse: data row and column passes, alpha rule
 template <int N>
-int run_group_n(const Group& g, const unsigned char* dev, int output, cudaStream_t st) {
+int run_group_pre_n(const Group& g, const unsigned char* dev, cudaStream_t st) {
   const PlanePtr* planes = reinterpret_cast<const PlanePtr*>(dev + g.off_planes);
   constexpr int TY = SmallTile<N>::row, TC = SmallTile<N>::col;
   FR3D_TRY((row_r2c_t<float, N, TY, TablePlanes>(g.H0, TablePlanes{planes}, g.nplanes, st)));
@@ -69,19 +75,23 @@ int run_group_n(const Group& g, const unsigned char* dev, int output, cudaStream
                                                    1.0 / ((double)N * N));
     FR3D_CUDA_TRY(cudaGetLastError());
   }
-  return inv_fused_batched_f32(N, reinterpret_cast<const FusedArgs*>(dev + g.off_fused),
-                               reinterpret_cast<const int2*>(dev + g.off_map), g.nclusters, output, st);
+  return FR3D_OK;
 }
 
-int run_group(const Group& g, const unsigned char* dev, int output, cudaStream_t st) {
+int run_group_pre(const Group& g, const unsigned char* dev, cudaStream_t st) {
   switch (g.n) {
 #define X(N) \
-  case N: return run_group_n<N>(g, dev, output, st);
+  case N: return run_group_pre_n<N>(g, dev, st);
     X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384)
 #undef X
   }
   return FR3D_ERR_UNSUPPORTED_SIZE;
 }
+
+const FusedArgs* fused_of(const Group& g, const unsigned char* dev) {
+  return reinterpret_cast<const FusedArgs*>(dev + g.off_fused);
+}
+const int2* map_of(const Group& g, const unsigned char* dev) { return reinterpret_cast<const int2*>(dev + g.off_map); }
 
 size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -201,9 +211,28 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
 }
 
 extern "C" int fr3d_batch_run(fr3d_batch* h, void* stream) {
+  using namespace fr3d;
   if (!h) return FR3D_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  for (const auto& g : h->b.groups) FR3D_TRY(fr3d::run_group(g, h->b.dev, h->b.output, st));
+  const int mode = fused_tune_mode_get();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FR3D_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  for (auto& g : h->b.groups) {
+    FR3D_TRY(run_group_pre(g, h->b.dev, st));
+    int v = mode >= 2 ? mode - 2 : 0;
+    if (mode == 1) {
+      if (g.var < 0 && cs == cudaStreamCaptureStatusNone) {
+        // the first run outside a capture times the variants on this group (their launches leave
+        // the group's outputs complete: every variant writes the same bits)
+        FR3D_TRY(fused_tune_batched(g.n, fused_of(g, h->b.dev), map_of(g, h->b.dev), g.nclusters, h->b.output, st,
+                                    &g.var));
+        continue;
+      }
+      v = g.var < 0 ? 0 : g.var;
+    }
+    FR3D_TRY(inv_fused_batched_f32(g.n, fused_of(g, h->b.dev), map_of(g, h->b.dev), g.nclusters, h->b.output, v,
+                                   st));
+  }
   return FR3D_OK;
 }
 

@@ -88,7 +88,7 @@ struct Handle {
   unsigned char* cband = nullptr; // [C] radial band of every class for cband_nb bands
   int cband_nb = 0;
   std::vector<double> band_count; // grid frequencies per band (sum of the classes' member weights)
-  float* dsel32 = nullptr;        // [n/2+1][n] solve weights of each bin's band alpha (per-band calls)
+  unsigned char* bbin = nullptr;  // [n/2+1][n] radial band of every half-spectrum bin for cband_nb bands
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -122,7 +122,7 @@ int smem_optin(const void* kernel, size_t bytes);
 
 // stage kinds reported by fr3d_profile_read
 enum StageKind { kStRowR2C = 0, kStColFwd = 1, kStAlpha = 2, kStColSolve = 3, kStRowC2R = 4, kStTable = 5,
-                 kStContract = 6, kStColInv = 7, kStOther = 8, kStFused = 9, kStBandSelect = 10 };
+                 kStContract = 6, kStColInv = 7, kStOther = 8, kStFused = 9 };
 // Inside a stream capture an event is recorded with cudaEventRecordExternal so that it becomes a
 // graph node and a replayed graph records the stage events too; outside a capture it is a plain
 // record.  A failed record stops the tracing of this call (n_ev = 0) and clears the error.

@@ -99,7 +99,7 @@ struct FusedArgs {
   const float* A;      // [M' = j][n/2+1][n] dense kernel table
   const float* Dd;     // [n_alpha][n/2+1][n] dense solve weights
   const int* aidx;     // chosen row of Dd per band
-  const unsigned char* cband;  // band of every frequency class (nb > 1)
+  const unsigned char* bbin;   // [n/2+1][n] band of every half-spectrum bin (nb > 1)
   int nb;              // bands (1: one alpha for the whole spectrum)
   const float* W;      // [Q][M'][n][n] combination weights V0_q / sum_q' V0_q'^2 (XI mode)
   float* out;          // XI: [M'][n][n]; ZETA: [Q][M'][n][n]
@@ -138,29 +138,48 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   {
     const float* Aj = a.A + (long)j * ps;
     const float* drow = a.Dd + (long)s_aidx[0] * ps;
-    // solve weight of bin o = kx n + ky: the row of its band's alpha
-    auto dval = [&](long o) -> float {
-      if (a.nb == 1) return __ldg(drow + o);
-      const int kx = (int)(o / N), ky = (int)(o % N);
-      return __ldg(a.Dd + (long)s_aidx[a.cband[class_of(kx, ky, N)]] * ps + o);
-    };
     for (int e = tid; e < N; e += NT) tws[e] = __ldg(a.tw_n + e);
     build_passtw<N, 1, NT>(ptc, a.tw_n, tid);
     build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
+    // solve weight of bin o = kx n + ky: row aidx[band(o)] of Dd (one row when nb = 1); with bands the
+    // band indices of all of this thread's bins are fetched first, then every weight in one round
+    if (a.nb == 1) {
 #pragma unroll
-    for (int b0 = 0; b0 < CLD; b0 += CB) {
-      float wa[CB], wd[CB];
+      for (int b0 = 0; b0 < CLD; b0 += CB) {
+        float wa[CB], wd[CB];
 #pragma unroll
-      for (int i = 0; i < CB; ++i) {
-        const long o = (long)c0 * N + tid + (b0 + i) * NT;   // columns c0.. are contiguous
-        wa[i] = __ldg(Aj + o);
-        wd[i] = dval(o);
+        for (int i = 0; i < CB; ++i) {
+          const long o = (long)c0 * N + tid + (b0 + i) * NT;   // columns c0.. are contiguous
+          wa[i] = __ldg(Aj + o);
+          wd[i] = __ldg(drow + o);
+        }
+#pragma unroll
+        for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = wa[i] * wd[i];
       }
+      if (r == 0)
+        for (int e = tid; e < N; e += NT) wsm[CPC * N + e] = __ldg(Aj + (long)L * N + e) * __ldg(drow + (long)L * N + e);
+    } else {
 #pragma unroll
-      for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = wa[i] * wd[i];
+      for (int b0 = 0; b0 < CLD; b0 += CB) {
+        int bb[CB];
+        float wa[CB], wd[CB];
+#pragma unroll
+        for (int i = 0; i < CB; ++i) bb[i] = __ldg(a.bbin + (long)c0 * N + tid + (b0 + i) * NT);
+#pragma unroll
+        for (int i = 0; i < CB; ++i) {
+          const long o = (long)c0 * N + tid + (b0 + i) * NT;
+          wa[i] = __ldg(Aj + o);
+          wd[i] = __ldg(a.Dd + (long)s_aidx[bb[i]] * ps + o);
+        }
+#pragma unroll
+        for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = wa[i] * wd[i];
+      }
+      if (r == 0)
+        for (int e = tid; e < N; e += NT) {
+          const long o = (long)L * N + e;
+          wsm[CPC * N + e] = __ldg(Aj + o) * __ldg(a.Dd + (long)s_aidx[__ldg(a.bbin + o)] * ps + o);
+        }
     }
-    if (r == 0)
-      for (int e = tid; e < N; e += NT) wsm[CPC * N + e] = __ldg(Aj + (long)L * N + e) * dval((long)L * N + e);
   }
   __syncthreads();
 

@@ -121,7 +121,7 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   a.A = H->A32;
   a.Dd = Dd;
   a.aidx = aidx;
-  a.cband = H->cband;
+  a.bbin = H->bbin;
   a.nb = nb;
   a.W = W;
   a.out = out;
@@ -136,16 +136,53 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   return launch_variant(v, H->n, xi, a, nj, st);
 }
 
-int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st) {
-  // batched plans use variant 0 unless a variant is forced
-  const int mode = g_tune_mode.load();
-  const int v = mode >= 2 ? std::min(mode - 2, kFusedVariants - 1) : 0;
-  const bool xi = output == FR3D_OUT_XI;
+namespace {
+int launch_batched_variant(int v, int n, bool xi, const FusedArgs* inst, const int2* map, int ncl, cudaStream_t st) {
   switch (v) {
-    case 1: return fused_launch_batched<1>(n, xi, inst, map, nclusters, st);
-    case 2: return fused_launch_batched<2>(n, xi, inst, map, nclusters, st);
+    case 0: return fused_launch_batched<0>(n, xi, inst, map, ncl, st);
+    case 1: return fused_launch_batched<1>(n, xi, inst, map, ncl, st);
+    case 2: return fused_launch_batched<2>(n, xi, inst, map, ncl, st);
   }
-  return fused_launch_batched<0>(n, xi, inst, map, nclusters, st);
+  return FR3D_ERR_INVALID_ARG;
+}
+}  // namespace
+
+int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, int variant,
+                          cudaStream_t st) {
+  return launch_batched_variant(std::min(std::max(variant, 0), kFusedVariants - 1), n, output == FR3D_OUT_XI, inst,
+                                map, nclusters, st);
+}
+
+int fused_tune_mode_get() { return g_tune_mode.load(); }
+
+// Time every variant of a batched group's fused launch (1 warm-up + 2 timed launches each) and return
+// the fastest in *best.  Synchronises the stream.
+int fused_tune_batched(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st,
+                       int* best) {
+  const bool xi = output == FR3D_OUT_XI;
+  cudaEvent_t e0, e1;
+  FR3D_CUDA_TRY(cudaEventCreate(&e0));
+  FR3D_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = FR3D_OK, bv = 0;
+  float bms = 3.4e38f;
+  for (int v = 0; v < kFusedVariants && rc == FR3D_OK; ++v) {
+    rc = launch_batched_variant(v, n, xi, inst, map, nclusters, st);
+    if (rc == FR3D_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = FR3D_ERR_CUDA;
+    for (int k = 0; k < 2 && rc == FR3D_OK; ++k) rc = launch_batched_variant(v, n, xi, inst, map, nclusters, st);
+    if (rc == FR3D_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = FR3D_ERR_CUDA;
+    if (rc == FR3D_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = FR3D_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == FR3D_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = FR3D_ERR_CUDA;
+    if (rc == FR3D_OK && ms < bms) {
+      bms = ms;
+      bv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FR3D_TRY(rc);
+  *best = bv;
+  return FR3D_OK;
 }
 
 void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
@@ -154,7 +191,7 @@ void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const in
   a->A = H->A32;
   a->Dd = Dd;
   a->aidx = aidx;
-  a->cband = H->cband;
+  a->bbin = H->bbin;
   a->nb = nb;
   a->W = W;
   a->out = out;

@@ -49,7 +49,8 @@ int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, dou
 
 // alpha-rule partial sums buffer (per block, band and candidate)
 int ensure_partials(Handle* H);
-// band of every frequency class for nb radial bands, and the number of grid frequencies per band
+// band of every frequency class (cband) and of every half-spectrum bin (bbin) for nb radial bands,
+// and the number of grid frequencies per band
 int ensure_bands(Handle* H, int nb, std::vector<double>* count);
 
 // learned per-band alpha (learned.cu): one launch computing the band features (to feat, if given)
@@ -57,9 +58,6 @@ int ensure_bands(Handle* H, int nb, std::vector<double>* count);
 bool learned_net_fits(const fr3d_mlp* net, int nb);
 int learned_alpha(Handle* H, const float2* Uh, int nplanes, int nb, double delta, const double* alphas, int na,
                   const fr3d_mlp* net, int* aidx, float* feat, int* info, cudaStream_t st);
-
-// per-band calls: the solve-weight table of every bin's band alpha (Dd32 rows selected by aidx) into dsel32
-int band_select_f32(Handle* H, const int* aidx, cudaStream_t st);
 
 // precision-independent table builders (alpha tables, fixed alpha)
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st);

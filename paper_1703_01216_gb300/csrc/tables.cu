@@ -44,24 +44,13 @@ __global__ void k_dense_d(const float* __restrict__ D, int na, int Cn, int n, fl
   }
 }
 
-// Dsel[o] = Dd[aidx[band(o)]][o] for every half-spectrum bin o = kx n + ky
-__global__ void k_band_select(const float* __restrict__ Dd, const int* __restrict__ aidx,
-                              const unsigned char* __restrict__ cband, int n, int ps, float* __restrict__ Dsel) {
+// bbin[o] = band of the class of half-spectrum bin o = kx n + ky
+__global__ void k_bin_bands(const unsigned char* __restrict__ cband, int n, int ps, unsigned char* __restrict__ bbin) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= ps) return;
-  const int b = cband[class_of(o / n, o % n, n)];
-  Dsel[o] = __ldg(Dd + (long)__ldg(aidx + b) * ps + o);
+  if (o < ps) bbin[o] = cband[class_of(o / n, o % n, n)];
 }
 
 }  // namespace
-
-int band_select_f32(Handle* H, const int* aidx, cudaStream_t st) {
-  const int ps = (H->n / 2 + 1) * H->n;
-  if (!H->dsel32) FR3D_CUDA_TRY(cudaMalloc(&H->dsel32, sizeof(float) * ps));
-  k_band_select<<<(ps + 255) / 256, 256, 0, st>>>(H->Dd32, aidx, H->cband, H->n, ps, H->dsel32);
-  FR3D_CUDA_TRY(cudaGetLastError());
-  return FR3D_OK;
-}
 
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) {
   if ((int)H->alpha_key.size() == n_alpha && memcmp(H->alpha_key.data(), alphas, n_alpha * sizeof(double)) == 0)
@@ -134,6 +123,11 @@ int ensure_bands(Handle* H, int nb, std::vector<double>* count) {
       }
     if (!H->cband) FR3D_CUDA_TRY(cudaMalloc(&H->cband, H->C));
     FR3D_CUDA_TRY(cudaMemcpy(H->cband, band.data(), H->C, cudaMemcpyHostToDevice));
+    const int ps = (n / 2 + 1) * n;
+    if (!H->bbin) FR3D_CUDA_TRY(cudaMalloc(&H->bbin, ps));
+    k_bin_bands<<<(ps + 255) / 256, 256>>>(H->cband, n, ps, H->bbin);
+    FR3D_CUDA_TRY(cudaGetLastError());
+    FR3D_CUDA_TRY(cudaDeviceSynchronize());
     H->cband_nb = nb;
     H->band_count = cnt;
   }

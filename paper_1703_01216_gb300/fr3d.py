@@ -269,7 +269,7 @@ def last_launch_count(handle: Handle) -> int:
 
 
 STAGE_NAMES = ("row_r2c", "col_fwd", "alpha", "col_solve", "row_c2r", "table", "contract", "col_inv", "other",
-               "inv_fused", "band_select")
+               "inv_fused")
 
 
 def profile_enable(handle: Handle, enable: bool = True):
