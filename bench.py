@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="fr3d", choices=["fr3d", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-alpha leg")
+    ap.add_argument("--fused-variant", type=int, default=None,
+                    help="force the fused inverse's tile variant (default: autotuned on the first call)")
     ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
@@ -223,6 +225,8 @@ def run_fr3d(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
+    if args.fused_variant is not None:
+        fr3d.autotune_mode(2 + args.fused_variant)
     w = I.config_workload(CONFIG_ID, instance=rank)
     n, Mp, Q = w.n, w.Mp, w.Q
     voxels = n * n * Mp
@@ -321,8 +325,9 @@ def run_fr3d(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = algo / (per_launch_ms * 1e-3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom),
+    dom_key = f"{dom}/v{tuned_variant}" if dom == "inv_fused" else dom
+    roof = {"kernel": dom_key, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom_key),
             "algorithmic_bytes_per_launch": algo, "ms_per_launch": round(per_launch_ms, 5),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"}
 
@@ -341,7 +346,8 @@ def run_fr3d(args):
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
         "cold_setup_s": round(t_cold, 3),
         "fused_variant": {"chosen": tuned_variant, "tuning_ms_per_launch": [round(t, 5) for t in tune_ms],
-                          "mode": "autotuned on the first call (1 warm-up + 3 timed launches per variant)"},
+                          "mode": ("forced" if args.fused_variant is not None else
+                                   "autotuned on the first call (1 warm-up + 3 timed launches per variant)")},
         "alpha_index": int(idx.item()), "info": int(info.item()),
         "rel_l2_vs_truth": round(rel_truth, 4),
     }
