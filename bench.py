@@ -109,6 +109,21 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline bookkeeping
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (one all_reduce); x itself in a single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, steps: int, seconds: float) -> float:
+    """Throughput of the whole job: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world * steps / seconds
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1703_01216_gb300", "csrc")
@@ -283,12 +298,8 @@ def run_fr3d(args):
         dist.barrier()
     fr3d.profile_enable(H, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = voxels * world * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    value = whole_job_rate(voxels, world, args.steps, total_s)
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside the region)
     U_host = U.cpu().pin_memory()
@@ -306,10 +317,7 @@ def run_fr3d(args):
         a = time.perf_counter()
         fr3d.invert_host(H, U_host, Q, out_host, opts)   # H2D copy, inversion, D2H copy, stream sync
         e2e_total += time.perf_counter() - a
-    if dist:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
 
     # reconstruction quality of the last step (not timed)
     xi_true = torch.tensor(w.xi_true, device=dev)
@@ -340,7 +348,7 @@ def run_fr3d(args):
                    "voxels_per_instance": voxels, "instances_per_gpu": 1, "l2": "flushed (256 MB write) before every step", "launch": "one CUDA graph replay per step",
                    "parallelism": f"replicas x{world} (independent instances)"},
         "gpu_launches": launches,
-        "e2e": {"value": voxels * world * e2e_steps / e2e_total, "unit": "voxels/s",
+        "e2e": {"value": whole_job_rate(voxels, world, e2e_steps, e2e_total), "unit": "voxels/s",
                 "h2d_bytes_per_step": int(U_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4)},
         "roofline": roof,
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
@@ -431,13 +439,8 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
                 stage_ms[name] = stage_ms.get(name, 0.0) + ms
     torch.cuda.synchronize()
     fr3d.profile_enable(H, False)
-    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    world = 1
-    if dist:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        world = dist.get_world_size()
+    total_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, dev)
+    world = dist.get_world_size() if dist else 1
     xi_true = torch.tensor(w.xi_true, device=dev)
     rel = float((out.double() - xi_true).norm() / xi_true.norm())
     # the ceiling of a per-band rule: the error-optimal candidate of every band (needs the true zeta)
@@ -449,7 +452,7 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
     fr3d.invert(H, U, Q, out, fr3d.Opts(alphas=w.alphas, points=w.sources, alpha_idx=best, n_bands=n_bands,
                                         given=True))
     rel_best = float((out.double() - xi_true).norm() / xi_true.norm())
-    res = {"value": n * n * Mp * world * args.steps / total_s, "unit": "voxels/s",
+    res = {"value": whole_job_rate(n * n * Mp, world, args.steps, total_s), "unit": "voxels/s",
            "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
            "band_optimal_rel_l2_vs_truth": round(rel_best, 4),
            "band_optimal_alpha_index": [int(v) for v in best.cpu().numpy()],
