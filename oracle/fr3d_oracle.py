@@ -42,7 +42,7 @@ import numpy as np
 __all__ = [
     "kernel_K", "wrapped_lags", "kernel_samples", "dft_matrix", "dft2", "idft2",
     "kernel_hat", "A_matrices", "alpha_scale", "forward_direct", "forward_dft",
-    "tikhonov_qr", "residual_sq", "radial_bands", "choose_alpha_index", "V0", "zeta_from_xi",
+    "tikhonov_qr", "tsvd_solve", "residual_sq", "radial_bands", "choose_alpha_index", "V0", "zeta_from_xi",
     "combine_sources", "invert", "A0_of", "A2_of",
 ]
 
@@ -206,6 +206,22 @@ def tikhonov_qr(A: np.ndarray, Uh: np.ndarray, alpha_s2: float) -> np.ndarray:
     return x[..., :K] + 1j * x[..., K:]
 
 
+def tsvd_solve(A: np.ndarray, Uh: np.ndarray, t: float) -> np.ndarray:
+    """Truncated-SVD solution of A x = u for a batch of small systems (the regularising algorithm the
+    paper reports as its best, Sec. 5): with A = W diag(sigma) V^T (numpy.linalg.svd, LAPACK gesdd),
+    x_t = sum over the singular values with sigma^2 >= t of v_i (w_i^T u) / sigma_i, so that t plays the
+    role of alpha s^2 (a reading: the paper does not say how the truncation level is chosen; here the
+    discrepancy principle picks it from the same candidate list).
+
+    A: [B, M, M'] real.  Uh: [B, M, K] complex.  Returns [B, M', K]."""
+    A = np.asarray(A, np.float64)
+    W, sig, Vt = np.linalg.svd(A, full_matrices=False)              # [B,M,r], [B,r], [B,r,M']
+    keep = sig * sig >= t
+    inv = np.where(keep, 1.0 / np.where(sig > 0, sig, 1.0), 0.0)
+    proj = np.swapaxes(W, -1, -2) @ Uh                                # [B, r, K]
+    return np.swapaxes(Vt, -1, -2) @ (inv[..., None] * proj)
+
+
 def residual_sq(A: np.ndarray, Zh: np.ndarray, Uh: np.ndarray, n_freq: int | None = None) -> float:
     """sum over frequencies and right-hand sides of |A^(m) zeta~ - U~|^2, divided by L^2.
 
@@ -302,7 +318,8 @@ def combine_sources(zeta: np.ndarray, sources: np.ndarray, n: int, x0: float, h:
 # --------------------------------------------------------------------------- Algorithm 1
 def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int = 1,
            alpha=None, alphas=None, delta=None, tau: float = 1.1, sources=None, A0: float = 1.0,
-           output: str = "xi", chunk: int = 4096, bins=None, A=None, n_bands: int = 1, band_alpha_index=None):
+           output: str = "xi", chunk: int = 4096, bins=None, A=None, n_bands: int = 1, band_alpha_index=None,
+           ra: str = "tikhonov"):
     """Algorithm 1 (Sec. 4) in its finite-dimensional form (Sec. 5).
 
     U: [Q, M, n, n] data for Q source parameters.
@@ -319,6 +336,8 @@ def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int =
     ``output="none"`` stops after step 2.  ``bins`` (optional) restricts step 2 to a subset of
     the flattened frequencies; every other frequency gets the zero solution, which is exact when
     the data spectrum vanishes there (a zero right-hand side has the zero Tikhonov solution).
+    ``ra="tsvd"`` replaces the Tikhonov solution by the truncated SVD with truncation level alpha s^2
+    (tsvd_solve); everything else is unchanged.
     ``n_bands`` > 1 applies the discrepancy principle per radial band of frequencies (see
     radial_bands): band b gets its own alpha, the largest with residual_b <= tau delta_b, where
     delta_b^2 = delta^2 (frequencies in b) / L^2 (the share of white noise in the band); ``res2``
@@ -343,7 +362,7 @@ def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int =
         Z = np.empty((sel.size, Mp, Q), np.complex128)
         for s in range(0, sel.size, chunk):
             b = sel[s:s + chunk]
-            Z[s:s + b.size] = tikhonov_qr(Af[b], Uf[b], a * s2)
+            Z[s:s + b.size] = (tsvd_solve if ra == "tsvd" else tikhonov_qr)(Af[b], Uf[b], a * s2)
         return Z
 
     res2 = None

@@ -168,13 +168,15 @@ def test_tikhonov_optimality_pinv_limit_and_dual_identity():
     assert np.all(np.diff(res) >= -1e-12) and np.all(np.diff(nrm) <= 1e-12)
 
 
-def test_algorithm1_equals_dense_tikhonov_of_full_operator():
+@pytest.mark.parametrize("zy", [[0.0], [0.0, -0.15]])
+def test_algorithm1_equals_dense_tikhonov_of_full_operator(zy):
     """Per-frequency Tikhonov + inverse DFT (Algorithm 1, Lemma 1) equals Tikhonov on the whole
-    discretised operator of Eq. (4), assembled by brute force from the direct quadrature."""
-    n, h, zy, zr, nu = 4, 0.3, [0.0], [0.5, 0.7, 0.9], [0.2, 0.2, 0.2]
+    discretised operator of Eq. (4), assembled by brute force from the direct quadrature (one and two
+    observation planes)."""
+    n, h, zr, nu = 4, 0.3, [0.5, 0.7, 0.9], [0.2, 0.2, 0.2]
     Aop = _operator_matrix(n, h, zy, zr, nu)
     rng = np.random.default_rng(3)
-    U = rng.standard_normal((1, 1, n, n))
+    U = rng.standard_normal((1, len(zy), n, n))
     A = O.A_matrices(n, h, zy, zr, nu)
     s2 = O.alpha_scale(A)
     for alpha in [1e-12, 1e-3, 0.5]:
@@ -301,3 +303,35 @@ def test_band_residuals_partition_the_global_residual():
     one = O.invert(U, n, -1.2, h, zy, zr, nu, alphas=al, delta=0.5, tau=1.1, output="zeta", band_alpha_index=[3])
     fix = O.invert(U, n, -1.2, h, zy, zr, nu, alpha=al[3], output="zeta")
     assert np.allclose(one["zeta"], fix["zeta"], rtol=0, atol=1e-13 * np.abs(fix["zeta"]).max())
+
+
+# ------------------------------------------------------------------ truncated SVD (Sec. 5, the paper's best RA)
+def test_tsvd_matches_library_pseudo_inverse_and_limits():
+    """tsvd_solve against numpy.linalg.pinv with the matching cut-off, and its two limits."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((5, 3, 6)) * np.array([1.0, 0.1, 1e-3])[None, :, None]
+    Uh = rng.standard_normal((5, 3, 2)) + 1j * rng.standard_normal((5, 3, 2))
+    sig = np.linalg.svd(A, compute_uv=False)
+    for b in range(5):
+        for keep in (1, 2, 3):
+            # a level strictly between the kept and the dropped squared singular values
+            t = sig[b, keep - 1] ** 2 * 0.5 if keep == 3 else np.sqrt(sig[b, keep - 1] ** 2 * sig[b, keep] ** 2)
+            x = O.tsvd_solve(A[b:b + 1], Uh[b:b + 1], t)[0]
+            P = np.linalg.pinv(A[b], rcond=np.sqrt(t) / sig[b, 0])
+            assert rel(x, P @ Uh[b]) < 1e-10
+    assert np.allclose(O.tsvd_solve(A, Uh, 1e-30), np.linalg.pinv(A) @ Uh, rtol=0, atol=1e-9 * np.abs(np.linalg.pinv(A) @ Uh).max())
+    assert np.all(O.tsvd_solve(A, Uh, 10 * sig.max() ** 2) == 0)
+
+
+def test_tsvd_inversion_residual_is_monotone_and_reaches_the_data_norm():
+    """The squared residual grows with the truncation level; with every singular value truncated it is
+    ||U||^2 (the zero solution), and at M = 1 with none truncated it is 0 (an exact fit)."""
+    n, h, zy, zr, nu = 8, 0.25, [0.0], [0.3, 0.45, 0.6], [0.15] * 3
+    rng = np.random.default_rng(12)
+    U = rng.standard_normal((2, 1, n, n))
+    al = np.logspace(-9, 1, 11)
+    out = O.invert(U, n, -1.0, h, zy, zr, nu, alphas=al, delta=1.0, tau=1.1, output="none", ra="tsvd")
+    r = out["res2"]
+    assert np.all(np.diff(r) >= -1e-12 * r.max())
+    assert abs(r[-1] - np.sum(U ** 2)) < 1e-10 * np.sum(U ** 2)
+    assert r[0] < 1e-20 * np.sum(U ** 2)
