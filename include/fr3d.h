@@ -75,6 +75,9 @@ extern "C" {
 #define FR3D_ALPHA_DISCREPANCY 1
 #define FR3D_ALPHA_GIVEN 2        /* per-band indices into `alphas` supplied in alpha_idx (no sweep) */
 #define FR3D_ALPHA_LEARNED 3      /* per-band alpha predicted by a trained network (fr3d_mlp, below) */
+#define FR3D_RA_TIKHONOV 0 /* regularising algorithm: Tikhonov, regulariser alpha s^2 ||zeta~||^2 (Sec. 4) */
+#define FR3D_RA_TSVD 1     /* truncated SVD per frequency (Sec. 5, the paper's best RA): singular values
+                              with sigma^2 < alpha s^2 are dropped */
 #define FR3D_OUT_ZETA 0   /* output zeta_q per source parameter: [Q][M'][n][n] */
 #define FR3D_OUT_XI 1     /* output xi (Algorithm 1 step 4): [M'][n][n] */
 
@@ -129,6 +132,8 @@ typedef struct fr3d_invert_opts {
                               discrepancy bound of band b is tau delta sqrt(frequencies in b / n^2)
                               (white noise).  DISCREPANCY, GIVEN and LEARNED only, M = 1. */
   const fr3d_mlp* net;     /* LEARNED: the network (n_in == n_out == max(1, n_bands)); NULL otherwise */
+  int ra;                  /* FR3D_RA_TIKHONOV (0, default) or FR3D_RA_TSVD: alpha (or each candidate) is
+                              then the truncation level relative to s^2; every alpha mode but LEARNED */
 } fr3d_invert_opts;
 
 /* Step 1 for the kernel (Algorithm 1, Sec. 5): samples K at the periodic lags for every

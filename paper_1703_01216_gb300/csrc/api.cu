@@ -140,7 +140,7 @@ int choose_impl(Handle* H, const T* U, int Q, const double* alphas, int n_alpha,
   FR3D_TRY(ensure_ws(H, align_up(sizeof(C) * ps * Q * H->M)));
   C* Uh = reinterpret_cast<C*>(H->ws);
   FR3D_TRY(data_fft<T>(H, U, Q, Uh, st));
-  FR3D_TRY(alpha_tables(H, alphas, n_alpha, st));
+  FR3D_TRY(alpha_tables(H, alphas, n_alpha, FR3D_RA_TIKHONOV, st));
   const double thr2 = (tau * delta) * (tau * delta);
   FR3D_TRY(Ops<T>::alpha_choose(H, Uh, Q * H->M, n_alpha, &thr2, 1, alpha_idx, residuals, info, st));
   H->last_launches = 3;
@@ -199,6 +199,7 @@ int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
   if (H->M != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
   if (o->output != FR3D_OUT_XI && o->output != FR3D_OUT_ZETA) return FR3D_ERR_INVALID_ARG;
   if (o->n_bands < 0 || o->n_bands > FR3D_MAX_BANDS) return FR3D_ERR_INVALID_ARG;
+  if (o->ra != FR3D_RA_TIKHONOV && o->ra != FR3D_RA_TSVD) return FR3D_ERR_INVALID_ARG;
   if (o->alpha_mode == FR3D_ALPHA_FIXED) {
     if (!(o->alpha > 0) || !isfinite(o->alpha)) return FR3D_ERR_INVALID_ARG;
     if (o->n_bands > 1) return FR3D_ERR_INVALID_ARG;
@@ -211,7 +212,7 @@ int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
   } else if (o->alpha_mode == FR3D_ALPHA_LEARNED) {
     FR3D_TRY(check_alphas(o->alphas, o->n_alpha));
     if (!(o->delta > 0) || !isfinite(o->delta)) return FR3D_ERR_INVALID_ARG;
-    if (o->precision != FR3D_PREC_FP32) return FR3D_ERR_INVALID_ARG;
+    if (o->precision != FR3D_PREC_FP32 || o->ra != FR3D_RA_TIKHONOV) return FR3D_ERR_INVALID_ARG;
     if (!learned_net_fits(o->net, o->n_bands > 1 ? o->n_bands : 1)) return FR3D_ERR_INVALID_ARG;
   } else {
     return FR3D_ERR_INVALID_ARG;
@@ -241,7 +242,7 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
   const int nb = o->n_bands > 1 ? o->n_bands : 1;
   if (nb > 1) FR3D_TRY(ensure_bands(H, nb, nullptr));
   if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
-    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, o->ra, st));
     prof_mark(H, kStTable, st);
     int* idx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
     double thr2[FR3D_MAX_BANDS];
@@ -253,7 +254,7 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
     if constexpr (sizeof(T) == 4) D = H->D32;
     else D = H->D64;
   } else if (o->alpha_mode == FR3D_ALPHA_LEARNED) {
-    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, o->ra, st));
     prof_mark(H, kStTable, st);
     int* idx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
     if constexpr (sizeof(T) == 4) {
@@ -266,14 +267,14 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
     launches += 1;
     aidx = idx;
   } else if (o->alpha_mode == FR3D_ALPHA_GIVEN) {
-    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, o->ra, st));
     prof_mark(H, kStTable, st);
     aidx = o->alpha_idx;
     if constexpr (sizeof(T) == 4) D = H->D32;
     else D = H->D64;
     if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
   } else {
-    FR3D_TRY(fixed_table(H, o->alpha, st));
+    FR3D_TRY(fixed_table(H, o->alpha, o->ra, st));
     prof_mark(H, kStTable, st);
     aidx = H->zero_idx;
     if constexpr (sizeof(T) == 4) D = H->Dfix32;
@@ -333,12 +334,12 @@ int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** U
   if (nb > 1) FR3D_TRY(ensure_bands(H, nb, nullptr));
   if (o->alpha_mode == FR3D_ALPHA_LEARNED) return FR3D_ERR_INVALID_ARG;   // not in batched plans
   if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY || o->alpha_mode == FR3D_ALPHA_GIVEN) {
-    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, st));
+    FR3D_TRY(alpha_tables(H, o->alphas, o->n_alpha, o->ra, st));
     FR3D_TRY(ensure_partials(H));
     *Dd = H->Dd32;
     *aidx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
   } else {
-    FR3D_TRY(fixed_table(H, o->alpha, st));
+    FR3D_TRY(fixed_table(H, o->alpha, o->ra, st));
     *Dd = H->Ddfix32;
     *aidx = H->zero_idx;
   }

@@ -60,6 +60,7 @@ struct Handle {
   int tw_off[kNumLengths] = {0};
   // alpha tables, keyed by the candidate list
   std::vector<double> alpha_key;
+  int alpha_ra = -1;          // regularising algorithm of the alpha tables (FR3D_RA_*)
   double* Ft = nullptr;       // [C][n_alpha]  ((alpha s^2) / (nrm + alpha s^2))^2
   float* D32 = nullptr;       // [n_alpha][C]  1 / (n^2 (nrm + alpha s^2))
   float* Dd32 = nullptr;      // [n_alpha][n/2+1][n]  the same per half-spectrum bin
@@ -67,6 +68,7 @@ struct Handle {
   int alpha_cap = 0;
   // fixed-alpha table
   double fixed_key = -1.0;
+  int fixed_ra = -1;
   float* Dfix32 = nullptr;    // [C]
   float* Ddfix32 = nullptr;   // [n/2+1][n]
   double* Dfix64 = nullptr;   // [C]

@@ -60,8 +60,8 @@ int learned_alpha(Handle* H, const float2* Uh, int nplanes, int nb, double delta
                   const fr3d_mlp* net, int* aidx, float* feat, int* info, cudaStream_t st);
 
 // precision-independent table builders (alpha tables, fixed alpha)
-int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st);
-int fixed_table(Handle* H, double alpha, cudaStream_t st);
+int alpha_tables(Handle* H, const double* alphas, int n_alpha, int ra, cudaStream_t st);
+int fixed_table(Handle* H, double alpha, int ra, cudaStream_t st);
 int build_dense64(Handle* H, cudaStream_t st);
 
 }  // namespace fr3d

@@ -19,16 +19,29 @@ struct AlphaList {
   double a[FR3D_MAX_ALPHAS];
 };
 
-__global__ void k_alpha_tables(AlphaList al, int na, const double* __restrict__ nrm, const double* __restrict__ s2,
-                               int Cn, double inv_n2, double* __restrict__ Ft, float* __restrict__ D32,
-                               double* __restrict__ D64) {
+// Per class c (M = 1, a = A^(c), n_c = ||a||^2) and candidate k, the solution of a frequency of the class
+// is zeta~ = D a U~ (with the inverse DFT's 1/n^2 folded into D) and its squared residual is Ft |U~|^2:
+//   Tikhonov (ra = 0): D = 1 / (n_c + alpha s^2),            Ft = (alpha s^2 / (n_c + alpha s^2))^2;
+//   TSVD     (ra = 1): D = 1 / n_c if n_c >= alpha s^2 else 0, Ft = 0 if kept else 1
+// (the single singular value of the 1 x M' system is sqrt(n_c); kept, the fit is exact).
+__global__ void k_alpha_tables(AlphaList al, int na, int ra, const double* __restrict__ nrm,
+                               const double* __restrict__ s2, int Cn, double inv_n2, double* __restrict__ Ft,
+                               float* __restrict__ D32, double* __restrict__ D64) {
   const int total = na * Cn;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     const int c = idx / na, k = idx - c * na;
     const double as2 = al.a[k] * (*s2);
-    const double d = 1.0 / (nrm[c] + as2);
-    const double f = as2 * d;
-    if (Ft) Ft[(long)c * na + k] = f * f;
+    double d, f2;
+    if (ra == FR3D_RA_TSVD) {
+      const bool keep = nrm[c] >= as2;
+      d = keep ? 1.0 / nrm[c] : 0.0;
+      f2 = keep ? 0.0 : 1.0;
+    } else {
+      d = 1.0 / (nrm[c] + as2);
+      const double f = as2 * d;
+      f2 = f * f;
+    }
+    if (Ft) Ft[(long)c * na + k] = f2;
     D64[(long)k * Cn + c] = d * inv_n2;
     D32[(long)k * Cn + c] = (float)(d * inv_n2);
   }
@@ -52,8 +65,9 @@ __global__ void k_bin_bands(const unsigned char* __restrict__ cband, int n, int 
 
 }  // namespace
 
-int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) {
-  if ((int)H->alpha_key.size() == n_alpha && memcmp(H->alpha_key.data(), alphas, n_alpha * sizeof(double)) == 0)
+int alpha_tables(Handle* H, const double* alphas, int n_alpha, int ra, cudaStream_t st) {
+  if (H->alpha_ra == ra && (int)H->alpha_key.size() == n_alpha &&
+      memcmp(H->alpha_key.data(), alphas, n_alpha * sizeof(double)) == 0)
     return FR3D_OK;
   if (H->alpha_cap < n_alpha) {
     cudaFree(H->Ft);
@@ -76,10 +90,12 @@ int alpha_tables(Handle* H, const double* alphas, int n_alpha, cudaStream_t st) 
   for (int k = 0; k < n_alpha; ++k) al.a[k] = alphas[k];
   const double inv_n2 = 1.0 / ((double)H->n * H->n);
   const int total = n_alpha * H->C;
-  k_alpha_tables<<<(total + 255) / 256, 256, 0, st>>>(al, n_alpha, H->nrm, H->s2, H->C, inv_n2, H->Ft, H->D32, H->D64);
+  k_alpha_tables<<<(total + 255) / 256, 256, 0, st>>>(al, n_alpha, ra, H->nrm, H->s2, H->C, inv_n2, H->Ft, H->D32,
+                                                      H->D64);
   k_dense_d<<<1024, 256, 0, st>>>(H->D32, n_alpha, H->C, H->n, H->Dd32);
   FR3D_CUDA_TRY(cudaGetLastError());
   H->alpha_key.assign(alphas, alphas + n_alpha);
+  H->alpha_ra = ra;
   return FR3D_OK;
 }
 
@@ -135,8 +151,8 @@ int ensure_bands(Handle* H, int nb, std::vector<double>* count) {
   return FR3D_OK;
 }
 
-int fixed_table(Handle* H, double alpha, cudaStream_t st) {
-  if (H->fixed_key == alpha && H->Dfix32) return FR3D_OK;
+int fixed_table(Handle* H, double alpha, int ra, cudaStream_t st) {
+  if (H->fixed_key == alpha && H->fixed_ra == ra && H->Dfix32) return FR3D_OK;
   if (!H->Dfix32) {
     FR3D_CUDA_TRY(cudaMalloc(&H->Dfix32, sizeof(float) * H->C));
     FR3D_CUDA_TRY(cudaMalloc(&H->Dfix64, sizeof(double) * H->C));
@@ -145,11 +161,12 @@ int fixed_table(Handle* H, double alpha, cudaStream_t st) {
   AlphaList al;
   al.a[0] = alpha;
   const double inv_n2 = 1.0 / ((double)H->n * H->n);
-  k_alpha_tables<<<(H->C + 255) / 256, 256, 0, st>>>(al, 1, H->nrm, H->s2, H->C, inv_n2, nullptr, H->Dfix32,
+  k_alpha_tables<<<(H->C + 255) / 256, 256, 0, st>>>(al, 1, ra, H->nrm, H->s2, H->C, inv_n2, nullptr, H->Dfix32,
                                                      H->Dfix64);
   k_dense_d<<<256, 256, 0, st>>>(H->Dfix32, 1, H->C, H->n, H->Ddfix32);
   FR3D_CUDA_TRY(cudaGetLastError());
   H->fixed_key = alpha;
+  H->fixed_ra = ra;
   return FR3D_OK;
 }
 

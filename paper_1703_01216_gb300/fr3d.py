@@ -21,6 +21,7 @@ PREC_FP32, PREC_FP64 = 0, 1
 ALPHA_FIXED, ALPHA_DISCREPANCY, ALPHA_GIVEN, ALPHA_LEARNED = 0, 1, 2, 3
 MAX_BANDS = 16
 OUT_ZETA, OUT_XI = 0, 1
+RA_TIKHONOV, RA_TSVD = 0, 1
 INFO_ALPHA_NONE_SATISFIES, INFO_ALPHA_ALL_SATISFY, INFO_NONFINITE, INFO_LEARNED_OUT_OF_RANGE = 1, 2, 4, 8
 MAX_HIDDEN = 96
 K_DZ_INV_R = 0
@@ -44,7 +45,7 @@ class InvertOpts(ct.Structure):
     _fields_ = [("alpha_mode", ct.c_int), ("alpha", ct.c_double), ("alphas", _dp), ("n_alpha", ct.c_int),
                 ("delta", ct.c_double), ("tau", ct.c_double), ("output", ct.c_int), ("precision", ct.c_int),
                 ("sources", ct.POINTER(Sources)), ("alpha_idx", ct.c_void_p), ("residuals", ct.c_void_p),
-                ("info", ct.c_void_p), ("n_bands", ct.c_int), ("net", ct.c_void_p)]
+                ("info", ct.c_void_p), ("n_bands", ct.c_int), ("net", ct.c_void_p), ("ra", ct.c_int)]
 
 
 class Instance(ct.Structure):
@@ -232,8 +233,10 @@ class Opts:
     """Builds fr3d_invert_opts and keeps its host arrays alive."""
 
     def __init__(self, *, alpha=None, alphas=None, delta=0.0, tau=1.1, output=OUT_XI, precision=PREC_FP32,
-                 points=None, A0=1.0, alpha_idx=None, residuals=None, info=None, n_bands=1, given=False, net=None):
+                 points=None, A0=1.0, alpha_idx=None, residuals=None, info=None, n_bands=1, given=False, net=None,
+                 ra=RA_TIKHONOV):
         o = InvertOpts()
+        o.ra = int(ra)
         self._net = net
         if alpha is not None:
             o.alpha_mode, o.alpha = ALPHA_FIXED, float(alpha)

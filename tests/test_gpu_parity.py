@@ -291,3 +291,57 @@ def test_invert_per_band_discrepancy_and_given_bands(F, n, mp, q, nb):
     ref2 = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, sources=w.sources, A=A, n_bands=nb,
                     band_alpha_index=got)
     assert rel(host(xg), ref2["xi"]) <= 1e-4
+
+
+# ------------------------------------------------------------------ truncated SVD (Sec. 5)
+def _level_away_from_norms(A, s2, alpha):
+    """Shift a truncation level so that no class norm sits within 1e-9 of it (the keep decision is then
+    the same in any FP64 evaluation of the norms)."""
+    nrm = np.sum(A.reshape(A.shape[0] * A.shape[1], -1) ** 2, axis=1)
+    while np.min(np.abs(nrm - alpha * s2)) <= 1e-9 * alpha * s2:
+        alpha *= 1.0 + 1e-6
+    return alpha
+
+
+@pytest.mark.parametrize("n,mp,q", [(32, 8, 2), (48, 6, 1)])
+def test_tsvd_fixed_level_matches_oracle(F, n, mp, q):
+    w = I.make_workload(n, mp, q=q, n_incl=3, noise_level=0.02, seed=800 + n)
+    A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu)
+    s2 = O.alpha_scale(A)
+    U, delta, _ = noisy_data(w, A)
+    H = handle_for(F, w)
+    for alpha in (1e-3, 3e-2):
+        a = _level_away_from_norms(A, s2, alpha)
+        ref = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alpha=a, sources=w.sources, A=A, ra="tsvd")
+        for prec, dt, tol in [(F.PREC_FP32, torch.float32, 1e-4), (F.PREC_FP64, torch.float64, 1e-9)]:
+            xi = torch.empty((mp, n, n), dtype=dt, device="cuda")
+            F.invert(H, dev(U, dt), q, xi, F.Opts(alpha=a, points=w.sources, precision=prec, ra=F.RA_TSVD))
+            assert rel(host(xi), ref["xi"]) <= tol, (alpha, prec, rel(host(xi), ref["xi"]))
+
+
+@pytest.mark.parametrize("n,mp,q", [(32, 8, 1), (64, 10, 3)])
+def test_tsvd_discrepancy_matches_oracle(F, n, mp, q):
+    w = I.make_workload(n, mp, q=q, n_incl=4, noise_level=0.02, n_alpha=16, seed=820 + n)
+    A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu)
+    s2 = O.alpha_scale(A)
+    alphas = np.array([_level_away_from_norms(A, s2, a) for a in w.alphas])
+    U, delta, _ = noisy_data(w, A)
+    ref = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=alphas, delta=delta, tau=1.1, sources=w.sources,
+                   A=A, ra="tsvd")
+    H = handle_for(F, w)
+    idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    res = torch.zeros(alphas.size, dtype=torch.float64, device="cuda")
+    xi = torch.empty((mp, n, n), device="cuda")
+    F.invert(H, dev(U), q, xi, F.Opts(alphas=alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx,
+                                      residuals=res, ra=F.RA_TSVD))
+    r = host(res)
+    assert np.max(np.abs(r - ref["res2"]) / np.maximum(ref["res2"], 1e-30 * ref["res2"].max())) <= 1e-5
+    assert np.all(np.diff(ref["res2"]) >= 0)
+    got = int(idx.item())
+    _check_choice(got, ref["res2"], (1.1 * delta) ** 2, 1e-4)
+    if got == ref["alpha_index"]:
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+    # the same inversion with Tikhonov is a different result (the option is honoured)
+    xt = torch.empty_like(xi)
+    F.invert(H, dev(U), q, xt, F.Opts(alphas=alphas, delta=delta, tau=1.1, points=w.sources))
+    assert not torch.equal(xt, xi)
