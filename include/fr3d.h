@@ -84,6 +84,7 @@ extern "C" {
 #define FR3D_MAX_ALPHAS 128
 #define FR3D_MAX_BANDS 16
 #define FR3D_MAX_SOURCE_POINTS 256 /* total points over all source parameters q */
+#define FR3D_MAX_OBS_DEPTHS 64     /* M (observation depths) of fr3d_invert; M > 1 needs FP32 and n <= 384 */
 
 /* Flat-layer geometry (Sec. 3: R = R^2 x [h, H], Y = R^2 x [h_Y, H_Y]; Sec. 5 grids). */
 typedef struct fr3d_geometry {

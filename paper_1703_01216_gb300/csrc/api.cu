@@ -164,6 +164,7 @@ InvertPlan plan_invert(const Handle* H, int Q, bool host_io, int output) {
   const size_t per_j = ps_b * Q;
   const bool fused = sizeof(T) == 4 && fused_supported(n);
   int chunk = fused ? 0 : (int)std::max<size_t>(1, std::min<size_t>(H->Mp, kChunkBytes / per_j));
+  if (fused && H->M > 1) off = multi_ws_bytes(H, Q);   // the M > 1 path lays out its own workspace first
   if (fused) {
     p.chunk = H->Mp;
     p.t_off = off;
@@ -196,7 +197,12 @@ InvertPlan plan_invert(const Handle* H, int Q, bool host_io, int output) {
 int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
   if (!o || Q < 1) return FR3D_ERR_INVALID_ARG;
   if (!valid_precision(o->precision)) return FR3D_ERR_INVALID_ARG;
-  if (H->M != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
+  if (H->M > FR3D_MAX_OBS_DEPTHS) return FR3D_ERR_UNSUPPORTED_SIZE;
+  if (H->M > 1) {
+    // several observation depths: FP32 path with the fused inverse (eigen tables, multi.cu)
+    if (o->precision != FR3D_PREC_FP32 || !fused_supported(H->n)) return FR3D_ERR_UNSUPPORTED_SIZE;
+    if (o->alpha_mode == FR3D_ALPHA_LEARNED) return FR3D_ERR_INVALID_ARG;
+  }
   if (o->output != FR3D_OUT_XI && o->output != FR3D_OUT_ZETA) return FR3D_ERR_INVALID_ARG;
   if (o->n_bands < 0 || o->n_bands > FR3D_MAX_BANDS) return FR3D_ERR_INVALID_ARG;
   if (o->ra != FR3D_RA_TIKHONOV && o->ra != FR3D_RA_TSVD) return FR3D_ERR_INVALID_ARG;
@@ -229,6 +235,12 @@ template <typename T>
 int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out, const InvertPlan& p,
                 cudaStream_t st) {
   using C = typename Ops<T>::C;
+  if constexpr (sizeof(T) == 4) {
+    if (H->M > 1) {
+      if (o->output == FR3D_OUT_XI) FR3D_TRY(ensure_wtab(H, o->sources, st));
+      return invert_multi(H, U, Q, o, out, st);
+    }
+  }
   C* Uh = reinterpret_cast<C*>((char*)H->ws + p.uh_off);
   C* Tb = reinterpret_cast<C*>((char*)H->ws + p.t_off);
   int launches = 0;
@@ -379,8 +391,11 @@ extern "C" int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const dou
   FR3D_TRY(fr3d::check_alphas(alphas, n_alpha));
   if (!(delta >= 0) || !isfinite(delta) || !(tau > 0) || !isfinite(tau)) return FR3D_ERR_INVALID_ARG;
   Handle* H = &h->h;
-  if (H->M != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
   cudaStream_t st = (cudaStream_t)stream;
+  if (H->M > 1) {
+    if (H->M > FR3D_MAX_OBS_DEPTHS || precision != FR3D_PREC_FP32) return FR3D_ERR_UNSUPPORTED_SIZE;
+    return fr3d::choose_multi(H, (const float*)U, Q, alphas, n_alpha, delta, tau, alpha_idx, residuals, info, st);
+  }
   if (precision == FR3D_PREC_FP64)
     return fr3d::choose_impl<double>(H, (const double*)U, Q, alphas, n_alpha, delta, tau, alpha_idx, residuals,
                                      info, st);

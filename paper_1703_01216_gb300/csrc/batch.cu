@@ -46,7 +46,6 @@ int fused_tune_batched(int n, const FusedArgs* inst, const int2* map, int nclust
                        int* best);
 void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
                     float* out, int Q, FusedArgs* a);
-void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double* thr2);
 int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** Uh, const float** Dd, const int** aidx,
                          cudaStream_t st);
 

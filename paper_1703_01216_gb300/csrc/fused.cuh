@@ -98,13 +98,16 @@ struct FusedArgs {
   const float2* Uh;    // [Q][n/2+1][n] data spectra
   const float* A;      // [M' = j][n/2+1][n] dense kernel table
   const float* Dd;     // [n_alpha][n/2+1][n] dense solve weights
-  const int* aidx;     // chosen row of Dd per band
+  const int* aidx;     // chosen row of Dd per band (clamped to [0, na))
+  int na;              // rows of Dd
   const unsigned char* bbin;   // [n/2+1][n] band of every half-spectrum bin (nb > 1)
   int nb;              // bands (1: one alpha for the whole spectrum)
   const float* W;      // [Q][M'][n][n] combination weights V0_q / sum_q' V0_q'^2 (XI mode)
   float* out;          // XI: [M'][n][n]; ZETA: [Q][M'][n][n]
   const float2* tw_n;  // length-n twiddles
   int Q, j0, Mp;
+  const float2* Zs;    // NULL, or solved spectra [Q][M'][n/2+1][n] (1/n^2 folded in): then A, Dd, aidx
+                       // are not read and the column phase transforms Zs directly (M > 1 path)
 };
 
 template <int N, int MODE, int V>
@@ -133,7 +136,7 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
 
   // ---------------- set-up: twiddles and the q-invariant solve weights of the owned columns
   __shared__ int s_aidx[FR3D_MAX_BANDS];
-  if (tid < a.nb) s_aidx[tid] = a.aidx[tid];
+  if (tid < a.nb) s_aidx[tid] = min(max(a.aidx[tid], 0), a.na - 1);   // a caller-given index stays in the table
   __syncthreads();
   {
     const float* Aj = a.A + (long)j * ps;
@@ -143,7 +146,9 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
     build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
     // solve weight of bin o = kx n + ky: row aidx[band(o)] of Dd (one row when nb = 1); with bands the
     // band indices of all of this thread's bins are fetched first, then every weight in one round
-    if (a.nb == 1) {
+    if (a.Zs) {
+      // solved spectra: no weights
+    } else if (a.nb == 1) {
 #pragma unroll
       for (int b0 = 0; b0 < CLD; b0 += CB) {
         float wa[CB], wd[CB];
@@ -206,8 +211,18 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
       if (q > 0) cluster_wait();
     // ---------------- column phase: U~_q w_j loaded straight into the registers of the first pass of
     // the inverse column DFTs (no shared-memory round trip for the input)
+    const float2* Zj = a.Zs ? a.Zs + ((long)q * a.Mp + j) * ps : nullptr;
     auto ldc = [&](int col, int ky) -> float2 {
       const int e = col * N + ky;
+      if (Zj) {                   // solved spectrum of depth j (M > 1 path)
+        float2 v = __ldg(Zj + (long)c0 * N + e);
+        if (r == 0 && col == 0) {
+          const float2 un = __ldg(Zj + (long)L * N + ky);
+          v.x -= un.y;
+          v.y += un.x;
+        }
+        return v;
+      }
       const float2 u = __ldg(Zq + (long)c0 * N + e);
       const float w = wsm[e];
       float2 v = make_float2(u.x * w, u.y * w);

@@ -61,7 +61,7 @@ int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, cudaStream_t 
   }
   *v_out = 0;
   if (mode == 0) return FR3D_OK;
-  const TuneKey key{H->dev, H->n, nj, a.Q, xi ? 1 : 0};
+  const TuneKey key{H->dev, H->n, nj, a.Q, (xi ? 1 : 0) + (a.Zs ? 2 : 0)};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -121,6 +121,7 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   a.A = H->A32;
   a.Dd = Dd;
   a.aidx = aidx;
+  a.na = Dd == H->Ddfix32 ? 1 : std::max(1, (int)H->alpha_key.size());
   a.bbin = H->bbin;
   a.nb = nb;
   a.W = W;
@@ -129,6 +130,7 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   a.Q = Q;
   a.j0 = j0;
   a.Mp = H->Mp;
+  a.Zs = nullptr;
   const bool xi = output == FR3D_OUT_XI;
   int v = 0;
   FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, nj, xi, st, &v));
@@ -185,12 +187,37 @@ int fused_tune_batched(int n, const FusedArgs* inst, const int2* map, int nclust
   return FR3D_OK;
 }
 
+int inv_fused_presolved_f32(const Handle* H, const float2* Zs, const float* W, float* out, int Q, int output,
+                            cudaStream_t st) {
+  FusedArgs a;
+  a.Uh = nullptr;
+  a.A = nullptr;
+  a.Dd = nullptr;
+  a.aidx = H->zero_idx;
+  a.na = 1;
+  a.bbin = nullptr;
+  a.nb = 1;
+  a.W = W;
+  a.out = out;
+  a.tw_n = H->tw32 + twiddle_offset(H, H->n);
+  a.Q = Q;
+  a.j0 = 0;
+  a.Mp = H->Mp;
+  a.Zs = Zs;
+  const bool xi = output == FR3D_OUT_XI;
+  int v = 0;
+  FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, H->Mp, xi, st, &v));
+  const_cast<Handle*>(H)->fused_var = v;
+  return launch_variant(v, H->n, xi, a, H->Mp, st);
+}
+
 void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
                     float* out, int Q, FusedArgs* a) {
   a->Uh = Uh;
   a->A = H->A32;
   a->Dd = Dd;
   a->aidx = aidx;
+  a->na = Dd == H->Ddfix32 ? 1 : std::max(1, (int)H->alpha_key.size());
   a->bbin = H->bbin;
   a->nb = nb;
   a->W = W;
@@ -199,6 +226,7 @@ void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const in
   a->Q = Q;
   a->j0 = 0;
   a->Mp = H->Mp;
+  a->Zs = nullptr;
 }
 
 int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st) {

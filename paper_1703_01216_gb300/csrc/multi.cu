@@ -1,0 +1,550 @@
+// Several observation depths (M > 1): the per-frequency systems A^(m) zeta~ = U~^(m) of Eq. (6) are
+// M x M' instead of rows, so step 2 needs more than a division per frequency class.
+//
+// Cold (once per handle, FP64): for every frequency class c the Gram matrix G_c = A_c A_c^T (M x M) and
+// its eigendecomposition G_c = U_c diag(lambda_c) U_c^T by the cyclic Jacobi method (rotation pairs of a
+// round are disjoint, so their angles come from the same G and the rotations apply together), and
+// W_c = U_c^T A_c (M x M').  With p = U_c^T U~ the Tikhonov solution and its squared residual are
+//     zeta~ = A_c^T (G_c + alpha s^2 I)^-1 U~ = W_c^T diag(g) p,   g_i = 1 / (lambda_i + alpha s^2),
+//     ||A_c zeta~ - U~||^2 = sum_i (alpha s^2 / (lambda_i + alpha s^2))^2 |p_i|^2,
+// (the dual form of the Tikhonov normal equation, an exact identity for any M, M'), and the truncated
+// SVD keeps the components with lambda_i >= alpha s^2: g_i = 1 / lambda_i, residual weight 0, else 0 and 1.
+// Hot path (FP32 data, FP64 sums): data FFT of all Q M planes; per class the projection p = U_c^T U~ in
+// place and the class powers P_ci = sum wt |p_i|^2; the alpha rule over sum_c sum_i F(lambda_ci) P_ci;
+// per class the solve zeta~_j = sum_i W_c[i][j] g_i p_i written as spectra [q][j][bin]; the fused
+// inverse DFT + combination reading those spectra.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fused.cuh"
+#include "ops.cuh"
+
+namespace fr3d {
+
+namespace {
+
+constexpr int kMaxM = FR3D_MAX_OBS_DEPTHS;  // observation depths handled by the M > 1 path
+constexpr int kSweeps = 30;                // Jacobi sweep limit (convergence is checked every sweep)
+
+__device__ inline void class_pq_m(int c, int& p, int& q) {
+  p = (int)((sqrtf(8.f * (float)c + 1.f) - 1.f) * 0.5f);
+  while ((p + 1) * (p + 2) / 2 <= c) ++p;
+  while (p * (p + 1) / 2 > c) --p;
+  q = c - p * (p + 1) / 2;
+}
+
+// One CTA per class.  Shared memory: G [Me][Me], U [Me][Me] (Me = M rounded up to even), FP64.
+__global__ void __launch_bounds__(256) k_class_eig(const double* __restrict__ A64, int M, int Mp, int Cn,
+                                                   double* __restrict__ lam, float* __restrict__ Ut,
+                                                   float* __restrict__ W, int* __restrict__ sweeps_out) {
+  extern __shared__ double smd[];
+  const int c = blockIdx.x;
+  const int Me = (M + 1) & ~1;
+  double* G = smd;                 // [Me][Me]
+  double* U = G + Me * Me;         // [Me][Me], column i = eigenvector i
+  __shared__ double cs[kMaxM / 2 + 1][2];
+  __shared__ int pr[kMaxM / 2 + 1][2];
+  __shared__ double off_s, diag_s;
+  __shared__ double red[256][2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double* A = A64 + (long)c * M * Mp;
+  // G = A A^T (padded with an identity row/column when M is odd: the pad never couples)
+  for (int e = tid; e < Me * Me; e += nt) {
+    const int a = e / Me, b = e % Me;
+    double s = 0.0;
+    if (a < M && b < M) {
+      for (int j = 0; j < Mp; ++j) s = fma(A[(long)a * Mp + j], A[(long)b * Mp + j], s);
+    } else if (a == b) {
+      s = 0.0;
+    }
+    G[e] = s;
+    U[e] = a == b ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < kSweeps; ++sweep) {
+    // convergence: off-diagonal mass against the diagonal (block reduction)
+    {
+      double off = 0.0, dg = 0.0;
+      for (int e = tid; e < Me * Me; e += nt) {
+        const double v = G[e] * G[e];
+        if (e / Me == e % Me) dg += v;
+        else off += v;
+      }
+      red[tid][0] = off;
+      red[tid][1] = dg;
+      __syncthreads();
+      for (int k = nt / 2; k > 0; k >>= 1) {
+        if (tid < k) {
+          red[tid][0] += red[tid + k][0];
+          red[tid][1] += red[tid + k][1];
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        off_s = red[0][0];
+        diag_s = red[0][1];
+      }
+      __syncthreads();
+    }
+    if (!(off_s > 1e-30 * diag_s) || Me == 1) break;
+    // round-robin tournament: Me - 1 rounds of Me / 2 disjoint pairs
+    for (int round = 0; round < Me - 1; ++round) {
+      if (tid < Me / 2) {
+        // player positions: 0 fixed, the others rotate
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (Me - 1); };
+        int p = player(tid), q = player(Me - 1 - tid);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        pr[tid][0] = p;
+        pr[tid][1] = q;
+        const double gpq = G[p * Me + q], gpp = G[p * Me + p], gqq = G[q * Me + q];
+        double cth = 1.0, sth = 0.0;
+        if (gpq != 0.0) {
+          // rotation that zeroes G[p][q] (Rutishauser's stable form)
+          const double tau = (gqq - gpp) / (2.0 * gpq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          cth = 1.0 / sqrt(1.0 + t * t);
+          sth = t * cth;
+        }
+        cs[tid][0] = cth;
+        cs[tid][1] = sth;
+      }
+      __syncthreads();
+      // rows: G <- J^T G (pair k rotates rows p, q at every column b)
+      for (int e = tid; e < (Me / 2) * Me; e += nt) {
+        const int k = e / Me, b = e % Me;
+        const int p = pr[k][0], q = pr[k][1];
+        const double cth = cs[k][0], sth = cs[k][1];
+        const double gp = G[p * Me + b], gq = G[q * Me + b];
+        G[p * Me + b] = cth * gp - sth * gq;
+        G[q * Me + b] = sth * gp + cth * gq;
+      }
+      __syncthreads();
+      // columns: G <- G J, and U <- U J
+      for (int e = tid; e < (Me / 2) * Me; e += nt) {
+        const int k = e / Me, a = e % Me;
+        const int p = pr[k][0], q = pr[k][1];
+        const double cth = cs[k][0], sth = cs[k][1];
+        const double gp = G[a * Me + p], gq = G[a * Me + q];
+        G[a * Me + p] = cth * gp - sth * gq;
+        G[a * Me + q] = sth * gp + cth * gq;
+        const double up = U[a * Me + p], uq = U[a * Me + q];
+        U[a * Me + p] = cth * up - sth * uq;
+        U[a * Me + q] = sth * up + cth * uq;
+      }
+      __syncthreads();
+    }
+  }
+  // lambda_i = G[i][i] (clamped at 0: the Gram matrix is positive semidefinite), Ut[i][k] = U[k][i],
+  // W[i][j] = sum_k U[k][i] A[k][j]
+  for (int i = tid; i < M; i += nt) lam[(long)c * M + i] = fmax(G[i * Me + i], 0.0);
+  for (int e = tid; e < M * M; e += nt) {
+    const int i = e / M, k = e % M;
+    Ut[(long)c * M * M + e] = (float)U[k * Me + i];
+  }
+  for (int e = tid; e < M * Mp; e += nt) {
+    const int i = e / Mp, j = e % Mp;
+    double s = 0.0;
+    for (int k = 0; k < M; ++k) s = fma(U[k * Me + i], A[(long)k * Mp + j], s);
+    W[(long)c * M * Mp + e] = (float)s;
+  }
+  if (tid == 0 && sweeps_out) atomicMax(sweeps_out, sweep);
+}
+
+// members (kx, ky) of class c in the stored half spectrum and their weights (1 on the kx = 0 and
+// kx = n/2 rows, whose mirror bins are stored too, 2 elsewhere)
+__device__ inline int class_members(int c, int n, int* kxs, int* kys, float* wts) {
+  int p, q, nm = 0;
+  class_pq_m(c, p, q);
+  kxs[nm] = p; kys[nm++] = q;
+  if (q != 0 && 2 * q != n) { kxs[nm] = p; kys[nm++] = n - q; }
+  if (p != q) {
+    kxs[nm] = q; kys[nm++] = p;
+    if (p != 0 && 2 * p != n) { kxs[nm] = q; kys[nm++] = n - p; }
+  }
+  for (int m = 0; m < nm; ++m) wts[m] = (kxs[m] == 0 || 2 * kxs[m] == n) ? 1.f : 2.f;
+  return nm;
+}
+
+// Projection p = U_c^T U~ in place for every member bin and plane set q, and the class powers
+// P_ci = sum over members and q of wt |p_i|^2 (FP32 terms in a fixed order, stored in FP64).
+// One CTA per class; Uh planes are [q][i] (plane q M + i).
+__global__ void __launch_bounds__(256) k_project(float2* __restrict__ Uh, long ps, int Q, int M, int n,
+                                                 const float* __restrict__ Ut, double* __restrict__ Pc) {
+  __shared__ float ut[kMaxM * kMaxM];
+  __shared__ float2 x[4 * kMaxM], y[4 * kMaxM];
+  __shared__ float pw[kMaxM];
+  __shared__ int kxs[4], kys[4];
+  __shared__ float wts[4];
+  __shared__ int nm_s;
+  const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    int kx[4], ky[4];
+    float wt[4];
+    const int nm = class_members(c, n, kx, ky, wt);
+    for (int m = 0; m < nm; ++m) {
+      kxs[m] = kx[m];
+      kys[m] = ky[m];
+      wts[m] = wt[m];
+    }
+    nm_s = nm;
+  }
+  for (int e = tid; e < M * M; e += nt) ut[e] = __ldg(Ut + (long)c * M * M + e);
+  for (int i = tid; i < M; i += nt) pw[i] = 0.f;
+  __syncthreads();
+  const int nm = nm_s;
+  for (int q = 0; q < Q; ++q) {
+    for (int e = tid; e < nm * M; e += nt) {
+      const int m = e / M, k = e % M;
+      x[e] = Uh[((long)q * M + k) * ps + (long)kxs[m] * n + kys[m]];
+    }
+    __syncthreads();
+    for (int e = tid; e < nm * M; e += nt) {
+      const int m = e / M, i = e % M;
+      float2 s = make_float2(0.f, 0.f);
+      for (int k = 0; k < M; ++k) {
+        const float u = ut[i * M + k];
+        s.x = fmaf(u, x[m * M + k].x, s.x);
+        s.y = fmaf(u, x[m * M + k].y, s.y);
+      }
+      y[e] = s;
+      Uh[((long)q * M + i) * ps + (long)kxs[m] * n + kys[m]] = s;
+    }
+    __syncthreads();
+    for (int i = tid; i < M; i += nt) {
+      float s = pw[i];
+      for (int m = 0; m < nm; ++m) s = fmaf(wts[m], y[m * M + i].x * y[m * M + i].x + y[m * M + i].y * y[m * M + i].y, s);
+      pw[i] = s;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < M; i += nt) Pc[(long)c * M + i] = (double)pw[i];
+}
+
+struct MAlphas {
+  double a[FR3D_MAX_ALPHAS];
+};
+
+// residual weight of component (lambda, t = alpha s^2): Tikhonov (t / (lambda + t))^2, TSVD [lambda < t]
+__device__ inline float resid_weight(float lam, float t, int ra) {
+  if (ra == FR3D_RA_TSVD) return lam < t ? 1.f : 0.f;
+  const float f = t / (lam + t);
+  return f * f;
+}
+
+constexpr int kMCPB = 64;   // classes per block of the residual sums
+
+// Block partials of r_b^2(alpha_k) * n^2 = sum_{c in b} sum_i F(lambda_ci, alpha_k) P_ci: the sum over
+// i in FP32 (M terms), over classes in FP64; thread per candidate.
+__global__ void __launch_bounds__(128) k_alpha_m_partial(const double* __restrict__ lam, const double* __restrict__ Pc,
+                                                         int M, int Cn, const unsigned char* __restrict__ cband,
+                                                         int nb, MAlphas al, const double* __restrict__ s2,
+                                                         int na, int ra, double* __restrict__ partials) {
+  __shared__ float sl[kMCPB * kMaxM], sp[kMCPB * kMaxM];
+  const int c0 = blockIdx.x * kMCPB, ncl = min(kMCPB, Cn - c0);
+  for (int e = threadIdx.x; e < ncl * M; e += blockDim.x) {
+    sl[e] = (float)lam[(long)c0 * M + e];
+    sp[e] = (float)Pc[(long)c0 * M + e];
+  }
+  __syncthreads();
+  const int k = threadIdx.x;
+  if (k >= na) return;
+  const float t = (float)(al.a[k] * (*s2));
+  double acc[FR3D_MAX_BANDS];
+  for (int b = 0; b < nb; ++b) acc[b] = 0.0;
+  for (int cc = 0; cc < ncl; ++cc) {
+    float f = 0.f;
+    for (int i = 0; i < M; ++i) f = fmaf(resid_weight(sl[cc * M + i], t, ra), sp[cc * M + i], f);
+    acc[nb > 1 ? (int)cband[c0 + cc] : 0] += (double)f;
+  }
+  for (int b = 0; b < nb; ++b) partials[((long)blockIdx.x * nb + b) * na + k] = acc[b];
+}
+
+// Sum of the partials (fixed order), r^2 = sum / n^2, and the discrepancy choice per band (one warp
+// per band: ballots of r^2 <= thr, the largest index wins).
+struct MThr {
+  double t[FR3D_MAX_BANDS];
+};
+__global__ void __launch_bounds__(256) k_alpha_m_finish(const double* __restrict__ partials, int nblk, int nb, int na,
+                                                        double inv_n2, MThr thr, int* __restrict__ aidx,
+                                                        double* __restrict__ res_out, int* __restrict__ info) {
+  __shared__ double r2[FR3D_MAX_BANDS * FR3D_MAX_ALPHAS];
+  __shared__ int flg[FR3D_MAX_BANDS];
+  const int tid = threadIdx.x, O = nb * na;
+  for (int o = tid; o < O; o += blockDim.x) {
+    double s = 0.0;
+    for (int blk = 0; blk < nblk; ++blk) s += partials[(long)blk * O + o];
+    r2[o] = s * inv_n2;
+    if (res_out) res_out[o] = s * inv_n2;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int b = warp; b < nb; b += blockDim.x / 32) {
+    int best = -1, ok = 0, flags = 0;
+    for (int k0 = 0; k0 < na; k0 += 32) {
+      const int k = k0 + lane;
+      bool good = false, bad = false;
+      if (k < na) {
+        const double v = r2[b * na + k];
+        bad = ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
+        good = v <= thr.t[b];
+      }
+      const unsigned bg = __ballot_sync(0xffffffffu, good);
+      if (__ballot_sync(0xffffffffu, bad)) flags |= FR3D_INFO_NONFINITE;
+      if (bg) best = k0 + 31 - __clz(bg);
+      ok += __popc(bg);
+    }
+    if (best < 0) {
+      best = 0;
+      flags |= FR3D_INFO_ALPHA_NONE_SATISFIES;
+    } else if (ok == na) {
+      flags |= FR3D_INFO_ALPHA_ALL_SATISFY;
+    }
+    if (lane == 0) {
+      aidx[b] = best;
+      flg[b] = flags;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int flags = 0;
+    for (int b = 0; b < nb; ++b) flags |= flg[b];
+    if (info) *info = flags;
+  }
+}
+
+// zeta~_j(bin, q) = sum_i W_c[i][j] g_i p_i(bin, q) / n^2 with g_i of the class's band alpha, written to
+// the spectra Zs [q][j][bin].  One CTA per class; the projected data of all members and of a chunk of
+// source parameters are staged in shared memory, W_c is read once per chunk.
+constexpr int kSolveQC = 8;   // source parameters per chunk
+__global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, long ps, int Q, int M, int Mp, int n,
+                                                 const double* __restrict__ lam, const float* __restrict__ W,
+                                                 const unsigned char* __restrict__ cband, int nb,
+                                                 const int* __restrict__ aidx, int na, MAlphas al,
+                                                 const double* __restrict__ s2, int ra, double inv_n2,
+                                                 float2* __restrict__ Zs) {
+  __shared__ float2 x[kSolveQC * 4 * kMaxM];
+  __shared__ float g[kMaxM];
+  __shared__ long ob[4];
+  __shared__ int nm_s;
+  const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    int kx[4], ky[4];
+    float wt[4];
+    const int nm = class_members(c, n, kx, ky, wt);
+    for (int m = 0; m < nm; ++m) ob[m] = (long)kx[m] * n + ky[m];
+    nm_s = nm;
+  }
+  if (tid < M) {
+    const int k = min(max(aidx[nb > 1 ? (int)cband[c] : 0], 0), na - 1);   // caller-given indices stay in range
+    const double t = al.a[k] * (*s2);
+    const double l = lam[(long)c * M + tid];
+    double gi;
+    if (ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? 1.0 / l : 0.0;
+    else gi = 1.0 / (l + t);
+    g[tid] = (float)(gi * inv_n2);
+  }
+  __syncthreads();
+  const int nm = nm_s;
+  const float* Wc = W + (long)c * M * Mp;
+  for (int q0 = 0; q0 < Q; q0 += kSolveQC) {
+    const int qc = min(kSolveQC, Q - q0);
+    for (int e = tid; e < qc * nm * M; e += nt) {
+      const int qq = e / (nm * M), m = (e / M) % nm, i = e % M;
+      const float2 v = P[((long)(q0 + qq) * M + i) * ps + ob[m]];
+      x[e] = make_float2(v.x * g[i], v.y * g[i]);
+    }
+    __syncthreads();
+    for (int j = tid; j < Mp; j += nt) {
+      float2 z[kSolveQC * 4];
+#pragma unroll
+      for (int e = 0; e < kSolveQC * 4; ++e) z[e] = make_float2(0.f, 0.f);
+      for (int i = 0; i < M; ++i) {
+        const float w = __ldg(Wc + (long)i * Mp + j);
+#pragma unroll
+        for (int e = 0; e < kSolveQC * 4; ++e)
+          if (e < qc * nm) {
+            z[e].x = fmaf(w, x[e * M + i].x, z[e].x);
+            z[e].y = fmaf(w, x[e * M + i].y, z[e].y);
+          }
+      }
+#pragma unroll
+      for (int e = 0; e < kSolveQC * 4; ++e)
+        if (e < qc * nm) {
+          const int qq = e / nm, m = e % nm;
+          Zs[((long)(q0 + qq) * Mp + j) * ps + ob[m]] = z[e];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// Eigen tables of every class (built on the first call with M > 1, synchronously).
+int ensure_multi_tables(Handle* H, cudaStream_t st) {
+  if (H->mlam) return FR3D_OK;
+  const int M = H->M, Mp = H->Mp, C = H->C;
+  double* lam = nullptr;
+  float *Ut = nullptr, *W = nullptr;
+  int* sweeps = nullptr;
+  cudaError_t e = cudaMalloc(&lam, sizeof(double) * C * M);
+  if (e == cudaSuccess) e = cudaMalloc(&Ut, sizeof(float) * C * M * M);
+  if (e == cudaSuccess) e = cudaMalloc(&W, sizeof(float) * (size_t)C * M * Mp);
+  if (e == cudaSuccess) e = cudaMalloc(&sweeps, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(sweeps, 0, sizeof(int), st);
+  const int Me = (M + 1) & ~1;
+  const size_t sm = sizeof(double) * 2 * Me * Me;
+  int rc = e == cudaSuccess ? FR3D_OK : (e == cudaErrorMemoryAllocation ? FR3D_ERR_OOM : FR3D_ERR_CUDA);
+  if (rc == FR3D_OK) rc = smem_optin(reinterpret_cast<const void*>(k_class_eig), sm);
+  if (rc == FR3D_OK) {
+    k_class_eig<<<C, 256, sm, st>>>(H->A64, M, Mp, C, lam, Ut, W, sweeps);
+    int sw = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&sw, sweeps, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = FR3D_ERR_CUDA;
+    H->m_sweeps = sw;
+  }
+  cudaFree(sweeps);
+  if (rc != FR3D_OK) {
+    cudaFree(lam);
+    cudaFree(Ut);
+    cudaFree(W);
+    return rc;
+  }
+  H->mlam = lam;
+  H->mUt = Ut;
+  H->mW = W;
+  return FR3D_OK;
+}
+
+// workspace of invert_multi: data spectra [Q][M], solved spectra [Q][M'], class powers [C][M]
+size_t multi_ws_bytes(const Handle* H, int Q) {
+  const size_t ps = (size_t)(H->n / 2 + 1) * H->n;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return up(sizeof(float2) * ps * Q * H->M) + up(sizeof(float2) * ps * Q * H->Mp) + up(sizeof(double) * H->C * H->M);
+}
+
+namespace {
+
+struct MultiWs {
+  float2* Uh;   // [Q][M] half spectra, projected in place
+  float2* Zs;   // [Q][M'] solved spectra
+  double* Pc;   // [C][M] class powers
+};
+
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int multi_ws(Handle* H, int Q, bool with_zs, MultiWs* w) {
+  const long ps = (long)(H->n / 2 + 1) * H->n;
+  const size_t ub = up256(sizeof(float2) * ps * Q * H->M);
+  const size_t zb = with_zs ? up256(sizeof(float2) * ps * Q * H->Mp) : 0;
+  const size_t pb = up256(sizeof(double) * H->C * H->M);
+  FR3D_TRY(ensure_ws(H, std::max(ub + zb + pb, with_zs ? multi_ws_bytes(H, Q) : 0)));
+  w->Uh = reinterpret_cast<float2*>(H->ws);
+  w->Zs = with_zs ? reinterpret_cast<float2*>((char*)H->ws + ub) : nullptr;
+  w->Pc = reinterpret_cast<double*>((char*)H->ws + ub + zb);
+  return FR3D_OK;
+}
+
+// data spectra of every (q, i) plane and their projection onto the class eigenvectors
+int multi_data(Handle* H, const float* U, int Q, const MultiWs& w, int* launches, cudaStream_t st) {
+  const long ps = (long)(H->n / 2 + 1) * H->n;
+  FR3D_TRY(Ops<float>::row_r2c(H, U, (long)H->n * H->n, w.Uh, Q * H->M, st));
+  prof_mark(H, kStRowR2C, st);
+  FR3D_TRY(Ops<float>::col_plain(H, w.Uh, w.Uh, Q * H->M, false, st));
+  prof_mark(H, kStColFwd, st);
+  k_project<<<H->C, 256, 0, st>>>(w.Uh, ps, Q, H->M, H->n, H->mUt, w.Pc);
+  FR3D_CUDA_TRY(cudaGetLastError());
+  prof_mark(H, kStOther, st);
+  *launches += 3;
+  return FR3D_OK;
+}
+
+int multi_alpha(Handle* H, const MultiWs& w, const double* alphas, int na, int ra, int nb, const double* thr2,
+                int* aidx, double* residuals, int* info, cudaStream_t st) {
+  FR3D_TRY(ensure_partials(H));
+  MAlphas al;
+  for (int k = 0; k < na; ++k) al.a[k] = alphas[k];
+  const int nblk = (H->C + kMCPB - 1) / kMCPB;
+  k_alpha_m_partial<<<nblk, 128, 0, st>>>(H->mlam, w.Pc, H->M, H->C, H->cband, nb, al, H->s2, na, ra, H->partials);
+  MThr t;
+  for (int b = 0; b < nb; ++b) t.t[b] = thr2[b];
+  k_alpha_m_finish<<<1, 256, 0, st>>>(H->partials, nblk, nb, na, 1.0 / ((double)H->n * H->n), t, aidx, residuals,
+                                      info);
+  FR3D_CUDA_TRY(cudaGetLastError());
+  prof_mark(H, kStAlpha, st);
+  return FR3D_OK;
+}
+
+}  // namespace
+
+// Algorithm 1 for M > 1 (FP32 data and FFTs, FP64 eigen tables and residual sums).
+// The combination table (XI) is built by the caller.
+int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, float* out, cudaStream_t st) {
+  FR3D_TRY(ensure_multi_tables(H, st));
+  const int nb = o->n_bands > 1 ? o->n_bands : 1;
+  std::vector<double> count;
+  FR3D_TRY(ensure_bands(H, nb, &count));
+  MultiWs w;
+  FR3D_TRY(multi_ws(H, Q, true, &w));
+  int launches = 0;
+  prof_begin(H, st);
+  FR3D_TRY(multi_data(H, U, Q, w, &launches, st));
+  MAlphas al;
+  const int* aidx;
+  if (o->alpha_mode == FR3D_ALPHA_FIXED) {
+    al.a[0] = o->alpha;
+    aidx = H->zero_idx;
+    if (o->alpha_idx) FR3D_CUDA_TRY(cudaMemsetAsync(o->alpha_idx, 0, sizeof(int), st));
+    if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
+  } else {
+    for (int k = 0; k < o->n_alpha; ++k) al.a[k] = o->alphas[k];
+    if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
+      int* idx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
+      double thr2[FR3D_MAX_BANDS];
+      band_thresholds(H, o, nb, thr2);
+      FR3D_TRY(multi_alpha(H, w, o->alphas, o->n_alpha, o->ra, nb, thr2, idx, o->residuals, o->info, st));
+      launches += 2;
+      aidx = idx;
+    } else {
+      aidx = o->alpha_idx;
+      if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
+    }
+  }
+  const long ps = (long)(H->n / 2 + 1) * H->n;
+  const int na = o->alpha_mode == FR3D_ALPHA_FIXED ? 1 : o->n_alpha;
+  k_solve_m<<<H->C, 256, 0, st>>>(w.Uh, ps, Q, H->M, H->Mp, H->n, H->mlam, H->mW, H->cband, nb, aidx, na, al, H->s2,
+                                  o->ra, 1.0 / ((double)H->n * H->n), w.Zs);
+  FR3D_CUDA_TRY(cudaGetLastError());
+  prof_mark(H, kStColSolve, st);
+  FR3D_TRY(inv_fused_presolved_f32(H, w.Zs, H->wtab, out, Q, o->output, st));
+  prof_mark(H, kStFused, st);
+  H->last_launches = launches + 2;
+  return FR3D_OK;
+}
+
+// Discrepancy choice alone for M > 1 (fr3d_choose_alpha): data FFT, projection, residual sums.
+int choose_multi(Handle* H, const float* U, int Q, const double* alphas, int na, double delta, double tau,
+                 int* aidx, double* residuals, int* info, cudaStream_t st) {
+  FR3D_TRY(ensure_multi_tables(H, st));
+  FR3D_TRY(ensure_bands(H, 1, nullptr));
+  MultiWs w;
+  FR3D_TRY(multi_ws(H, Q, false, &w));
+  int launches = 0;
+  prof_begin(H, st);
+  FR3D_TRY(multi_data(H, U, Q, w, &launches, st));
+  const double thr2 = (tau * delta) * (tau * delta);
+  FR3D_TRY(multi_alpha(H, w, alphas, na, FR3D_RA_TIKHONOV, 1, &thr2, aidx, residuals, info, st));
+  H->last_launches = launches + 2;
+  return FR3D_OK;
+}
+
+}  // namespace fr3d

@@ -59,6 +59,18 @@ bool learned_net_fits(const fr3d_mlp* net, int nb);
 int learned_alpha(Handle* H, const float2* Uh, int nplanes, int nb, double delta, const double* alphas, int na,
                   const fr3d_mlp* net, int* aidx, float* feat, int* info, cudaStream_t st);
 
+// several observation depths (multi.cu): eigen tables of every class, the inversion and the alpha
+// choice, and the workspace bytes the inversion lays out from the start of the handle's workspace
+int ensure_multi_tables(Handle* H, cudaStream_t st);
+size_t multi_ws_bytes(const Handle* H, int Q);
+int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, float* out, cudaStream_t st);
+int choose_multi(Handle* H, const float* U, int Q, const double* alphas, int na, double delta, double tau, int* aidx,
+                 double* residuals, int* info, cudaStream_t st);
+void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double* thr2);
+// fused inverse DFT + combination of already solved spectra Zs [Q][M'][n/2+1][n] (1/n^2 folded in)
+int inv_fused_presolved_f32(const Handle* H, const float2* Zs, const float* W, float* out, int Q, int output,
+                            cudaStream_t st);
+
 // precision-independent table builders (alpha tables, fixed alpha)
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, int ra, cudaStream_t st);
 int fixed_table(Handle* H, double alpha, int ra, cudaStream_t st);

@@ -1,0 +1,151 @@
+"""Several observation depths (M > 1): the eigen-table path of step 2 against the FP64 oracle's
+per-frequency QR (Tikhonov) and SVD (TSVD) solutions.
+
+Tolerances: reconstruction 1e-4 relative at fixed alpha >= 1e-4 (FP32 data spectra, FP32 projected
+components and solve tables, amplified by at most 1/(2 sqrt(alpha))); squared-residual curves 1e-5 per
+candidate (FP32 component terms summed per class, FP64 over classes).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1703_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1703_01216_gb300 import build, fr3d
+    assert torch.cuda.is_available()
+    build.build()
+    fr3d.load()
+    return fr3d
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def _problem(n, mp, q, m, seed, noise=0.02, n_alpha=12):
+    w = I.make_workload(n, mp, q=q, m_obs=m, n_incl=3, noise_level=noise, n_alpha=n_alpha, seed=seed)
+    A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu)
+    zeta = O.zeta_from_xi(w.xi_true, w.sources, n, w.x0, w.h, w.zr)
+    U = O.forward_dft(zeta, n, w.h, w.zy, w.zr, w.nu, A=A)
+    nz = w.noise * (noise * np.linalg.norm(U) / np.linalg.norm(w.noise))
+    return w, A, U + nz, float(np.linalg.norm(nz))
+
+
+def _levels_away_from_spectrum(A, s2, alphas, gap=1e-4):
+    """Shift TSVD levels so that no squared singular value of any frequency lies within `gap` (relative)
+    of a level: the keep decision is then the same for the oracle's SVD and the GPU's Gram eigenvalues."""
+    L = A.shape[0]
+    sig2 = np.linalg.svd(A.reshape(L * L, A.shape[2], A.shape[3]), compute_uv=False).ravel() ** 2
+    out = []
+    for a in alphas:
+        while np.min(np.abs(sig2 - a * s2)) <= gap * a * s2:
+            a *= 1.0 + 3 * gap
+        out.append(a)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n,mp,q,m", [(32, 8, 1, 3), (48, 6, 2, 4), (32, 3, 1, 6)])
+@pytest.mark.parametrize("output", ["xi", "zeta"])
+def test_fixed_alpha_tikhonov_matches_oracle(F, n, mp, q, m, output):
+    w, A, U, delta = _problem(n, mp, q, m, seed=900 + n + m)
+    H = F.kernel_transform(n, w.x0, w.h, w.zr, w.zy, w.nu)
+    assert H.M == m
+    kind = F.OUT_XI if output == "xi" else F.OUT_ZETA
+    shape = (mp, n, n) if output == "xi" else (q, mp, n, n)
+    for alpha in (1e-4, 1e-2):
+        ref = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alpha=alpha, sources=w.sources, A=A, output=output)
+        o = torch.full(shape, float("nan"), device="cuda")
+        F.invert(H, dev(U), q, o, F.Opts(alpha=alpha, output=kind, points=w.sources))
+        assert rel(host(o), ref[output]) <= 1e-4, (alpha, rel(host(o), ref[output]))
+
+
+@pytest.mark.parametrize("n,mp,q,m,nb", [(32, 8, 1, 3, 1), (48, 6, 2, 4, 1), (32, 6, 2, 3, 4)])
+def test_discrepancy_matches_oracle(F, n, mp, q, m, nb):
+    w, A, U, delta = _problem(n, mp, q, m, seed=950 + n + m + nb, n_alpha=16)
+    ref = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=delta, tau=1.1, sources=w.sources,
+                   A=A, n_bands=nb)
+    H = F.kernel_transform(n, w.x0, w.h, w.zr, w.zy, w.nu)
+    idx = torch.zeros(nb, dtype=torch.int32, device="cuda")
+    res = torch.zeros((nb, w.alphas.size) if nb > 1 else w.alphas.size, dtype=torch.float64, device="cuda")
+    info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    xi = torch.empty((mp, n, n), device="cuda")
+    F.invert(H, dev(U), q, xi, F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx,
+                                      residuals=res, info=info, n_bands=nb))
+    r = host(res)
+    assert np.max(np.abs(r - ref["res2"]) / np.maximum(ref["res2"], 1e-300)) <= 1e-5
+    got = [int(v) for v in idx.cpu().numpy()]
+    want = ref["alpha_index"] if nb > 1 else [ref["alpha_index"]]
+    count = np.bincount(O.radial_bands(n, nb), minlength=nb)
+    for b in range(nb):
+        rb = ref["res2"][b] if nb > 1 else ref["res2"]
+        thr = (1.1 * delta) ** 2 * count[b] / (n * n)
+        if got[b] != want[b]:
+            near = np.abs(rb - thr) <= 1e-4 * thr
+            assert near[min(got[b], want[b]):max(got[b], want[b]) + 1].any()
+    if got == want:
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+    # the host-buffer entry point gives the same bits
+    xh = torch.empty((mp, n, n), dtype=torch.float32).pin_memory()
+    F.invert_host(H, torch.as_tensor(U, dtype=torch.float32).pin_memory(), q, xh,
+                  F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, n_bands=nb))
+    assert torch.equal(xh, xi.cpu())
+
+
+def test_choose_alpha_matches_oracle(F):
+    w, A, U, delta = _problem(32, 6, 2, 3, seed=977, n_alpha=16)
+    ref = O.invert(U, 32, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=delta, tau=1.1, A=A, output="none")
+    H = F.kernel_transform(32, w.x0, w.h, w.zr, w.zy, w.nu)
+    idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    res = torch.zeros(w.alphas.size, dtype=torch.float64, device="cuda")
+    F.choose_alpha(H, dev(U), 2, w.alphas, delta, 1.1, idx, res)
+    assert np.max(np.abs(host(res) - ref["res2"]) / ref["res2"]) <= 1e-5
+
+
+@pytest.mark.parametrize("n,mp,q,m", [(32, 5, 1, 3), (48, 4, 2, 2)])
+def test_tsvd_matches_oracle(F, n, mp, q, m):
+    w, A, U, delta = _problem(n, mp, q, m, seed=990 + n, n_alpha=12)
+    s2 = O.alpha_scale(A)
+    H = F.kernel_transform(n, w.x0, w.h, w.zr, w.zy, w.nu)
+    for a in _levels_away_from_spectrum(A, s2, [1e-4, 1e-2]):
+        ref = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alpha=a, sources=w.sources, A=A, ra="tsvd")
+        xi = torch.empty((mp, n, n), device="cuda")
+        F.invert(H, dev(U), q, xi, F.Opts(alpha=a, points=w.sources, ra=F.RA_TSVD))
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+    al = _levels_away_from_spectrum(A, s2, np.logspace(-6, -1, 12))
+    ref = O.invert(U, n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=al, delta=delta, tau=1.1, sources=w.sources, A=A,
+                   ra="tsvd")
+    res = torch.zeros(al.size, dtype=torch.float64, device="cuda")
+    idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    xi = torch.empty((mp, n, n), device="cuda")
+    F.invert(H, dev(U), q, xi, F.Opts(alphas=al, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx,
+                                      residuals=res, ra=F.RA_TSVD))
+    r = host(res)
+    assert np.max(np.abs(r - ref["res2"]) / np.maximum(ref["res2"], 1e-12 * ref["res2"].max())) <= 1e-5
+    if int(idx.item()) == ref["alpha_index"]:
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+
+
+def test_unsupported_combinations_are_rejected(F):
+    w, A, U, delta = _problem(32, 4, 1, 2, seed=5)
+    H = F.kernel_transform(32, w.x0, w.h, w.zr, w.zy, w.nu)
+    xi = torch.empty((4, 32, 32), dtype=torch.float64, device="cuda")
+    with pytest.raises(F.Fr3dError):
+        F.invert(H, dev(U, torch.float64), 1, xi, F.Opts(alpha=1e-3, points=w.sources, precision=F.PREC_FP64))
