@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--fused-variant", type=int, default=None,
                     help="force the fused inverse's tile variant (default: autotuned on the first call)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-paper-geometry", action="store_true", help="skip the M = M' = 51 leg")
     return ap.parse_args()
 
 
@@ -214,7 +215,7 @@ def setup_gpu(w, dev):
     xi = torch.tensor(w.xi_true, dtype=torch.float32, device=dev)
     zeta = torch.empty((w.Q, w.Mp, w.n, w.n), device=dev)
     fr3d.zeta_from_xi(H, xi, w.sources, zeta)
-    U = torch.empty((w.Q, 1, w.n, w.n), device=dev)
+    U = torch.empty((w.Q, w.M, w.n, w.n), device=dev)
     fr3d.fwd_apply(H, zeta, w.Q, U)
     nz = torch.tensor(w.noise, dtype=torch.float32, device=dev)
     nz *= w.noise_level * U.norm() / nz.norm()
@@ -365,6 +366,8 @@ def run_fr3d(args):
         result["learned"] = bench_learned(args, dev, flush, w, H, U, delta, rel_truth, dist)
     if rank == 0 and not args.no_batch:
         result["batched"] = bench_batched(args, dev, flush)
+    if rank == 0 and not args.no_paper_geometry:
+        result["paper_geometry"] = bench_paper_geometry(args, dev, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -465,6 +468,58 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
            "pair_recipe": "synthetic inclusions (1-12, Gaussian/ellipsoid), 0.5-5% noise, same geometry and "
                           "sources; seeds 20000+ (workload seed differs)"}
     net.close()
+    return res
+
+
+def bench_paper_geometry(args, dev, flush, n=256, m=51, mp=51, n_alpha=32):
+    """The paper's own experiment shape (Sec. 6: M = M' = 51 observation and unknown depths), here at
+    n = 256 on the periodic box, one source, 10 inclusions, 1 % noise: truncated SVD (the paper's best
+    regularising algorithm) and Tikhonov, alpha by the discrepancy principle; one graph replay per step,
+    L2 flushed before each.  Cold = kernel transform + the per-class eigen tables of the first call."""
+    import torch
+    from paper_1703_01216_gb300 import fr3d
+    from paper_1703_01216_gb300 import inputs as I
+    w = I.make_workload(n, mp, q=1, m_obs=m, n_incl=10, kinds=("gauss", "ellipsoid"), noise_level=0.01,
+                        n_alpha=n_alpha, seed=6000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H, U, delta = setup_gpu(w, dev)
+    out = torch.empty((mp, n, n), device=dev)
+    xi_true = torch.tensor(w.xi_true, device=dev)
+    res = {"workload": f"{n}^2 x {mp} unknown depths, {m} observation depths, 1 source, {n_alpha} alphas",
+           "voxels": n * n * mp}
+    st = torch.cuda.current_stream(dev)
+    for name, ra in (("tsvd", fr3d.RA_TSVD), ("tikhonov", fr3d.RA_TIKHONOV)):
+        idx = torch.zeros(1, dtype=torch.int32, device=dev)
+        opts = fr3d.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx, ra=ra)
+        fr3d.invert(H, U, 1, out, opts)            # builds the eigen tables, tunes the fused variant
+        torch.cuda.synchronize()
+        if name == "tsvd":
+            res["cold_s"] = round(time.perf_counter() - t0, 3)
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(st)
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g, stream=cap):
+                fr3d.invert(H, U, 1, out, opts)
+        st.wait_stream(cap)
+        for _ in range(3):
+            flush.fill_(1.0)
+            g.replay()
+        torch.cuda.synchronize()
+        reps = max(5, min(args.steps, 20))
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            g.replay()
+            b.record(st)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        res[name] = {"value": n * n * mp * reps / (tot * 1e-3), "unit": "voxels/s", "ms_per_step": tot / reps,
+                     "alpha_index": int(idx.item()), "launches": fr3d.last_launch_count(H),
+                     "rel_l2_vs_truth": round(float((out.double() - xi_true).norm() / xi_true.norm()), 4)}
     return res
 
 

@@ -110,7 +110,8 @@ struct FusedArgs {
                        // are not read and the column phase transforms Zs directly (M > 1 path)
 };
 
-template <int N, int MODE, int V>
+// PRE: the column phase transforms the solved spectra a.Zs (M > 1 path) instead of weighting U~.
+template <int N, int MODE, int V, bool PRE = false>
 __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   using G = FusedGeom<N, V>;
   constexpr int CL = G::CL, NT = G::NT, RB = G::RB, L = G::L;
@@ -146,7 +147,7 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
     build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
     // solve weight of bin o = kx n + ky: row aidx[band(o)] of Dd (one row when nb = 1); with bands the
     // band indices of all of this thread's bins are fetched first, then every weight in one round
-    if (a.Zs) {
+    if constexpr (PRE) {
       // solved spectra: no weights
     } else if (a.nb == 1) {
 #pragma unroll
@@ -211,10 +212,10 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
       if (q > 0) cluster_wait();
     // ---------------- column phase: U~_q w_j loaded straight into the registers of the first pass of
     // the inverse column DFTs (no shared-memory round trip for the input)
-    const float2* Zj = a.Zs ? a.Zs + ((long)q * a.Mp + j) * ps : nullptr;
+    const float2* Zj = PRE ? a.Zs + ((long)q * a.Mp + j) * ps : nullptr;
     auto ldc = [&](int col, int ky) -> float2 {
       const int e = col * N + ky;
-      if (Zj) {                   // solved spectrum of depth j (M > 1 path)
+      if constexpr (PRE) {        // solved spectrum of depth j (M > 1 path)
         float2 v = __ldg(Zj + (long)c0 * N + e);
         if (r == 0 && col == 0) {
           const float2 un = __ldg(Zj + (long)L * N + ky);
@@ -320,9 +321,9 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
 }
 
 // Both kernels are launched with a cluster dimension of FusedCfg<N>::CL (launch_clustered).
-template <int N, int MODE, int V>
+template <int N, int MODE, int V, bool PRE = false>
 __global__ void __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB) k_inv_fused(FusedArgs a) {
-  inv_fused_body<N, MODE, V>(a, (int)blockIdx.x / FusedCfg<N>::CL);
+  inv_fused_body<N, MODE, V, PRE>(a, (int)blockIdx.x / FusedCfg<N>::CL);
 }
 
 // Batched instances of one grid size n: cluster c handles depth map[c].y of instance map[c].x.
@@ -362,8 +363,10 @@ int launch_clustered(K kern, int clusters, int nt, size_t sm, cudaStream_t st, A
   return FR3D_OK;
 }
 
-// Launchers of variant V for every supported n (defined in fused_v<V>.cu).
+// Launchers of variant V for every supported n (defined in fused_v<V>.cu), and of the solved-spectra
+// form (variant 1, fused_pre.cu).
 template <int V> int fused_launch(int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st);
+int fused_launch_pre(int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st);
 template <int V>
 int fused_launch_batched(int n, bool xi, const FusedArgs* inst, const int2* map, int nclusters, cudaStream_t st);
 

@@ -61,7 +61,7 @@ int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, cudaStream_t 
   }
   *v_out = 0;
   if (mode == 0) return FR3D_OK;
-  const TuneKey key{H->dev, H->n, nj, a.Q, (xi ? 1 : 0) + (a.Zs ? 2 : 0)};
+  const TuneKey key{H->dev, H->n, nj, a.Q, xi ? 1 : 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -204,11 +204,8 @@ int inv_fused_presolved_f32(const Handle* H, const float2* Zs, const float* W, f
   a.j0 = 0;
   a.Mp = H->Mp;
   a.Zs = Zs;
-  const bool xi = output == FR3D_OUT_XI;
-  int v = 0;
-  FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, H->Mp, xi, st, &v));
-  const_cast<Handle*>(H)->fused_var = v;
-  return launch_variant(v, H->n, xi, a, H->Mp, st);
+  const_cast<Handle*>(H)->fused_var = 1;
+  return fused_launch_pre(H->n, output == FR3D_OUT_XI, a, H->Mp, st);
 }
 
 void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
