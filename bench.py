@@ -496,6 +496,7 @@ def bench_paper_geometry(args, dev, flush, n=256, m=51, mp=51, n_alpha=32):
         torch.cuda.synchronize()
         if name == "tsvd":
             res["cold_s"] = round(time.perf_counter() - t0, 3)
+        fr3d.profile_enable(H, True)
         g = torch.cuda.CUDAGraph()
         cap = torch.cuda.Stream(dev)
         cap.wait_stream(st)
@@ -509,6 +510,7 @@ def bench_paper_geometry(args, dev, flush, n=256, m=51, mp=51, n_alpha=32):
         torch.cuda.synchronize()
         reps = max(5, min(args.steps, 20))
         tot = 0.0
+        stages = {}
         for _ in range(reps):
             flush.fill_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -517,7 +519,11 @@ def bench_paper_geometry(args, dev, flush, n=256, m=51, mp=51, n_alpha=32):
             b.record(st)
             b.synchronize()
             tot += a.elapsed_time(b)
+            for k, v in fr3d.profile_read(H):
+                stages[k] = stages.get(k, 0.0) + v
+        fr3d.profile_enable(H, False)
         res[name] = {"value": n * n * mp * reps / (tot * 1e-3), "unit": "voxels/s", "ms_per_step": tot / reps,
+                     "stages_ms_per_step": {k: round(v / reps, 5) for k, v in stages.items()},
                      "alpha_index": int(idx.item()), "launches": fr3d.last_launch_count(H),
                      "rel_l2_vs_truth": round(float((out.double() - xi_true).norm() / xi_true.norm()), 4)}
     return res

@@ -157,6 +157,24 @@ __global__ void __launch_bounds__(256) k_class_eig(const double* __restrict__ A6
   if (tid == 0 && sweeps_out) atomicMax(sweeps_out, sweep);
 }
 
+// dst[e] = src(e) for e < count by the whole CTA, eight loads of a thread in flight at a time
+template <class Src>
+__device__ __forceinline__ void stage(float* dst, int count, Src src, int tid, int nt) {
+  for (int e0 = tid; e0 < count; e0 += 8 * nt) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt;
+      v[u] = e < count ? src(e) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt;
+      if (e < count) dst[e] = v[u];
+    }
+  }
+}
+
 // members (kx, ky) of class c in the stored half spectrum and their weights (1 on the kx = 0 and
 // kx = n/2 rows, whose mirror bins are stored too, 2 elsewhere)
 __device__ inline int class_members(int c, int n, int* kxs, int* kys, float* wts) {
@@ -195,7 +213,8 @@ __global__ void __launch_bounds__(256) k_project(float2* __restrict__ Uh, long p
     }
     nm_s = nm;
   }
-  for (int e = tid; e < M * M; e += nt) ut[e] = __ldg(Ut + (long)c * M * M + e);
+  const float* utc = Ut + (long)c * M * M;
+  stage(ut, M * M, [&](int e) { return __ldg(utc + e); }, tid, nt);
   for (int i = tid; i < M; i += nt) pw[i] = 0.f;
   __syncthreads();
   const int nm = nm_s;
@@ -234,36 +253,50 @@ struct MAlphas {
 // residual weight of component (lambda, t = alpha s^2): Tikhonov (t / (lambda + t))^2, TSVD [lambda < t]
 __device__ inline float resid_weight(float lam, float t, int ra) {
   if (ra == FR3D_RA_TSVD) return lam < t ? 1.f : 0.f;
-  const float f = t / (lam + t);
+  const float f = t * __frcp_rn(lam + t);
   return f * f;
 }
 
 constexpr int kMCPB = 64;   // classes per block of the residual sums
+constexpr int kMThreads = 256;
 
 // Block partials of r_b^2(alpha_k) * n^2 = sum_{c in b} sum_i F(lambda_ci, alpha_k) P_ci: the sum over
-// i in FP32 (M terms), over classes in FP64; thread per candidate.
-__global__ void __launch_bounds__(128) k_alpha_m_partial(const double* __restrict__ lam, const double* __restrict__ Pc,
-                                                         int M, int Cn, const unsigned char* __restrict__ cband,
-                                                         int nb, MAlphas al, const double* __restrict__ s2,
-                                                         int na, int ra, double* __restrict__ partials) {
+// i in FP32 (M terms), over classes in FP64; S = 256 / n_alpha threads per candidate take every S-th
+// class, their sums are added in a fixed order.
+__global__ void __launch_bounds__(kMThreads) k_alpha_m_partial(
+    const double* __restrict__ lam, const double* __restrict__ Pc, int M, int Cn,
+    const unsigned char* __restrict__ cband, int nb, MAlphas al, const double* __restrict__ s2, int na, int ra,
+    double* __restrict__ partials) {
   __shared__ float sl[kMCPB * kMaxM], sp[kMCPB * kMaxM];
+  __shared__ double red[kMThreads];
+  __shared__ unsigned char sb[kMCPB];
   const int c0 = blockIdx.x * kMCPB, ncl = min(kMCPB, Cn - c0);
   for (int e = threadIdx.x; e < ncl * M; e += blockDim.x) {
     sl[e] = (float)lam[(long)c0 * M + e];
     sp[e] = (float)Pc[(long)c0 * M + e];
   }
+  for (int e = threadIdx.x; e < ncl; e += blockDim.x) sb[e] = nb > 1 ? cband[c0 + e] : 0;
   __syncthreads();
-  const int k = threadIdx.x;
-  if (k >= na) return;
+  const int S = kMThreads / na, k = threadIdx.x % na, sub = threadIdx.x / na;
   const float t = (float)(al.a[k] * (*s2));
-  double acc[FR3D_MAX_BANDS];
-  for (int b = 0; b < nb; ++b) acc[b] = 0.0;
-  for (int cc = 0; cc < ncl; ++cc) {
-    float f = 0.f;
-    for (int i = 0; i < M; ++i) f = fmaf(resid_weight(sl[cc * M + i], t, ra), sp[cc * M + i], f);
-    acc[nb > 1 ? (int)cband[c0 + cc] : 0] += (double)f;
+  for (int b = 0; b < nb; ++b) {
+    double acc = 0.0;
+    if (sub < S)
+      for (int cc = sub; cc < ncl; cc += S) {
+        if (sb[cc] != b) continue;
+        float f = 0.f;
+        for (int i = 0; i < M; ++i) f = fmaf(resid_weight(sl[cc * M + i], t, ra), sp[cc * M + i], f);
+        acc += (double)f;
+      }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < na) {
+      double s = 0.0;
+      for (int q = 0; q < S; ++q) s += red[q * na + threadIdx.x];
+      partials[((long)blockIdx.x * nb + b) * na + threadIdx.x] = s;
+    }
+    __syncthreads();
   }
-  for (int b = 0; b < nb; ++b) partials[((long)blockIdx.x * nb + b) * na + k] = acc[b];
 }
 
 // Sum of the partials (fixed order), r^2 = sum / n^2, and the discrepancy choice per band (one warp
@@ -320,15 +353,18 @@ __global__ void __launch_bounds__(256) k_alpha_m_finish(const double* __restrict
 }
 
 // zeta~_j(bin, q) = sum_i W_c[i][j] g_i p_i(bin, q) / n^2 with g_i of the class's band alpha, written to
-// the spectra Zs [q][j][bin].  One CTA per class; the projected data of all members and of a chunk of
-// source parameters are staged in shared memory, W_c is read once per chunk.
-constexpr int kSolveQC = 8;   // source parameters per chunk
+// the spectra Zs [q][j][bin].  One CTA per class: W_c is staged in shared memory by depth chunks (all
+// loads of a thread in flight), the projected data of the members by chunks of source parameters, and
+// every thread computes outputs (q, member, j) with j fastest.
+constexpr int kSolveQC = 8;     // source parameters per chunk
+constexpr int kSolveWC = 4096;  // floats of W_c per depth chunk
 __global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, long ps, int Q, int M, int Mp, int n,
                                                  const double* __restrict__ lam, const float* __restrict__ W,
                                                  const unsigned char* __restrict__ cband, int nb,
                                                  const int* __restrict__ aidx, int na, MAlphas al,
                                                  const double* __restrict__ s2, int ra, double inv_n2,
                                                  float2* __restrict__ Zs) {
+  __shared__ float Ws[kSolveWC];
   __shared__ float2 x[kSolveQC * 4 * kMaxM];
   __shared__ float g[kMaxM];
   __shared__ long ob[4];
@@ -353,35 +389,32 @@ __global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, l
   __syncthreads();
   const int nm = nm_s;
   const float* Wc = W + (long)c * M * Mp;
-  for (int q0 = 0; q0 < Q; q0 += kSolveQC) {
-    const int qc = min(kSolveQC, Q - q0);
-    for (int e = tid; e < qc * nm * M; e += nt) {
-      const int qq = e / (nm * M), m = (e / M) % nm, i = e % M;
-      const float2 v = P[((long)(q0 + qq) * M + i) * ps + ob[m]];
-      x[e] = make_float2(v.x * g[i], v.y * g[i]);
-    }
-    __syncthreads();
-    for (int j = tid; j < Mp; j += nt) {
-      float2 z[kSolveQC * 4];
-#pragma unroll
-      for (int e = 0; e < kSolveQC * 4; ++e) z[e] = make_float2(0.f, 0.f);
-      for (int i = 0; i < M; ++i) {
-        const float w = __ldg(Wc + (long)i * Mp + j);
-#pragma unroll
-        for (int e = 0; e < kSolveQC * 4; ++e)
-          if (e < qc * nm) {
-            z[e].x = fmaf(w, x[e * M + i].x, z[e].x);
-            z[e].y = fmaf(w, x[e * M + i].y, z[e].y);
-          }
+  const int JC = min(Mp, kSolveWC / M);
+  for (int j0 = 0; j0 < Mp; j0 += JC) {
+    const int jc = min(JC, Mp - j0);
+    stage(Ws, M * jc, [&](int e) { return __ldg(Wc + (long)(e / jc) * Mp + j0 + e % jc); }, tid, nt);
+    for (int q0 = 0; q0 < Q; q0 += kSolveQC) {
+      const int qc = min(kSolveQC, Q - q0);
+      for (int e = tid; e < qc * nm * M; e += nt) {
+        const int qq = e / (nm * M), m = (e / M) % nm, i = e % M;
+        const float2 v = P[((long)(q0 + qq) * M + i) * ps + ob[m]];
+        x[e] = make_float2(v.x * g[i], v.y * g[i]);
       }
-#pragma unroll
-      for (int e = 0; e < kSolveQC * 4; ++e)
-        if (e < qc * nm) {
-          const int qq = e / nm, m = e % nm;
-          Zs[((long)(q0 + qq) * Mp + j) * ps + ob[m]] = z[e];
+      __syncthreads();
+      for (int o = tid; o < qc * nm * jc; o += nt) {
+        const int jj = o % jc, qm = o / jc;
+        const float2* xr = x + qm * M;
+        float2 z = make_float2(0.f, 0.f);
+        for (int i = 0; i < M; ++i) {
+          const float w = Ws[i * jc + jj];
+          z.x = fmaf(w, xr[i].x, z.x);
+          z.y = fmaf(w, xr[i].y, z.y);
         }
+        const int qq = qm / nm, m = qm % nm;
+        Zs[((long)(q0 + qq) * Mp + j0 + jj) * ps + ob[m]] = z;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -474,7 +507,7 @@ int multi_alpha(Handle* H, const MultiWs& w, const double* alphas, int na, int r
   MAlphas al;
   for (int k = 0; k < na; ++k) al.a[k] = alphas[k];
   const int nblk = (H->C + kMCPB - 1) / kMCPB;
-  k_alpha_m_partial<<<nblk, 128, 0, st>>>(H->mlam, w.Pc, H->M, H->C, H->cband, nb, al, H->s2, na, ra, H->partials);
+  k_alpha_m_partial<<<nblk, kMThreads, 0, st>>>(H->mlam, w.Pc, H->M, H->C, H->cband, nb, al, H->s2, na, ra, H->partials);
   MThr t;
   for (int b = 0; b < nb; ++b) t.t[b] = thr2[b];
   k_alpha_m_finish<<<1, 256, 0, st>>>(H->partials, nblk, nb, na, 1.0 / ((double)H->n * H->n), t, aidx, residuals,
