@@ -40,7 +40,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "kernel_K", "wrapped_lags", "kernel_samples", "dft_matrix", "dft2", "idft2",
+    "KINDS", "kernel_K", "wrapped_lags", "kernel_samples", "dft_matrix", "dft2", "idft2",
     "kernel_hat", "A_matrices", "alpha_scale", "forward_direct", "forward_dft",
     "tikhonov_qr", "tsvd_solve", "residual_sq", "radial_bands", "choose_alpha_index", "V0", "zeta_from_xi",
     "combine_sources", "invert", "A0_of", "A2_of",
@@ -48,12 +48,21 @@ __all__ = [
 
 
 # --------------------------------------------------------------------------- kernel
-def kernel_K(x, y, z):
-    """K(x, y, z) = d/dz (1/r) = -z / (x^2 + y^2 + z^2)^(3/2)   (Sec. 3, kernel of Eq. (4))."""
+KINDS = ("dz_inv_r", "inv_r")
+
+
+def kernel_K(x, y, z, kind: str = "dz_inv_r"):
+    """K(x, y, z) = d/dz (1/r) = -z / (x^2 + y^2 + z^2)^(3/2)  (Sec. 3, the kernel of Eq. (4) and of the
+    equation the paper solves), or with kind="inv_r" K = 1/r, the kernel of the first equation the paper
+    derives (for data V2 instead of its z-derivative, Sec. 3)."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     z = np.asarray(z, dtype=np.float64)
     r2 = x * x + y * y + z * z
+    if kind == "inv_r":
+        return 1.0 / np.sqrt(r2)
+    if kind != "dz_inv_r":
+        raise ValueError(kind)
     return -z / (r2 * np.sqrt(r2))
 
 
@@ -70,10 +79,10 @@ def wrapped_lags(n: int, pad: int = 1) -> np.ndarray:
     return np.where(t < L // 2, t, t - L)
 
 
-def kernel_samples(n: int, h: float, dz: float, pad: int = 1) -> np.ndarray:
+def kernel_samples(n: int, h: float, dz: float, pad: int = 1, kind: str = "dz_inv_r") -> np.ndarray:
     """K at the wrapped lags (dy, dx) * h for one depth difference dz, shape [L, L] ([y, x])."""
     lag = wrapped_lags(n, pad) * h
-    return kernel_K(lag[None, :], lag[:, None], dz)
+    return kernel_K(lag[None, :], lag[:, None], dz, kind)
 
 
 # --------------------------------------------------------------------------- DFT
@@ -99,7 +108,7 @@ def idft2(F: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------- Eq. (6)
-def kernel_hat(n: int, h: float, zy, zr, pad: int = 1) -> np.ndarray:
+def kernel_hat(n: int, h: float, zy, zr, pad: int = 1, kind: str = "dz_inv_r") -> np.ndarray:
     """Discrete analogue of K~(w1, w2, z_i - z'_j) (Algorithm 1 step 1, Sec. 5).
 
     Returns h^2 * DFT of the sampled kernel, shape [M, M', L, L] ([i, j, ky, kx]).
@@ -112,19 +121,19 @@ def kernel_hat(n: int, h: float, zy, zr, pad: int = 1) -> np.ndarray:
     out = np.empty((zy.size, zr.size, L, L))
     for i, zi in enumerate(zy):
         for j, zj in enumerate(zr):
-            Kh = h * h * dft2(kernel_samples(n, h, zi - zj, pad))
+            Kh = h * h * dft2(kernel_samples(n, h, zi - zj, pad, kind))
             assert np.max(np.abs(Kh.imag)) <= 1e-9 * max(1.0, np.max(np.abs(Kh.real)))
             out[i, j] = Kh.real
     return out
 
 
-def A_matrices(n: int, h: float, zy, zr, nu, pad: int = 1) -> np.ndarray:
+def A_matrices(n: int, h: float, zy, zr, nu, pad: int = 1, kind: str = "dz_inv_r") -> np.ndarray:
     """A^(m) = [nu_j K~(w^(m), z_i - z'_j)] of Eq. (6) for every frequency m.
 
     Shape [L, L, M, M'] ([ky, kx, i, j]): one M x M' matrix per grid frequency.
     """
     nu = np.asarray(nu, np.float64)
-    Kh = kernel_hat(n, h, zy, zr, pad)                      # [i, j, ky, kx]
+    Kh = kernel_hat(n, h, zy, zr, pad, kind)                # [i, j, ky, kx]
     A = Kh * nu[None, :, None, None]
     return np.ascontiguousarray(np.transpose(A, (2, 3, 0, 1)))
 
@@ -135,7 +144,7 @@ def alpha_scale(A: np.ndarray) -> float:
 
 
 # --------------------------------------------------------------------------- forward operator
-def forward_direct(zeta: np.ndarray, n: int, h: float, zy, zr, nu, pad: int = 1) -> np.ndarray:
+def forward_direct(zeta: np.ndarray, n: int, h: float, zy, zr, nu, pad: int = 1, kind: str = "dz_inv_r") -> np.ndarray:
     """Direct quadrature of the discretised Eq. (4) (the definition; O(n^4 M M')).
 
     U(b, a, i) = sum_{b', a', j} h^2 nu_j K(lag(a - a') h, lag(b - b') h, z_i - z'_j) zeta(b', a', j)
@@ -155,7 +164,7 @@ def forward_direct(zeta: np.ndarray, n: int, h: float, zy, zr, nu, pad: int = 1)
     for i, zi in enumerate(zy):
         for j, zj in enumerate(zr):
             # Kmat[b, a, b', a'] = K(lag[a, a'], lag[b, b'], dz)
-            Kmat = kernel_K(lag[None, :, None, :], lag[:, None, :, None], zi - zj)
+            Kmat = kernel_K(lag[None, :, None, :], lag[:, None, :, None], zi - zj, kind)
             out[..., i, :, :] += h * h * nu[j] * np.einsum("bacd,...cd->...ba", Kmat, zeta[..., j, :, :])
     return out
 
@@ -170,14 +179,15 @@ def _embed(f: np.ndarray, n: int, pad: int) -> np.ndarray:
     return g
 
 
-def forward_dft(zeta: np.ndarray, n: int, h: float, zy, zr, nu, pad: int = 1, A=None) -> np.ndarray:
+def forward_dft(zeta: np.ndarray, n: int, h: float, zy, zr, nu, pad: int = 1, A=None,
+                kind: str = "dz_inv_r") -> np.ndarray:
     """The same operator through the DFT (Eq. (5) discretised, Eq. (6)):
 
     U~_i(m) = sum_j A^(m)_ij zeta~_j(m),   U = IDFT2(U~) cropped to the n x n grid.
     ``zeta`` is [..., M', n, n]; the result is [..., M, n, n].
     """
     if A is None:
-        A = A_matrices(n, h, zy, zr, nu, pad)                # [ky, kx, i, j]
+        A = A_matrices(n, h, zy, zr, nu, pad, kind)          # [ky, kx, i, j]
     Zh = dft2(_embed(zeta, n, pad))                          # [..., j, ky, kx]
     Uh = np.einsum("yxij,...jyx->...iyx", A, Zh)
     U = idft2(Uh)
@@ -319,7 +329,7 @@ def combine_sources(zeta: np.ndarray, sources: np.ndarray, n: int, x0: float, h:
 def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int = 1,
            alpha=None, alphas=None, delta=None, tau: float = 1.1, sources=None, A0: float = 1.0,
            output: str = "xi", chunk: int = 4096, bins=None, A=None, n_bands: int = 1, band_alpha_index=None,
-           ra: str = "tikhonov"):
+           ra: str = "tikhonov", kind: str = "dz_inv_r"):
     """Algorithm 1 (Sec. 4) in its finite-dimensional form (Sec. 5).
 
     U: [Q, M, n, n] data for Q source parameters.
@@ -350,7 +360,7 @@ def invert(U: np.ndarray, n: int, x0: float, h: float, zy, zr, nu, *, pad: int =
     Mp = zr.size
     L = pad * n
     if A is None:
-        A = A_matrices(n, h, zy, zr, nu, pad)
+        A = A_matrices(n, h, zy, zr, nu, pad, kind)
     s2 = alpha_scale(A)
     Af = A.reshape(L * L, M, Mp)
     Uh = dft2(_embed(U, n, pad))                                     # [Q, M, L, L]

@@ -112,11 +112,12 @@ def test_dft2_agrees_with_library_fft_and_parseval():
 
 # ------------------------------------------------------------------ convolution theorem (Eq. (5))
 @pytest.mark.parametrize("n", [6, 8])
-def test_forward_dft_equals_direct_quadrature_periodic(n):
+@pytest.mark.parametrize("kind", ["dz_inv_r", "inv_r"])
+def test_forward_dft_equals_direct_quadrature_periodic(n, kind):
     h, zy, zr, nu = 0.25, [0.0, 0.1], [0.5, 0.6, 0.8], [0.1, 0.1, 0.2]
     zeta = rng0.standard_normal((2, 3, n, n))
-    Ud = O.forward_direct(zeta, n, h, zy, zr, nu)
-    Uf = O.forward_dft(zeta, n, h, zy, zr, nu)
+    Ud = O.forward_direct(zeta, n, h, zy, zr, nu, kind=kind)
+    Uf = O.forward_dft(zeta, n, h, zy, zr, nu, kind=kind)
     assert rel(Uf, Ud) < 1e-12
 
 
@@ -335,3 +336,26 @@ def test_tsvd_inversion_residual_is_monotone_and_reaches_the_data_norm():
     assert np.all(np.diff(r) >= -1e-12 * r.max())
     assert abs(r[-1] - np.sum(U ** 2)) < 1e-10 * np.sum(U ** 2)
     assert r[0] < 1e-20 * np.sum(U ** 2)
+
+
+# ------------------------------------------------------------------ the 1/r kernel of the first equation (Sec. 3)
+def test_inv_r_kernel_z_derivative_is_the_solved_kernel():
+    """d/dz of the 1/r kernel's discrete transform is the transform of d/dz (1/r), at every frequency
+    (central difference in the depth difference; the two kinds share grid, box and DFT)."""
+    n, h, e = 16, 0.125, 1e-4
+    for dz in (-0.6, -0.25, 0.4):
+        up = O.kernel_hat(n, h, [0.0], [-(dz + e)], kind="inv_r")[0, 0]
+        dn = O.kernel_hat(n, h, [0.0], [-(dz - e)], kind="inv_r")[0, 0]
+        want = O.kernel_hat(n, h, [0.0], [-dz])[0, 0]
+        assert rel((up - dn) / (2 * e), want) < 1e-6
+
+
+def test_inv_r_dc_bin_is_the_integral_over_the_box():
+    """h^2 * DFT at k = 0 of the sampled 1/r is the midpoint rule for its integral over the periodic
+    box's square; compare with scipy's adaptive quadrature of the same integral."""
+    from scipy.integrate import dblquad
+    n, h, dz = 64, 0.05, 0.3
+    Kh = O.kernel_hat(n, h, [0.0], [-dz], kind="inv_r")[0, 0]
+    lo, hi = -(n / 2 + 0.5) * h, (n / 2 - 0.5) * h
+    val = dblquad(lambda y, x: 1.0 / np.sqrt(x * x + y * y + dz * dz), lo, hi, lo, hi, epsabs=1e-11, epsrel=1e-11)[0]
+    assert abs(Kh[0, 0] - val) <= 2e-4 * val
