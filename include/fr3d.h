@@ -69,6 +69,8 @@ extern "C" {
 
 /* ---- enums ---- */
 #define FR3D_K_DZ_INV_R 0 /* K = d/dz (1/r), Eq. (4) (the equation the paper solves) */
+#define FR3D_K_INV_R 1    /* K = 1/r: the first equation Sec. 3 derives, for data V2 instead of its
+                             z-derivative; the periodic box keeps every bin finite, including k = 0 */
 #define FR3D_PREC_FP32 0  /* FP32 FFTs, FP64 alpha rule; data and outputs are float */
 #define FR3D_PREC_FP64 1  /* FP64 throughout; data and outputs are double */
 #define FR3D_ALPHA_FIXED 0
@@ -96,7 +98,7 @@ typedef struct fr3d_geometry {
   const double* nu;        /* host [M'] quadrature weights nu_j (NULL: midpoint, |z'_1 - z'_0|, or 1 if M' = 1) */
   int nzy;                 /* M >= 1: observation depths of Y */
   const double* zy;        /* host [M] depths z_i; z_i != z'_j for all i, j */
-  int kernel_kind;         /* FR3D_K_DZ_INV_R */
+  int kernel_kind;         /* FR3D_K_DZ_INV_R or FR3D_K_INV_R */
 } fr3d_geometry;
 
 /* Point sources of the model example (Sec. 6): for source parameter q the field source is

@@ -43,6 +43,7 @@ __host__ __device__ __forceinline__ int num_classes(int n) { return (n / 2 + 1) 
 struct Handle {
   int dev = 0;
   int n = 0, M = 0, Mp = 0, C = 0;
+  int kind = FR3D_K_DZ_INV_R;  // kernel of the equation (fr3d_geometry.kernel_kind)
   double x0 = 0, y0 = 0, h = 0;
   std::vector<double> zr, nu, zy;
   // kernel tables (owned)

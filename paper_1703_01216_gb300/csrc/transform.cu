@@ -1,4 +1,4 @@
-// Algorithm 1 step 1 for the kernel (Sec. 5): the discrete transform of K = d/dz (1/r)
+// Algorithm 1 step 1 for the kernel (Sec. 5): the discrete transform of K = d/dz (1/r) (or of 1/r)
 // sampled at the periodic lags, in FP64, and the per-frequency tables of Eq. (6).
 //
 // The sampled kernel is even in x and in y, so its DFT is the 2D cosine sum
@@ -23,7 +23,8 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-__global__ void k_samples(double* __restrict__ Ks, int H1, double h, const double* __restrict__ dz, int nij) {
+__global__ void k_samples(double* __restrict__ Ks, int H1, double h, const double* __restrict__ dz, int nij,
+                          int kind) {
   const long total = (long)nij * H1 * H1;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int a = (int)(idx % H1);
@@ -31,7 +32,8 @@ __global__ void k_samples(double* __restrict__ Ks, int H1, double h, const doubl
     const int ij = (int)(idx / ((long)H1 * H1));
     const double x = a * h, y = b * h, z = dz[ij];
     const double r2 = x * x + y * y + z * z;
-    Ks[idx] = -z / (r2 * sqrt(r2));  // K = -z / r^3 (Sec. 3)
+    // K = d/dz (1/r) = -z / r^3 (Eq. (4)), or 1/r (the first equation of Sec. 3, for V2 data)
+    Ks[idx] = kind == FR3D_K_INV_R ? 1.0 / sqrt(r2) : -z / (r2 * sqrt(r2));
   }
 }
 
@@ -183,6 +185,7 @@ static int kernel_transform_impl(const fr3d_geometry* g, Handle* H, cudaStream_t
   H->M = g->nzy;
   H->Mp = g->nzr;
   H->C = num_classes(n);
+  H->kind = g->kernel_kind;
   H->x0 = g->x0;
   H->y0 = g->y0;
   H->h = g->hx;
@@ -266,7 +269,7 @@ static int kernel_transform_impl(const fr3d_geometry* g, Handle* H, cudaStream_t
     TRYB(cudaMemcpyAsync(d_cw, cw.data(), plane * sizeof(double), cudaMemcpyHostToDevice, st));
     TRYB(cudaMemcpyAsync(H->zr64, H->zr.data(), H->Mp * sizeof(double), cudaMemcpyHostToDevice, st));
     TRYB(cudaMemcpyAsync(H->zr32, zr32.data(), H->Mp * sizeof(float), cudaMemcpyHostToDevice, st));
-    k_samples<<<1024, 256, 0, st>>>(d_ks, H1, H->h, d_dz, nij);
+    k_samples<<<1024, 256, 0, st>>>(d_ks, H1, H->h, d_dz, nij, H->kind);
     dim3 blk(16, 16), grd((H1 + 15) / 16, (H1 + 15) / 16, nij);
     // S[ij][b][k1] = sum_a Ks[ij][b][a] cw[k1][a]
     k_dgemm<true><<<grd, blk, 0, st>>>(d_ks, plane, d_cw, 0, d_s, plane, H1, 1.0);
@@ -302,7 +305,7 @@ void handle_free(Handle* H) {
 
 int validate_geometry(const fr3d_geometry* g) {
   if (!g || !g->zr || !g->zy || g->nzr < 1 || g->nzy < 1) return FR3D_ERR_INVALID_ARG;
-  if (g->kernel_kind != FR3D_K_DZ_INV_R) return FR3D_ERR_INVALID_ARG;
+  if (g->kernel_kind != FR3D_K_DZ_INV_R && g->kernel_kind != FR3D_K_INV_R) return FR3D_ERR_INVALID_ARG;
   if (g->nx != g->ny || !supported_n(g->nx)) return FR3D_ERR_UNSUPPORTED_SIZE;
   if (g->pad != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
   if (!(g->hx > 0) || g->hx != g->hy || !isfinite(g->x0) || !isfinite(g->y0)) return FR3D_ERR_BAD_GEOMETRY;

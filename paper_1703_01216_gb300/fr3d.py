@@ -24,7 +24,7 @@ OUT_ZETA, OUT_XI = 0, 1
 RA_TIKHONOV, RA_TSVD = 0, 1
 INFO_ALPHA_NONE_SATISFIES, INFO_ALPHA_ALL_SATISFY, INFO_NONFINITE, INFO_LEARNED_OUT_OF_RANGE = 1, 2, 4, 8
 MAX_HIDDEN = 96
-K_DZ_INV_R = 0
+K_DZ_INV_R, K_INV_R = 0, 1
 MAX_ALPHAS = 128
 MAX_SOURCE_POINTS = 256
 
@@ -171,7 +171,7 @@ def make_sources(points, A0: float = 1.0):
 class Handle:
     """Owns an fr3d_handle (fr3d_kernel_transform ... fr3d_handle_destroy)."""
 
-    def __init__(self, n, x0, h, zr, zy, nu=None, stream=None):
+    def __init__(self, n, x0, h, zr, zy, nu=None, stream=None, kind=K_DZ_INV_R):
         lib = load()
         self._zr, zrp = _f64(zr)
         self._zy, zyp = _f64(zy)
@@ -180,7 +180,7 @@ class Handle:
         else:
             self._nu, nup = _f64(nu)
         g = Geometry(int(n), int(n), float(x0), float(x0), float(h), float(h), 1, self._zr.size, zrp, nup,
-                     self._zy.size, zyp, K_DZ_INV_R)
+                     self._zy.size, zyp, int(kind))
         hp = ct.c_void_p()
         _check(lib.fr3d_kernel_transform(ct.byref(g), ct.byref(hp), _stream(stream)), "fr3d_kernel_transform")
         self.ptr = hp
@@ -200,8 +200,8 @@ class Handle:
             pass
 
 
-def kernel_transform(n, x0, h, zr, zy, nu=None, stream=None) -> Handle:
-    return Handle(n, x0, h, zr, zy, nu, stream)
+def kernel_transform(n, x0, h, zr, zy, nu=None, stream=None, kind=K_DZ_INV_R) -> Handle:
+    return Handle(n, x0, h, zr, zy, nu, stream, kind)
 
 
 def fwd_apply(handle: Handle, zeta, Q: int, U, precision: int = PREC_FP32, stream=None):

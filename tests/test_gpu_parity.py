@@ -345,3 +345,26 @@ def test_tsvd_discrepancy_matches_oracle(F, n, mp, q):
     xt = torch.empty_like(xi)
     F.invert(H, dev(U), q, xt, F.Opts(alphas=alphas, delta=delta, tau=1.1, points=w.sources))
     assert not torch.equal(xt, xi)
+
+
+# ------------------------------------------------------------------ the 1/r kernel (first equation of Sec. 3)
+@pytest.mark.parametrize("n,mp,q,m", [(32, 6, 1, 1), (48, 4, 2, 1), (32, 4, 1, 3)])
+def test_inv_r_kernel_forward_and_inversion_match_oracle(F, n, mp, q, m):
+    w = I.make_workload(n, mp, q=q, m_obs=m, n_incl=3, noise_level=0.02, n_alpha=12, seed=870 + n + m)
+    A = O.A_matrices(n, w.h, w.zy, w.zr, w.nu, kind="inv_r")
+    H = F.kernel_transform(n, w.x0, w.h, w.zr, w.zy, w.nu, kind=F.K_INV_R)
+    assert abs(H.s2 - O.alpha_scale(A)) <= 1e-12 * O.alpha_scale(A)
+    rng = np.random.default_rng(n + m)
+    zeta = rng.standard_normal((q, mp, n, n))
+    ref = O.forward_dft(zeta, n, w.h, w.zy, w.zr, w.nu, A=A)
+    U = torch.empty((q, m, n, n), device="cuda")
+    F.fwd_apply(H, dev(zeta), q, U)
+    assert rel(host(U), ref) <= 1e-5
+    zt = O.zeta_from_xi(w.xi_true, w.sources, n, w.x0, w.h, w.zr)
+    Ud = O.forward_dft(zt, n, w.h, w.zy, w.zr, w.nu, A=A)
+    Ud = Ud + w.noise * (0.02 * np.linalg.norm(Ud) / np.linalg.norm(w.noise))
+    for alpha in (1e-4, 1e-2):
+        r = O.invert(Ud, n, w.x0, w.h, w.zy, w.zr, w.nu, alpha=alpha, sources=w.sources, A=A)
+        xi = torch.empty((mp, n, n), device="cuda")
+        F.invert(H, dev(Ud), q, xi, F.Opts(alpha=alpha, points=w.sources))
+        assert rel(host(xi), r["xi"]) <= 1e-4, (alpha, rel(host(xi), r["xi"]))
