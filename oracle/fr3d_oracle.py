@@ -43,7 +43,7 @@ __all__ = [
     "KINDS", "kernel_K", "wrapped_lags", "kernel_samples", "dft_matrix", "dft2", "idft2",
     "kernel_hat", "A_matrices", "alpha_scale", "forward_direct", "forward_dft",
     "tikhonov_qr", "tsvd_solve", "residual_sq", "radial_bands", "choose_alpha_index", "V0", "zeta_from_xi",
-    "combine_sources", "invert", "A0_of", "A2_of",
+    "combine_sources", "invert", "A0_of", "A2_of", "pi_depths", "rhs_terms", "assemble_rhs", "simulate_dV2dz",
 ]
 
 
@@ -323,6 +323,52 @@ def combine_sources(zeta: np.ndarray, sources: np.ndarray, n: int, x0: float, h:
         num += v * zeta[q]
         den += v * v
     return num / den
+
+
+# --------------------------------------------------------------------------- right-hand side of Eq. (7)
+def pi_depths(n_pi: int, half: float):
+    """Midpoint grid of the vertical extent [-half, half] of the box Pi (Sec. 5: R^3 replaced by the
+    cube Pi = [-r, r]^3; horizontally the periodic box of the R grid) and its quadrature weights."""
+    dz = 2.0 * half / n_pi
+    return -half + (np.arange(n_pi) + 0.5) * dz, np.full(n_pi, dz)
+
+
+def rhs_terms(n: int, x0: float, h: float, zy, sources: np.ndarray, n_pi: int, half: float):
+    """The a-priori terms of Eq. (7) for point sources x_{q,l} (Sec. 6), on the observation grid:
+        S_q(x) = sum_l d/dx3 (1/|x - x_l|) = sum_l K(x - x_l),
+        I_q(x) = sum_l integral over Pi of d/dx3 (1/|x - x'|) / |x' - x_l| dx'
+    (R^3 replaced by Pi as the paper does when it simulates its data, Sec. 6); I_q is the discrete
+    operator of Eq. (4) with Pi's depth grid in place of R's, applied to f_q(x') = sum_l 1/|x' - x_l|.
+    Returns S, I of shape [Q, M, n, n]."""
+    zy = np.atleast_1d(np.asarray(zy, np.float64))
+    src = np.asarray(sources, np.float64)
+    X, Y, Zy = _grid_xyz(n, x0, h, zy)
+    zp, nup = pi_depths(n_pi, half)
+    Xp, Yp, Zp = _grid_xyz(n, x0, h, zp)
+    S = np.zeros((src.shape[0], zy.size, n, n))
+    f = np.zeros((src.shape[0], zp.size, n, n))
+    for q, pts in enumerate(src):
+        for (px, py, pz) in pts:
+            S[q] += kernel_K(X - px, Y - py, Zy - pz)
+            f[q] += 1.0 / np.sqrt((Xp - px) ** 2 + (Yp - py) ** 2 + (Zp - pz) ** 2)
+    I = forward_dft(f, n, h, zy, zp, nup)
+    return S, I
+
+
+def assemble_rhs(dV2dz: np.ndarray, n: int, x0: float, h: float, zy, sources, A0: float, A2: float, c0: float,
+                 n_pi: int, half: float) -> np.ndarray:
+    """Right-hand side of Eq. (7) from the measured dV2/dx3 on Y:
+        U = 2 pi dV2/dx3 + (A2 / 2) S - A0 / (4 pi c0^2) I."""
+    S, I = rhs_terms(n, x0, h, zy, sources, n_pi, half)
+    return 2.0 * np.pi * np.asarray(dV2dz, np.float64) + 0.5 * A2 * S - A0 / (4.0 * np.pi * c0 * c0) * I
+
+
+def simulate_dV2dz(U: np.ndarray, n: int, x0: float, h: float, zy, sources, A0: float, A2: float, c0: float,
+                   n_pi: int, half: float) -> np.ndarray:
+    """The paper's simulated measurement (Sec. 6) for a given left-hand side U = integral over R of
+    K zeta: dV2/dx3 = (U - (A2 / 2) S + A0 / (4 pi c0^2) I) / (2 pi)."""
+    S, I = rhs_terms(n, x0, h, zy, sources, n_pi, half)
+    return (np.asarray(U, np.float64) - 0.5 * A2 * S + A0 / (4.0 * np.pi * c0 * c0) * I) / (2.0 * np.pi)
 
 
 # --------------------------------------------------------------------------- Algorithm 1

@@ -359,3 +359,48 @@ def test_inv_r_dc_bin_is_the_integral_over_the_box():
     lo, hi = -(n / 2 + 0.5) * h, (n / 2 - 0.5) * h
     val = dblquad(lambda y, x: 1.0 / np.sqrt(x * x + y * y + dz * dz), lo, hi, lo, hi, epsabs=1e-11, epsrel=1e-11)[0]
     assert abs(Kh[0, 0] - val) <= 2e-4 * val
+
+
+# ------------------------------------------------------------------ right-hand side of Eq. (7)
+def test_rhs_source_term_is_the_z_derivative_of_the_inverse_distances():
+    """S = sum_l d/dx3 (1/|x - x_l|): central difference in the observation depth of the 1/r field."""
+    n, x0, h, zy = 8, -1.0, 0.25, [0.1, 0.3]
+    src = np.array([[[0.05, -0.2, -0.4], [0.6, 0.3, -0.7]]])
+    S, _ = O.rhs_terms(n, x0, h, zy, src, 4, 1.0)
+    c = x0 + (np.arange(n) + 0.5) * h
+    e = 1e-5
+    field = lambda z: sum(1.0 / np.sqrt((c[None, :] - p[0]) ** 2 + (c[:, None] - p[1]) ** 2 + (z - p[2]) ** 2)
+                          for p in src[0])
+    for i, z in enumerate(zy):
+        assert rel(S[0, i], (field(z + e) - field(z - e)) / (2 * e)) < 1e-8
+
+
+def test_pi_integral_of_a_constant_density_is_a_sum_of_solid_angles():
+    """The discrete operator on Pi's depth grid applied to a constant density: each layer contributes
+    -sgn(z - z') times the solid angle of the periodic square seen from distance |z - z'| (midpoint rule,
+    the closed form of the kernel's plane integral), times the layer thickness."""
+    n, h, half, n_pi = 128, 0.02, 1.28, 16
+    zp, nup = O.pi_depths(n_pi, half)
+    zy = [0.37]
+    U = O.forward_dft(np.ones((n_pi, n, n)), n, h, zy, zp, nup)
+    lo, hi = -(n / 2 + 0.5) * h, (n / 2 - 0.5) * h
+    want = sum(-np.sign(zy[0] - z) * _rect_solid_angle(lo, hi, lo, hi, zy[0] - z) * dz for z, dz in zip(zp, nup))
+    # the operator's horizontal sum is the midpoint rule of the plane integral: agreement to its error
+    assert np.max(np.abs(U - want)) <= 1e-3 * np.abs(want)
+
+
+def test_rhs_integral_term_equals_brute_force_quadrature_and_round_trip():
+    """I is the direct quadrature over Pi of K times sum_l 1/|x' - x_l| (built here from the definition),
+    and assembling the simulated measurement returns the left-hand side it was made from."""
+    n, x0, h, zy, half, n_pi = 6, -0.75, 0.25, [0.2], 0.75, 4
+    src = np.array([[[0.03, 0.01, -0.33]], [[-0.4, 0.2, -0.5]]])
+    S, I = O.rhs_terms(n, x0, h, zy, src, n_pi, half)
+    zp, nup = O.pi_depths(n_pi, half)
+    c = x0 + (np.arange(n) + 0.5) * h
+    for q in range(2):
+        p = src[q, 0]
+        f = 1.0 / np.sqrt((c[None, None, :] - p[0]) ** 2 + (c[None, :, None] - p[1]) ** 2 + (zp[:, None, None] - p[2]) ** 2)
+        assert rel(I[q], O.forward_direct(f, n, h, zy, zp, nup)) < 1e-12
+    U = np.random.default_rng(3).standard_normal((2, 1, n, n))
+    d = O.simulate_dV2dz(U, n, x0, h, zy, src, 1.0, 2.0, 0.5, n_pi, half)
+    assert rel(O.assemble_rhs(d, n, x0, h, zy, src, 1.0, 2.0, 0.5, n_pi, half), U) < 1e-12
