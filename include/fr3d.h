@@ -280,6 +280,20 @@ int fr3d_autotune_mode(int mode);
  * times the tuner measured on this handle (0 if it did not tune here).  Returns the variant count. */
 int fr3d_autotune_query(fr3d_handle* h, int* variant, float* ms, int cap);
 
+/* Right-hand side of Eq. (7) (the form Eq. (3) takes for point sources, Sec. 6) from the measured
+ * z-derivative of V2 on the observation depths:
+ *     U_q = 2 pi dV2/dx3 + (A2 / 2) sum_l d/dx3 (1/|x - x_{q,l}|)
+ *           - A0 / (4 pi c0^2) sum_l integral over Pi of d/dx3 (1/|x - x'|) / |x' - x_{q,l}| dx',
+ * R^3 replaced by the box Pi (Sec. 5): horizontally the handle's periodic grid, vertically a midpoint
+ * grid of n_pi (even) depths on [-pi_half, pi_half]; the integral is the discrete operator of Eq. (4)
+ * on that depth grid (the paper simulates its data this way, Sec. 6).  A0 = sources->A0; A2 =
+ * integral of t^2 g(t) dt (Sec. 2); c0 the background speed.  dV2dz and U: device [Q][M][n][n] float
+ * (U may be dV2dz).  The first call for a (n_pi, pi_half) pair builds the kernel tables of Pi's
+ * geometry (synchronous, allocates); an observation depth on Pi's depth grid is BAD_GEOMETRY, and so
+ * is a source point on a node of Pi's grid. */
+int fr3d_assemble_rhs(fr3d_handle* h, const float* dV2dz, int Q, const fr3d_sources* sources, double A2,
+                      double c0, int n_pi, double pi_half, float* U, void* stream);
+
 /* Number of kernel launches the last call on this handle enqueued (cache rebuilds excluded). */
 int fr3d_last_launch_count(fr3d_handle* h);
 

@@ -446,6 +446,68 @@ extern "C" int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const
   return invert_host_t<float>(H, U_host, Q, opts, out_host, st);
 }
 
+extern "C" int fr3d_assemble_rhs(fr3d_handle* h, const float* dV2dz, int Q, const fr3d_sources* sources, double A2,
+                                 double c0, int n_pi, double pi_half, float* U, void* stream) {
+  if (!h || !dV2dz || !U || Q < 1 || !sources || sources->q != Q) return FR3D_ERR_INVALID_ARG;
+  if (n_pi < 2 || (n_pi & 1) || !(pi_half > 0) || !isfinite(pi_half) || !isfinite(A2) || !(c0 > 0) || !isfinite(c0))
+    return FR3D_ERR_INVALID_ARG;
+  Handle* H = &h->h;
+  if (H->M > FR3D_MAX_OBS_DEPTHS) return FR3D_ERR_UNSUPPORTED_SIZE;
+  FR3D_TRY(fr3d::ensure_sources(H, sources));
+  const int L = sources->n_points;
+  // no source point may sit on a node of Pi's grid (the density 1/|x' - x_l| would be infinite there)
+  const double dzp = 2.0 * pi_half / n_pi;
+  for (int e = 0; e < Q * L; ++e) {
+    const double* p = sources->xyz + 3 * e;
+    auto off = [](double v, double o, double step) {
+      const double t = (v - o) / step - 0.5;
+      return fabs(t - nearbyint(t)) * step;
+    };
+    const double dx = off(p[0], H->x0, H->h), dy = off(p[1], H->y0, H->h), dz = off(p[2], -pi_half, dzp);
+    if (dx * dx + dy * dy + dz * dz < 1e-24 * (H->h * H->h)) return FR3D_ERR_BAD_GEOMETRY;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!H->pi || H->pi_n != n_pi || H->pi_half != pi_half) {
+    if (H->pi) fr3d_handle_destroy(H->pi);
+    H->pi = nullptr;
+    std::vector<double> zp(n_pi), nu(n_pi, dzp);
+    for (int k = 0; k < n_pi; ++k) zp[k] = -pi_half + (k + 0.5) * dzp;
+    fr3d_geometry g;
+    g.nx = g.ny = H->n;
+    g.x0 = H->x0;
+    g.y0 = H->y0;
+    g.hx = g.hy = H->h;
+    g.pad = 1;
+    g.nzr = n_pi;
+    g.zr = zp.data();
+    g.nu = nu.data();
+    g.nzy = H->M;
+    g.zy = H->zy.data();
+    g.kernel_kind = FR3D_K_DZ_INV_R;
+    FR3D_TRY(fr3d_kernel_transform(&g, &H->pi, stream));   // rejects observation depths on Pi's grid
+    H->pi_n = n_pi;
+    H->pi_half = pi_half;
+  }
+  const size_t plane = (size_t)H->n * H->n;
+  const size_t fb = (sizeof(float) * Q * n_pi * plane + 255) & ~(size_t)255;
+  const size_t ib = sizeof(float) * Q * H->M * plane;
+  if (H->rhs_bytes < fb + ib) {
+    if (H->rhs_buf) cudaFree(H->rhs_buf);
+    H->rhs_buf = nullptr;
+    H->rhs_bytes = 0;
+    FR3D_CUDA_TRY(cudaMalloc(&H->rhs_buf, fb + ib));
+    H->rhs_bytes = fb + ib;
+  }
+  float* f = reinterpret_cast<float*>(H->rhs_buf);
+  float* I = reinterpret_cast<float*>((char*)H->rhs_buf + fb);
+  FR3D_TRY(fr3d::rhs_pi_density(f, Q, n_pi, H->n, H->x0, H->h, pi_half, H->pts64, L, st));
+  FR3D_TRY(fr3d::fwd_impl<float>(&H->pi->h, f, Q, I, st));
+  const double coef = sources->A0 / (4.0 * 3.14159265358979323846 * c0 * c0);
+  FR3D_TRY(fr3d::rhs_combine(H, dV2dz, I, U, Q, H->pts64, L, A2, coef, st));
+  H->last_launches = 2 + H->pi->h.last_launches;
+  return FR3D_OK;
+}
+
 extern "C" int fr3d_last_launch_count(fr3d_handle* h) { return h ? h->h.last_launches : -1; }
 
 extern "C" int fr3d_profile_enable(fr3d_handle* h, int enable) {

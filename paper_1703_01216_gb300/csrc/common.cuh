@@ -97,6 +97,13 @@ struct Handle {
   float* mUt = nullptr;        // [C][M][M]
   float* mW = nullptr;         // [C][M][M']
   int m_sweeps = 0;            // Jacobi sweeps the slowest class needed
+  // right-hand side of Eq. (7): the handle of the box Pi's geometry (same grid, Pi's depths as the
+  // unknown depths) and its buffers (density on Pi, integral term on Y)
+  fr3d_handle* pi = nullptr;
+  int pi_n = 0;
+  double pi_half = 0.0;
+  void* rhs_buf = nullptr;
+  size_t rhs_bytes = 0;
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;

@@ -71,6 +71,13 @@ void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double*
 int inv_fused_presolved_f32(const Handle* H, const float2* Zs, const float* W, float* out, int Q, int output,
                             cudaStream_t st);
 
+// right-hand side of Eq. (7) (rhs.cu): the density sum_l 1/|x' - x_l| on the box Pi, and the combination
+// U = 2 pi d + (A2 / 2) sum_l d/dx3 (1/|x - x_l|) - coef I on the observation grid
+int rhs_pi_density(float* f, int Q, int npi, int n, double x0, double h, double half, const double* pts, int L,
+                   cudaStream_t st);
+int rhs_combine(const Handle* H, const float* d, const float* I, float* U, int Q, const double* pts, int L,
+                double A2, double coef, cudaStream_t st);
+
 // precision-independent table builders (alpha tables, fixed alpha)
 int alpha_tables(Handle* H, const double* alphas, int n_alpha, int ra, cudaStream_t st);
 int fixed_table(Handle* H, double alpha, int ra, cudaStream_t st);

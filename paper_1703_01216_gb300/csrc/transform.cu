@@ -296,11 +296,13 @@ static int kernel_transform_impl(const fr3d_geometry* g, Handle* H, cudaStream_t
 void handle_free(Handle* H) {
   void* ptrs[] = {H->A64, H->nrm, H->s2, H->A32, H->A64d, H->tw32, H->tw64, H->Ft, H->D32, H->D64,
                   H->Dfix32, H->Dfix64, H->zr64, H->zr32, H->wtab, H->Dd32, H->Ddfix32, H->pts32, H->pts64, H->counter, H->idx_scratch, H->zero_idx,
-                  H->info_scratch, H->partials, H->cband, H->bbin, H->mlam, H->mUt, H->mW, H->ws};
+                  H->info_scratch, H->partials, H->cband, H->bbin, H->mlam, H->mUt, H->mW, H->rhs_buf, H->ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < Handle::kMaxEv; ++i)
     if (H->ev[i]) cudaEventDestroy(H->ev[i]);
+  if (H->pi) fr3d_handle_destroy(H->pi);
+  H->pi = nullptr;
 }
 
 int validate_geometry(const fr3d_geometry* g) {

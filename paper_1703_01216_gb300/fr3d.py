@@ -70,7 +70,7 @@ EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", 
            "fr3d_invert_batched",
            "fr3d_mlp_create", "fr3d_mlp_destroy", "fr3d_mlp_query", "fr3d_mlp_get_params", "fr3d_mlp_set_params",
            "fr3d_mlp_forward", "fr3d_mlp_gradient", "fr3d_mlp_train_step", "fr3d_band_features",
-           "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query")
+           "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query", "fr3d_assemble_rhs")
 
 
 def load(path: str | None = None):
@@ -115,6 +115,7 @@ def load(path: str | None = None):
     lib.fr3d_band_alpha_targets.argtypes = [vp, vp, vp, i, _dp, i, i, vp, vp, vp, vp]
     lib.fr3d_autotune_mode.argtypes = [i]
     lib.fr3d_autotune_query.argtypes = [vp, ct.POINTER(i), ct.POINTER(ct.c_float), i]
+    lib.fr3d_assemble_rhs.argtypes = [vp, vp, i, ct.POINTER(Sources), d, d, i, d, vp, vp]
     lib.fr3d_status_string.argtypes = [i]
     lib.fr3d_status_string.restype = ct.c_char_p
     for name in EXPORTS:
@@ -285,6 +286,13 @@ def profile_read(handle: Handle, cap: int = 96):
     ms = (ct.c_float * cap)()
     n = _check(load().fr3d_profile_read(handle.ptr, kinds, ms, cap), "fr3d_profile_read")
     return [(STAGE_NAMES[kinds[i]], float(ms[i])) for i in range(n)]
+
+
+def assemble_rhs(handle: Handle, dV2dz, Q: int, points, A2: float, c0: float, n_pi: int, pi_half: float, U,
+                 A0: float = 1.0, stream=None):
+    src, keep = make_sources(points, A0)
+    _check(load().fr3d_assemble_rhs(handle.ptr, _ptr(dV2dz), int(Q), ct.byref(src), float(A2), float(c0), int(n_pi),
+                                    float(pi_half), _ptr(U), _stream(stream)), "fr3d_assemble_rhs")
 
 
 def autotune_mode(mode: int | None = None) -> int:

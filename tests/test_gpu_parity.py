@@ -368,3 +368,29 @@ def test_inv_r_kernel_forward_and_inversion_match_oracle(F, n, mp, q, m):
         xi = torch.empty((mp, n, n), device="cuda")
         F.invert(H, dev(Ud), q, xi, F.Opts(alpha=alpha, points=w.sources))
         assert rel(host(xi), r["xi"]) <= 1e-4, (alpha, rel(host(xi), r["xi"]))
+
+
+# ------------------------------------------------------------------ right-hand side of Eq. (7)
+@pytest.mark.parametrize("m", [1, 2])
+def test_assemble_rhs_matches_oracle(F, m):
+    n, n_pi, half, A2, c0 = 32, 8, 1.0, 2.0, 0.5
+    w = I.make_workload(n, 4, q=2, m_obs=m, seed=31 + m)
+    H = handle_for(F, w)
+    rng = np.random.default_rng(m)
+    d = rng.standard_normal((2, m, n, n))
+    ref = O.assemble_rhs(d, n, w.x0, w.h, w.zy, w.sources, 1.0, A2, c0, n_pi, half)
+    U = torch.empty((2, m, n, n), device="cuda")
+    F.assemble_rhs(H, dev(d), 2, w.sources, A2, c0, n_pi, half, U)
+    S, Iq = O.rhs_terms(n, w.x0, w.h, w.zy, w.sources, n_pi, half)
+    scale = np.linalg.norm(2 * np.pi * d) + np.linalg.norm(0.5 * A2 * S) + np.linalg.norm(Iq / (4 * np.pi * c0 * c0))
+    assert np.linalg.norm(host(U) - ref) <= 1e-5 * scale
+    # the simulated measurement of a left-hand side assembles back to it
+    lhs = rng.standard_normal((2, m, n, n))
+    meas = O.simulate_dV2dz(lhs, n, w.x0, w.h, w.zy, w.sources, 1.0, A2, c0, n_pi, half)
+    F.assemble_rhs(H, dev(meas), 2, w.sources, A2, c0, n_pi, half, U)
+    assert np.linalg.norm(host(U) - lhs) <= 1e-5 * scale
+    # a source on a node of Pi's grid is rejected before any launch
+    bad = np.array(w.sources)
+    bad[0, 0] = [w.x0 + 0.5 * w.h, w.x0 + 0.5 * w.h, -half + 0.5 * 2 * half / n_pi]
+    with pytest.raises(F.Fr3dError):
+        F.assemble_rhs(H, dev(d), 2, bad, A2, c0, n_pi, half, U)
