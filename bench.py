@@ -225,6 +225,39 @@ def setup_gpu(w, dev):
     return H, U, delta
 
 
+def capture_step(fr3d, H, dev, st, step, traced):
+    """One step (`step()`) captured as a CUDA graph: as is (traced=False: the timed step, no event nodes
+    between its launches) or with the library tracer's stage events between them (traced=True: the
+    per-stage times).  The tracer keeps the events of the latest traced capture only."""
+    import torch
+    fr3d.profile_enable(H, traced)
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(st)
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(g, stream=cap):
+            step()
+    st.wait_stream(cap)
+    return g
+
+
+def traced_stage_ms(fr3d, H, graph_tr, flush, reps):
+    """Per-stage milliseconds summed over `reps` replays of a traced capture (L2 flushed before each),
+    and the number of launches behind each sum; the cached-table stage is left out.  Switches the
+    tracer off afterwards."""
+    stage_ms, stage_launches = {}, {}
+    for _ in range(reps):
+        flush.fill_(1.0)
+        graph_tr.replay()
+        for name, ms in fr3d.profile_read(H):
+            if name == "table":
+                continue
+            stage_ms[name] = stage_ms.get(name, 0.0) + ms
+            stage_launches[name] = stage_launches.get(name, 0) + 1
+    fr3d.profile_enable(H, False)
+    return stage_ms, stage_launches
+
+
 def run_fr3d(args):
     import torch
     from paper_1703_01216_gb300 import fr3d
@@ -260,23 +293,19 @@ def run_fr3d(args):
         flush.fill_(1.0)
         fr3d.invert(H, U, Q, out, opts)
     torch.cuda.synchronize()
-    # one step captured as a CUDA graph (its launches, and the stage events of the tracer)
-    fr3d.profile_enable(H, True)
-    graph = torch.cuda.CUDAGraph()
-    cap = torch.cuda.Stream(dev)
-    cap.wait_stream(st)
-    with torch.cuda.stream(cap):
-        with torch.cuda.graph(graph, stream=cap):
-            fr3d.invert(H, U, Q, out, opts)
-    st.wait_stream(cap)
+    # one step captured as a CUDA graph, twice: as is (the timed step) and with the stage events of
+    # the library's tracer between its launches (the per-stage times, replayed after the timed loop)
+    def step():
+        fr3d.invert(H, U, Q, out, opts)
+    graph = capture_step(fr3d, H, dev, st, step, False)
+    graph_tr = capture_step(fr3d, H, dev, st, step, True)
     launches_per_step = fr3d.last_launch_count(H)
     tuned_variant, tune_ms = fr3d.autotune_query(H)
-    for _ in range(max(3, args.warmup)):
-        flush.fill_(1.0)
-        graph.replay()
+    for g in (graph, graph_tr):
+        for _ in range(max(3, args.warmup)):
+            flush.fill_(1.0)
+            g.replay()
     torch.cuda.synchronize()
-    stage_ms = {}
-    stage_launches = {}
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
@@ -289,15 +318,10 @@ def run_fr3d(args):
             graph.replay()
             ev[k][1].record(st)
             launches += launches_per_step
-            for name, ms in fr3d.profile_read(H):
-                if name == "table":
-                    continue
-                stage_ms[name] = stage_ms.get(name, 0.0) + ms
-                stage_launches[name] = stage_launches.get(name, 0) + 1
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    fr3d.profile_enable(H, False)
+    stage_ms, stage_launches = traced_stage_ms(fr3d, H, graph_tr, flush, args.steps)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
     value = whole_job_rate(voxels, world, args.steps, total_s)
@@ -414,21 +438,17 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
         flush.fill_(1.0)
         fr3d.invert(H, U, Q, out, opts)
     torch.cuda.synchronize()
-    fr3d.profile_enable(H, True)
-    graph = torch.cuda.CUDAGraph()
-    cap = torch.cuda.Stream(dev)
-    cap.wait_stream(st)
-    with torch.cuda.stream(cap):
-        with torch.cuda.graph(graph, stream=cap):
-            fr3d.invert(H, U, Q, out, opts)
-    st.wait_stream(cap)
+    def step():
+        fr3d.invert(H, U, Q, out, opts)
+    graph = capture_step(fr3d, H, dev, st, step, False)
+    graph_tr = capture_step(fr3d, H, dev, st, step, True)
     launches_per_step = fr3d.last_launch_count(H)
-    for _ in range(3):
-        flush.fill_(1.0)
-        graph.replay()
+    for g in (graph, graph_tr):
+        for _ in range(3):
+            flush.fill_(1.0)
+            g.replay()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_ms = {}
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -437,11 +457,8 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
         ev[k][0].record(st)
         graph.replay()
         ev[k][1].record(st)
-        for name, ms in fr3d.profile_read(H):
-            if name != "table":
-                stage_ms[name] = stage_ms.get(name, 0.0) + ms
     torch.cuda.synchronize()
-    fr3d.profile_enable(H, False)
+    stage_ms, _ = traced_stage_ms(fr3d, H, graph_tr, flush, args.steps)
     total_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, dev)
     world = dist.get_world_size() if dist else 1
     xi_true = torch.tensor(w.xi_true, device=dev)
@@ -496,21 +513,17 @@ def bench_paper_geometry(args, dev, flush, n=256, m=51, mp=51, n_alpha=32):
         torch.cuda.synchronize()
         if name == "tsvd":
             res["cold_s"] = round(time.perf_counter() - t0, 3)
-        fr3d.profile_enable(H, True)
-        g = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream(dev)
-        cap.wait_stream(st)
-        with torch.cuda.stream(cap):
-            with torch.cuda.graph(g, stream=cap):
-                fr3d.invert(H, U, 1, out, opts)
-        st.wait_stream(cap)
-        for _ in range(3):
-            flush.fill_(1.0)
-            g.replay()
+        def step():
+            fr3d.invert(H, U, 1, out, opts)
+        g = capture_step(fr3d, H, dev, st, step, False)
+        g_tr = capture_step(fr3d, H, dev, st, step, True)
+        for gr in (g, g_tr):
+            for _ in range(3):
+                flush.fill_(1.0)
+                gr.replay()
         torch.cuda.synchronize()
         reps = max(5, min(args.steps, 20))
         tot = 0.0
-        stages = {}
         for _ in range(reps):
             flush.fill_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -519,9 +532,7 @@ def bench_paper_geometry(args, dev, flush, n=256, m=51, mp=51, n_alpha=32):
             b.record(st)
             b.synchronize()
             tot += a.elapsed_time(b)
-            for k, v in fr3d.profile_read(H):
-                stages[k] = stages.get(k, 0.0) + v
-        fr3d.profile_enable(H, False)
+        stages, _ = traced_stage_ms(fr3d, H, g_tr, flush, reps)
         res[name] = {"value": n * n * mp * reps / (tot * 1e-3), "unit": "voxels/s", "ms_per_step": tot / reps,
                      "stages_ms_per_step": {k: round(v / reps, 5) for k, v in stages.items()},
                      "alpha_index": int(idx.item()), "launches": fr3d.last_launch_count(H),

@@ -39,6 +39,10 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 
+// Programmatic dependent launch: wait until the kernel this one depends on has completed and its
+// writes are visible (returns at once when the launch was not programmatic).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // CL: CTAs per cluster (above 8 a non-portable cluster size), NT: threads, RB: rows per row batch,
 // MINB: resident CTAs per SM that the register budget is sized for; GACC: accumulate xi in the output
 // array (L2-resident read-modify-write) instead of shared memory
@@ -136,15 +140,18 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   const long ps = (long)(L + 1) * N;
 
   // ---------------- set-up: twiddles and the q-invariant solve weights of the owned columns
+  // The twiddle tables depend on nothing the previous kernel writes: they are built before waiting on
+  // it (with a programmatic launch this kernel may start while the alpha rule finishes).
+  for (int e = tid; e < N; e += NT) tws[e] = __ldg(a.tw_n + e);
+  build_passtw<N, 1, NT>(ptc, a.tw_n, tid);
+  build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
+  grid_dependency_wait();
   __shared__ int s_aidx[FR3D_MAX_BANDS];
   if (tid < a.nb) s_aidx[tid] = min(max(a.aidx[tid], 0), a.na - 1);   // a caller-given index stays in the table
   __syncthreads();
   {
     const float* Aj = a.A + (long)j * ps;
     const float* drow = a.Dd + (long)s_aidx[0] * ps;
-    for (int e = tid; e < N; e += NT) tws[e] = __ldg(a.tw_n + e);
-    build_passtw<N, 1, NT>(ptc, a.tw_n, tid);
-    build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
     // solve weight of bin o = kx n + ky: row aidx[band(o)] of Dd (one row when nb = 1); with bands the
     // band indices of all of this thread's bins are fetched first, then every weight in one round
     if constexpr (PRE) {
@@ -352,13 +359,17 @@ int launch_clustered(K kern, int clusters, int nt, size_t sm, cudaStream_t st, A
   cfg.blockDim = dim3(nt);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  // cluster dimension, and a programmatic launch: the kernel may start while the previous kernel in the
+  // stream finishes (it builds its twiddle tables, then waits for that kernel before reading its output)
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   FR3D_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args...));
   return FR3D_OK;
 }
