@@ -267,7 +267,8 @@ int fr3d_band_alpha_targets(fr3d_handle* h, const float* U, const float* zeta_tr
  * The fused inverse has tile variants that compute the same bits (variant 0: the built-in table of
  * cluster size, threads and row-batch height per n with xi accumulated in shared memory; 1: xi
  * accumulated in the output array with taller row batches where they fit; 2: xi in the output
- * array, table batches).  Modes: 0 = always variant 0; 1 (default) = on the first fr3d_invert of a
+ * array, table batches; 3: one row batch of all a CTA's rows, xi accumulated in registers and
+ * written once).  Modes: 0 = always variant 0; 1 (default) = on the first fr3d_invert of a
  * shape (device, n, M', Q, output) made outside a stream capture, time every variant on that
  * call's own arguments (1 warm-up + 3 timed launches each, synchronising the stream once) and use
  * the fastest from then on, process-wide; 2 + v = always variant v.  A batched plan (mode 1) times

@@ -64,15 +64,20 @@ template <> struct FusedCfg<384> : FusedCfgBase { static constexpr int CL = 8, N
 // Tile variants of the fused inverse (chosen at run time by the autotuner in fused_f32.cu):
 //   V = 0  the table above;
 //   V = 1  xi accumulated in the output array, row batches twice as tall when they divide the rows;
-//   V = 2  xi accumulated in the output array, row batches as in the table.
+//   V = 2  xi accumulated in the output array, row batches as in the table;
+//   V = 3  one row batch of all the CTA's rows, so that every thread owns the same outputs for every
+//          source parameter: xi accumulated in registers and written once.
 // All variants perform the same arithmetic in the same order: their outputs are bit-identical.
-constexpr int kFusedVariants = 3;
+constexpr int kFusedVariants = 4;
 template <int N, int V> struct FusedCfgV {
   using B = FusedCfg<N>;
   static constexpr int CL = B::CL, NT = B::NT, MINB = B::MINB;
-  static constexpr int RB = (V == 1 && (N / CL) % (2 * B::RB) == 0 && (2 * B::RB * (N / 2)) % NT == 0)
+  static constexpr int RB = V == 3 ? N / CL
+                          : (V == 1 && (N / CL) % (2 * B::RB) == 0 && (2 * B::RB * (N / 2)) % NT == 0)
                                 ? 2 * B::RB : B::RB;
-  static constexpr bool GACC = V == 0 ? B::GACC : true;
+  static constexpr bool GACC = V == 0 ? B::GACC : V != 3;
+  static constexpr bool RACC = V == 3;
+  static constexpr bool SACC = !GACC && !RACC;   // xi accumulated in shared memory
 };
 
 template <int N, int V = 0> struct FusedGeom {
@@ -91,7 +96,7 @@ template <int N, int V = 0> struct FusedGeom {
   static constexpr int PTC = passtw_size<N>(), PTR = passtw_size<L>();
   static constexpr size_t smem_zeta = sizeof(float2) * ((size_t)CPC * SSC + (size_t)RB * SSR + N + PTC + PTR) +
                                       sizeof(float) * (size_t)(CPC + 1) * N;
-  static constexpr size_t smem_xi = smem_zeta + (Cf::GACC ? 0 : sizeof(float) * (size_t)NRW * N);
+  static constexpr size_t smem_xi = smem_zeta + (Cf::SACC ? sizeof(float) * (size_t)NRW * N : 0);
   static_assert(L % CL == 0, "column split");
   static_assert(NRW % RB == 0, "row batches");
   static_assert((RB * L) % NT == 0, "outputs per thread");
@@ -130,7 +135,8 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   float2* ptc = tws + N;                     // pass tables, length n (columns)
   float2* ptr = ptc + G::PTC;                // pass tables, length n/2 (rows)
   float* wsm = reinterpret_cast<float*>(ptr + G::PTR);   // [CPC][n] weights of the owned columns, then w(n/2, .)
-  float2* accs = reinterpret_cast<float2*>(wsm + (CPC + 1) * N);  // XI: [NRW][n/2] pairs of the owned rows
+  // XI with the shared-memory accumulator only: [NRW][n/2] pairs of the owned rows
+  float2* accs = reinterpret_cast<float2*>(wsm + (CPC + 1) * N);
   const int tid = threadIdx.x;
   int r = 0;
   if constexpr (CL > 1) r = (int)cg::this_cluster().block_rank();
@@ -211,6 +217,18 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
     if (kx == L) return make_float2(v.y, 0.f);   // imaginary part is kx = n/2
     return v;
   };
+
+  // register accumulator of xi (variant 3): element [k][rr] is the output that butterfly tid + k NT of
+  // the last row pass writes as its rr-th value (the same rows and columns for every q: one row batch)
+  using LPo = LastPass<L>;
+  constexpr bool RACC = MODE == 1 && G::Cf::RACC;
+  constexpr int KRA = RACC ? (RB * LPo::BPS + NT - 1) / NT : 1, RRA = RACC ? LPo::R : 1;
+  static_assert(!RACC || NB == 1, "the register accumulator needs one row batch");
+  float2 racc[KRA][RRA];
+#pragma unroll
+  for (int k = 0; k < KRA; ++k)
+#pragma unroll
+    for (int rr = 0; rr < RRA; ++rr) racc[k][rr] = make_float2(0.f, 0.f);
 
   for (int q = 0; q < a.Q; ++q) {
     const float2* Zq = a.Uh + (long)q * ps;
@@ -300,7 +318,13 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
         if (b == NB - 1) cluster_arrive_relaxed();
       __syncthreads();
       fft_passes<L, true, RB, NT, 0, Plan<L>::np - 1>(rowbuf, SSR, ptr, tid);
-      if constexpr (MODE == 1) {
+      if constexpr (RACC) {
+        // fmaf(w, v, 0) for q = 0, as in the accumulators of the other variants
+        auto emit = [&](int, int, float2 v, int k, int rr) {
+          racc[k][rr] = make_float2(fmaf(wv[k][rr].x, v.x, racc[k][rr].x), fmaf(wv[k][rr].y, v.y, racc[k][rr].y));
+        };
+        last_pass_to<L, true, RB, NT>(rowbuf, SSR, ptr, emit, tid);
+      } else if constexpr (MODE == 1) {
         float2* acb = accs + b * RB * L;
         if constexpr (G::Cf::GACC) acb = reinterpret_cast<float2*>(a.out + ((long)j * N + y0 + b * RB) * N);
         auto emit = [&](int sr, int t, float2 v, int k, int rr) {
@@ -317,9 +341,22 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
       __syncthreads();
     }
   }
+  if constexpr (RACC) {
+    // xi of the owned rows, in the positions the last row pass produced them
+    float2* ov = reinterpret_cast<float2*>(a.out + ((long)j * N + y0) * N);
+#pragma unroll
+    for (int k = 0; k < KRA; ++k) {
+      const int bb = tid + k * NT;
+      if ((RB * LPo::BPS) % NT == 0 || bb < RB * LPo::BPS) {
+        const int sr = bb / LPo::BPS, jq = bb - sr * LPo::BPS;
+#pragma unroll
+        for (int rr = 0; rr < RRA; ++rr) ov[sr * L + jq + rr * LPo::NS] = racc[k][rr];
+      }
+    }
+  }
   // no CTA leaves while a peer may still read its shared memory
   if constexpr (CL > 1) cluster_wait();
-  if constexpr (MODE == 1 && !G::Cf::GACC) {
+  if constexpr (MODE == 1 && G::Cf::SACC) {
     // xi of the owned rows; the last barrier of the q loop ordered every accumulator write first
     float2* ov = reinterpret_cast<float2*>(a.out + ((long)j * N + y0) * N);
 #pragma unroll 4

@@ -27,6 +27,8 @@ __global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, d
   }
 }
 
+static_assert(sizeof(Handle::fused_tune_ms) / sizeof(float) >= kFusedVariants, "one tuning time per variant");
+
 namespace {
 
 // ---------------- autotuner of the fused inverse's tile variant
@@ -49,6 +51,7 @@ int launch_variant(int v, int n, bool xi, const FusedArgs& a, int nj, cudaStream
     case 0: return fused_launch<0>(n, xi, a, nj, st);
     case 1: return fused_launch<1>(n, xi, a, nj, st);
     case 2: return fused_launch<2>(n, xi, a, nj, st);
+    case 3: return fused_launch<3>(n, xi, a, nj, st);
   }
   return FR3D_ERR_INVALID_ARG;
 }
@@ -144,6 +147,7 @@ int launch_batched_variant(int v, int n, bool xi, const FusedArgs* inst, const i
     case 0: return fused_launch_batched<0>(n, xi, inst, map, ncl, st);
     case 1: return fused_launch_batched<1>(n, xi, inst, map, ncl, st);
     case 2: return fused_launch_batched<2>(n, xi, inst, map, ncl, st);
+    case 3: return fused_launch_batched<3>(n, xi, inst, map, ncl, st);
   }
   return FR3D_ERR_INVALID_ARG;
 }

@@ -9,6 +9,7 @@ from paper_1703_01216_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+NV = 4   # tile variants of the fused inverse (0: shared-memory xi, 1-2: xi in the output array, 3: in registers)
 
 
 @pytest.fixture(scope="module")
@@ -41,13 +42,13 @@ def test_variants_are_bit_identical_and_match_oracle(F, n, mp, q, output):
     out_kind = F.OUT_XI if output == "xi" else F.OUT_ZETA
     shape = (mp, n, n) if output == "xi" else (q, mp, n, n)
     outs = []
-    for v in range(3):
+    for v in range(NV):
         F.autotune_mode(2 + v)
         o = torch.full(shape, float("nan"), device="cuda")
         F.invert(H, U, q, o, F.Opts(alpha=1e-3, output=out_kind, points=w.sources))
         assert F.autotune_query(H)[0] == v
         outs.append(o)
-    for v in (1, 2):
+    for v in range(1, NV):
         assert torch.equal(outs[v], outs[0]), v
     ref = O.invert(U.double().cpu().numpy(), n, w.x0, w.h, w.zy, w.zr, w.nu, alpha=1e-3, sources=w.sources,
                    output=output)
@@ -62,7 +63,7 @@ def test_tuner_times_every_variant_and_keeps_the_fastest(F):
     out = torch.empty((7, 128, 128), device="cuda")
     F.invert(H, U, 2, out, F.Opts(alphas=w.alphas, delta=delta, points=w.sources))
     v, ms = F.autotune_query(H)
-    assert len(ms) == 3 and all(t > 0 for t in ms)
+    assert len(ms) == NV and all(t > 0 for t in ms)
     assert ms[v] == min(ms)
     # a second handle of the same shape reuses the choice without timing
     H2 = F.kernel_transform(w.n, w.x0, w.h, w.zr, w.zy, w.nu)
@@ -82,14 +83,14 @@ def test_batched_plan_is_identical_under_every_variant(F):
         items.append((H, U, q, F.Opts(alphas=w.alphas, delta=delta, points=w.sources),
                       torch.empty((mp, n, n), device="cuda")))
     results = []
-    for v in range(3):
+    for v in range(NV):
         F.autotune_mode(2 + v)
         B = F.Batch(items)
         B.run()
         torch.cuda.synchronize()
         results.append([it[4].clone() for it in items])
         B.close()
-    for v in (1, 2):
+    for v in range(1, NV):
         for a, b in zip(results[0], results[v]):
             assert torch.equal(a, b)
     F.autotune_mode(1)
