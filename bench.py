@@ -374,7 +374,9 @@ def run_fr3d(args):
                    "parallelism": f"replicas x{world} (independent instances)"},
         "gpu_launches": launches,
         "e2e": {"value": whole_job_rate(voxels, world, e2e_steps, e2e_total), "unit": "voxels/s",
-                "h2d_bytes_per_step": int(U_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4)},
+                "h2d_bytes_per_step": int(U_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4),
+                "transfer": "page-locked host buffers used in place by the kernels over the host link (U read by "
+                            "the first row pass, xi written by the fused inverse), stream synchronised per step"},
         "roofline": roof,
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
         "cold_setup_s": round(t_cold, 3),

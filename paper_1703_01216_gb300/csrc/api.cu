@@ -233,7 +233,7 @@ int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
 
 template <typename T>
 int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out, const InvertPlan& p,
-                cudaStream_t st) {
+                cudaStream_t st, bool out_host_mapped = false) {
   using C = typename Ops<T>::C;
   if constexpr (sizeof(T) == 4) {
     if (H->M > 1) {
@@ -302,7 +302,7 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
         prof_mark(H, kStTable, st);
       }
       const float* Dd = o->alpha_mode == FR3D_ALPHA_FIXED ? H->Ddfix32 : H->Dd32;
-      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, nb, H->wtab, out, Q, 0, H->Mp, o->output, st));
+      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, nb, H->wtab, out, Q, 0, H->Mp, o->output, st, out_host_mapped));
       prof_mark(H, kStFused, st);
       H->last_launches = launches + 1;
       return FR3D_OK;
@@ -419,6 +419,23 @@ extern "C" int fr3d_invert(fr3d_handle* h, const void* U, int Q, const fr3d_inve
   return fr3d::invert_impl<float>(H, (const float*)U, Q, opts, (float*)out, p, st);
 }
 
+// The device address of a host buffer of `bytes` bytes that lies in one page-locked, device-mapped
+// range (cudaHostAlloc, cudaHostRegister), 16-byte aligned; nullptr otherwise (pageable memory).
+static void* host_mapped_alias(const void* p, size_t bytes) {
+  if (bytes == 0 || reinterpret_cast<uintptr_t>(p) % 16) return nullptr;
+  cudaPointerAttributes a0, a1;
+  const char* last = static_cast<const char*>(p) + (bytes - 1);
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+    return nullptr;
+  if (static_cast<char*>(a1.devicePointer) - static_cast<char*>(a0.devicePointer) != (ptrdiff_t)(bytes - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
 template <typename T>
 static int invert_host_t(Handle* H, const void* U_host, int Q, const fr3d_invert_opts* o, void* out_host,
                          cudaStream_t st) {
@@ -429,9 +446,18 @@ static int invert_host_t(Handle* H, const void* U_host, int Q, const fr3d_invert
   T* Od = reinterpret_cast<T*>((char*)H->ws + p.out_off);
   const size_t in_b = sizeof(T) * (size_t)Q * H->M * n * n;
   const size_t out_b = sizeof(T) * (size_t)(o->output == FR3D_OUT_XI ? 1 : Q) * H->Mp * n * n;
-  FR3D_CUDA_TRY(cudaMemcpyAsync(Ud, U_host, in_b, cudaMemcpyHostToDevice, st));
-  FR3D_TRY(fr3d::invert_impl<T>(H, Ud, Q, o, Od, p, st));
-  FR3D_CUDA_TRY(cudaMemcpyAsync(out_host, Od, out_b, cudaMemcpyDeviceToHost, st));
+  // FP32, one observation depth: page-locked host buffers are used in place over the host link (the
+  // first row pass reads U, the last kernel writes the result; each element crosses once), so the
+  // transfers overlap the kernels instead of preceding and following them
+  const T* Uin = Ud;
+  T* Out = Od;
+  if (sizeof(T) == 4 && H->M == 1) {
+    if (void* m = host_mapped_alias(U_host, in_b)) Uin = static_cast<const T*>(m);
+    if (void* m = host_mapped_alias(out_host, out_b)) Out = static_cast<T*>(m);
+  }
+  if (Uin == Ud) FR3D_CUDA_TRY(cudaMemcpyAsync(Ud, U_host, in_b, cudaMemcpyHostToDevice, st));
+  FR3D_TRY(fr3d::invert_impl<T>(H, Uin, Q, o, Out, p, st, Out != Od));
+  if (Out == Od) FR3D_CUDA_TRY(cudaMemcpyAsync(out_host, Od, out_b, cudaMemcpyDeviceToHost, st));
   FR3D_CUDA_TRY(cudaStreamSynchronize(st));
   return FR3D_OK;
 }

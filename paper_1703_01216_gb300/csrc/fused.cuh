@@ -69,6 +69,9 @@ template <> struct FusedCfg<384> : FusedCfgBase { static constexpr int CL = 8, N
 //          source parameter: xi accumulated in registers and written once.
 // All variants perform the same arithmetic in the same order: their outputs are bit-identical.
 constexpr int kFusedVariants = 4;
+// Variants 1 and 2 in XI mode read the output array back for every q (accumulator in the output
+// array); 0 and 3 write every output once.
+constexpr bool fused_rereads_output(int v) { return v == 1 || v == 2; }
 template <int N, int V> struct FusedCfgV {
   using B = FusedCfg<N>;
   static constexpr int CL = B::CL, NT = B::NT, MINB = B::MINB;

@@ -38,9 +38,9 @@ namespace {
 // variant v.  Calls inside a capture use the tuned choice if there is one, else variant 0.
 std::atomic<int> g_tune_mode{1};
 struct TuneKey {
-  int dev, n, nj, Q, xi;
+  int dev, n, nj, Q, xi, once;   // once: only variants that write every output once (mapped host output)
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, n, nj, Q, xi) < std::tie(o.dev, o.n, o.nj, o.Q, o.xi);
+    return std::tie(dev, n, nj, Q, xi, once) < std::tie(o.dev, o.n, o.nj, o.Q, o.xi, o.once);
   }
 };
 std::mutex g_tune_mu;
@@ -56,7 +56,9 @@ int launch_variant(int v, int n, bool xi, const FusedArgs& a, int nj, cudaStream
   return FR3D_ERR_INVALID_ARG;
 }
 
-int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, cudaStream_t st, int* v_out) {
+// once: the output lives in page-locked host memory that the kernel writes over the host link; the
+// tuner then times only the variants that write every output once (a forced variant is still used).
+int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, bool once, cudaStream_t st, int* v_out) {
   const int mode = g_tune_mode.load();
   if (mode >= 2) {
     *v_out = std::min(mode - 2, kFusedVariants - 1);
@@ -64,7 +66,8 @@ int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, cudaStream_t 
   }
   *v_out = 0;
   if (mode == 0) return FR3D_OK;
-  const TuneKey key{H->dev, H->n, nj, a.Q, xi ? 1 : 0};
+  once = once && xi;
+  const TuneKey key{H->dev, H->n, nj, a.Q, xi ? 1 : 0, once ? 1 : 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -82,6 +85,10 @@ int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, cudaStream_t 
   int best = 0, st_ok = FR3D_OK;
   float best_ms = 3.4e38f;
   for (int v = 0; v < kFusedVariants && st_ok == FR3D_OK; ++v) {
+    if (once && fused_rereads_output(v)) {
+      H->fused_tune_ms[v] = 0.f;
+      continue;
+    }
     st_ok = launch_variant(v, H->n, xi, a, nj, st);
     if (st_ok == FR3D_OK && cudaEventRecord(e0, st) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
     for (int rep = 0; rep < 3 && st_ok == FR3D_OK; ++rep) st_ok = launch_variant(v, H->n, xi, a, nj, st);
@@ -118,7 +125,7 @@ bool fused_supported(int n) {
 }
 
 int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
-                  float* out, int Q, int j0, int nj, int output, cudaStream_t st) {
+                  float* out, int Q, int j0, int nj, int output, cudaStream_t st, bool out_host_mapped) {
   FusedArgs a;
   a.Uh = Uh;
   a.A = H->A32;
@@ -136,7 +143,7 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   a.Zs = nullptr;
   const bool xi = output == FR3D_OUT_XI;
   int v = 0;
-  FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, nj, xi, st, &v));
+  FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, nj, xi, out_host_mapped, st, &v));
   const_cast<Handle*>(H)->fused_var = v;
   return launch_variant(v, H->n, xi, a, nj, st);
 }

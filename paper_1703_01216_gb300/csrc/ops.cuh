@@ -40,10 +40,12 @@ template <typename T> struct Ops {
                           double* residuals, int* info, cudaStream_t st);
 };
 
-// fused inverse (FP32, M = 1): solve + inverse 2D DFT + combination for depths j0 .. j0 + nj - 1
+// fused inverse (FP32, M = 1): solve + inverse 2D DFT + combination for depths j0 .. j0 + nj - 1;
+// out_host_mapped: out is the device address of page-locked host memory (the autotuner then keeps to
+// the variants that write every output once)
 bool fused_supported(int n);
 int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
-                  float* out, int Q, int j0, int nj, int output, cudaStream_t st);
+                  float* out, int Q, int j0, int nj, int output, cudaStream_t st, bool out_host_mapped = false);
 // W_q = V0_q / sum_q' V0_q'^2 on the R grid for the handle's cached sources
 int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st);
 
