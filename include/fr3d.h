@@ -187,9 +187,13 @@ int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const double* alphas
 int fr3d_invert(fr3d_handle* h, const void* U, int Q, const fr3d_invert_opts* opts, void* out,
                 void* stream);
 
-/* fr3d_invert with HOST buffers: copies U (host [Q][M][n][n]) to the device, inverts and copies
- * the result back to out (host); returns after the stream has synchronised.  Pinned host memory
- * gives asynchronous copies; pageable memory also works. */
+/* fr3d_invert with HOST buffers U (host [Q][M][n][n]) and out (host, the shape of fr3d_invert's
+ * out); returns after the stream has synchronised.  FP32 with one observation depth (M = 1): a
+ * buffer that lies in one page-locked, device-mapped range (cudaHostAlloc, cudaHostRegister) and
+ * starts on a 16-byte boundary is used in place: the first row pass reads U and the last kernel
+ * writes out over the host link, each element once.  Otherwise (pageable or unaligned memory,
+ * FP64, M > 1) U is copied to the handle's workspace and the result copied back.  Both forms
+ * give the same bits as fr3d_invert. */
 int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_invert_opts* opts,
                      void* out_host, void* stream);
 
