@@ -122,6 +122,15 @@ struct Handle {
   bool synced = false;
 };
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialisation may start
+// while the kernel before it in the stream is still running: before pdl_wait() it may read only data
+// that no kernel of the current call writes; pdl_wait() returns once that kernel has completed and its
+// writes are visible (at once for an ordinary launch).  pdl_release() lets this kernel's programmatic
+// successor start; a successor starts only after every block of this kernel has released it (or
+// exited), so all of this kernel's blocks are resident by then.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // launch-count bookkeeping (host)
 struct Launches {
   int n = 0;

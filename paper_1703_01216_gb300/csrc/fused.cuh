@@ -39,10 +39,6 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 
-// Programmatic dependent launch: wait until the kernel this one depends on has completed and its
-// writes are visible (returns at once when the launch was not programmatic).
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-
 // CL: CTAs per cluster (above 8 a non-portable cluster size), NT: threads, RB: rows per row batch,
 // MINB: resident CTAs per SM that the register budget is sized for; GACC: accumulate xi in the output
 // array (L2-resident read-modify-write) instead of shared memory
@@ -154,7 +150,7 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   for (int e = tid; e < N; e += NT) tws[e] = __ldg(a.tw_n + e);
   build_passtw<N, 1, NT>(ptc, a.tw_n, tid);
   build_passtw<L, 2, NT>(ptr, a.tw_n, tid);
-  grid_dependency_wait();
+  pdl_wait();
   __shared__ int s_aidx[FR3D_MAX_BANDS];
   if (tid < a.nb) s_aidx[tid] = min(max(a.aidx[tid], 0), a.na - 1);   // a caller-given index stays in the table
   __syncthreads();

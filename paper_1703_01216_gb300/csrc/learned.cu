@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kLearnedThreads) k_learned_alpha(
   if (!last) return;
   __threadfence();
   // every other block has finished: let a programmatically launched successor start its set-up
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  pdl_release();
   {
     // the partials of blocks tid and tid + 256 (the grid has at most 2 * 256 blocks), all loads in flight
     float v0[FR3D_MAX_BANDS], v1[FR3D_MAX_BANDS];

@@ -376,7 +376,7 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
   if (!last) return;
   __threadfence();
   // every other block has finished: let a programmatically launched successor start its set-up
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  pdl_release();
   // the last block: r^2 per (band, candidate) over the cluster partials (8 loads in flight per round)
   const int ncl = nblk / kAlphaCluster;
   for (int o = tid; o < O; o += 256) {

@@ -44,11 +44,12 @@ def _host_buffers(shape, pinned, misalign):
     return base[1:].view(shape) if misalign else base[:size].view(shape)
 
 
-@pytest.mark.parametrize("n,mp,q", [(64, 5, 3), (256, 3, 2), (512, 2, 1)])
+# (128, 150, 2) and (256, 70, 2) run the fused inverse in several waves of resident clusters
+@pytest.mark.parametrize("n,mp,q", [(64, 5, 3), (256, 3, 2), (512, 2, 1), (128, 150, 2), (256, 70, 2)])
 @pytest.mark.parametrize("output", ["xi", "zeta"])
 def test_host_forms_match_device_bits(F, n, mp, q, output):
     F.autotune_mode(1)
-    w, H, U, delta = _problem(F, n, mp, q, seed=700 + n)
+    w, H, U, delta = _problem(F, n, mp, q, seed=700 + n + mp)
     kind = F.OUT_XI if output == "xi" else F.OUT_ZETA
     shape = (mp, n, n) if output == "xi" else (q, mp, n, n)
     idx = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -71,6 +72,19 @@ def test_host_forms_match_device_bits(F, n, mp, q, output):
                     output=output)[output]
     got = ref.double().numpy()
     assert np.linalg.norm(got - want) <= 1e-4 * np.linalg.norm(want)
+
+
+def test_host_result_in_fp64(F):
+    """FP64 (whole copies through the workspace): the device entry point's bits."""
+    w, H, U, delta = _problem(F, 64, 9, 2, seed=91)
+    opts = F.Opts(alpha=1e-3, points=w.sources, precision=F.PREC_FP64)
+    od = torch.empty((9, 64, 64), dtype=torch.float64, device="cuda")
+    F.invert(H, torch.as_tensor(U, dtype=torch.float64, device="cuda"), 2, od, opts)
+    torch.cuda.synchronize()
+    uh = torch.as_tensor(U, dtype=torch.float64).pin_memory()
+    oh = torch.full((9, 64, 64), float("nan"), dtype=torch.float64).pin_memory()
+    F.invert_host(H, uh, 2, oh, opts)
+    assert torch.equal(oh, od.cpu())
 
 
 def test_tuner_keeps_write_once_variants_for_mapped_output(F):
