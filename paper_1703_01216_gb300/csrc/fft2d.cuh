@@ -223,12 +223,25 @@ __device__ __forceinline__ float v0_at(const Src32& s, int q, float x, float y, 
   }
   return s.coef * acc;
 }
+// 1 / sqrt(r2) in FP64 by Newton-Raphson for the reciprocal square root, y <- y (3 - r2 y^2) / 2, from
+// the single-precision estimate: each step squares the relative error (about 1e-7 -> 1e-14 -> below
+// the FP64 rounding), so two steps reach FP64 accuracy with a few FMAs instead of an FP64 square root
+// and division.  Arguments outside the single-precision range take the direct form.
+__device__ __forceinline__ double rsqrt_fp64(double r2) {
+  if (!(r2 > 1e-30 && r2 < 1e30)) return 1.0 / sqrt(r2);
+  double y = (double)rsqrtf((float)r2);
+  const double h = 0.5 * r2;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
 __device__ __forceinline__ double v0_at(const Src64& s, int q, double x, double y, double z) {
   double acc = 0.0;
   const double* p = s.pts + 3 * q * s.L;
   for (int l = 0; l < s.L; ++l) {
     const double dx = x - __ldg(p + 3 * l), dy = y - __ldg(p + 3 * l + 1), dz = z - __ldg(p + 3 * l + 2);
-    acc += 1.0 / sqrt(fma(dx, dx, fma(dy, dy, dz * dz)));
+    acc += rsqrt_fp64(fma(dx, dx, fma(dy, dy, dz * dz)));
   }
   return s.coef * acc;
 }

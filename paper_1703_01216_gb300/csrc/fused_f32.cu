@@ -9,8 +9,23 @@
 
 namespace fr3d {
 
-// W_q = V0_q / sum_q' V0_q'^2 on the R grid (Algorithm 1 step 4 for several source parameters),
-// in FP64, stored as FP32; depends only on the geometry and the sources
+// W_q = V0_q / sum_q' V0_q'^2 on the R grid (Algorithm 1 step 4 for several source parameters), stored
+// as FP32 for the FP32 fused inverse; depends only on the geometry and the sources.  With
+// V0_q = coef a_q, a_q = sum_l 1/|x - x_l|: W_q = a_q / (coef sum_q' a_q'^2).  The coordinate
+// differences are taken in FP64 (no cancellation near a source), a_q and the sum of squares in FP32
+// (relative error ~1e-7, the order of the table's own FP32 rounding), the scale 1/(coef sum) once per
+// voxel in FP64 (any A0).
+__device__ __forceinline__ float a_w(const Src64& s, int q, double x, double y, double z) {
+  float acc = 0.f;
+  const double* p = s.pts + 3 * q * s.L;
+  for (int l = 0; l < s.L; ++l) {
+    const float dx = (float)(x - __ldg(p + 3 * l)), dy = (float)(y - __ldg(p + 3 * l + 1)),
+                dz = (float)(z - __ldg(p + 3 * l + 2));
+    acc += rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  }
+  return acc;
+}
+
 __global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, double x0, double y0, double h,
                        const double* __restrict__ zr) {
   const long plane = (long)n * n, total = (long)Mp * plane;
@@ -18,16 +33,20 @@ __global__ void k_wtab(float* __restrict__ W, int Q, int Mp, int n, Src64 src, d
     const int j = (int)(idx / plane);
     const long pix = idx % plane;
     const double x = x0 + ((double)(pix % n) + 0.5) * h, y = y0 + ((double)(pix / n) + 0.5) * h;
-    double s = 0.0;
+    // every a_q once (the first kWtabKeep kept for the second loop, the rest evaluated again)
+    constexpr int kWtabKeep = 16;
+    float keep[kWtabKeep];
+    float s = 0.f;
     for (int q = 0; q < Q; ++q) {
-      const double v = v0_at(src, q, x, y, zr[j]);
-      s += v * v;
+      const float a = a_w(src, q, x, y, zr[j]);
+      if (q < kWtabKeep) keep[q] = a;
+      s = fmaf(a, a, s);
     }
-    for (int q = 0; q < Q; ++q) W[(long)q * total + idx] = (float)(v0_at(src, q, x, y, zr[j]) / s);
+    const double scale = 1.0 / (src.coef * (double)s);
+    for (int q = 0; q < Q; ++q)
+      W[(long)q * total + idx] = (float)((double)(q < kWtabKeep ? keep[q] : a_w(src, q, x, y, zr[j])) * scale);
   }
 }
-
-static_assert(sizeof(Handle::fused_tune_ms) / sizeof(float) >= kFusedVariants, "one tuning time per variant");
 
 namespace {
 
