@@ -236,6 +236,7 @@ __device__ __forceinline__ double sq_abs(double2 v) { return fma(v.x, v.x, v.y *
 constexpr int kAlphaCPB = 64;  // classes per block
 constexpr int kAlphaSplit = 4; // threads per class in the power gather
 constexpr int kAlphaCluster = 8; // blocks per cluster (the grid is padded to a multiple)
+static_assert(256 / kAlphaSplit >= kAlphaCPB, "every class of a block has its gather threads");
 
 // Per band b of frequency classes (one band: the whole spectrum),
 //   r_b^2(alpha_k) = n^-2 sum_{c in b} Ft[c][k] P[c]  (Parseval; M = 1 closed form of the residual),
@@ -283,8 +284,9 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
   if (tid < FR3D_MAX_BANDS) present[tid] = 0;
   // one round of global loads: this thread's share of the class powers and of the filter slab
   const int cl = tid / kAlphaSplit, sub = tid % kAlphaSplit, c = c0 + cl;
+  const bool own = cl < kAlphaCPB;            // threads past the block's classes gather nothing
   int kxs[4] = {0, 0, 0, 0}, kys[4] = {0, 0, 0, 0}, nm = 0;
-  if (c < Cn) {
+  if (own && c < Cn) {
     int p, q;
     class_pq(c, p, q);
     // members (kx, ky) of the class in the half spectrum
@@ -326,7 +328,7 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
   }
   // slabs longer than 16 loads per thread (more than 64 candidates) finish here
   for (int e = tid + 16 * 256; e < nF; e += 256) sF[e] = __ldg(slab + e);
-  if (sub == 0) {
+  if (sub == 0 && own) {
     sP[cl] = (double)acc;
     const int b = (c < Cn && nb > 1) ? (int)cband[c] : 0;
     sB[cl] = (unsigned char)b;
