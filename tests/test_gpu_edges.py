@@ -1,0 +1,151 @@
+"""Edge cases of the inversion against the FP64 oracle: the largest candidate list and band count the
+ABI accepts (and one more, rejected), a single candidate, a single unknown depth, the largest source
+point set (and one more, rejected), and zero data (exactly zero result, every candidate admissible).
+
+Tolerances as in test_gpu_parity.py: residual curves 1e-5 per candidate, reconstruction 1e-4 at the
+chosen alpha (FP32)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1703_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1703_01216_gb300 import build, fr3d
+    assert torch.cuda.is_available()
+    build.build()
+    fr3d.load()
+    return fr3d
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def _problem(n, mp, q, seed, n_alpha=16, points=None):
+    w = I.make_workload(n, mp, q=q, n_incl=2, noise_level=0.02, n_alpha=n_alpha, seed=seed)
+    src = w.sources if points is None else points
+    zeta = O.zeta_from_xi(w.xi_true, src, n, w.x0, w.h, w.zr)
+    U = O.forward_dft(zeta, n, w.h, w.zy, w.zr, w.nu)
+    nz = w.noise * (w.noise_level * np.linalg.norm(U) / np.linalg.norm(w.noise))
+    return w, src, U + nz, float(np.linalg.norm(nz))
+
+
+def _choice_ok(got, want, r2, thr2):
+    """Same index, or every candidate between the two lies within 1e-4 of the bound (FP32 vs FP64
+    residuals may then fall on either side)."""
+    if got == want:
+        return True
+    lo, hi = min(got, want), max(got, want)
+    return bool(np.all(np.abs(r2[lo:hi + 1] - thr2) <= 1e-4 * thr2))
+
+
+def test_largest_candidate_list_and_one_more(F):
+    w, src, U, delta = _problem(32, 4, 1, seed=301, n_alpha=F.MAX_ALPHAS)
+    alphas = np.logspace(-8, -1, F.MAX_ALPHAS)
+    ref = O.invert(U, 32, w.x0, w.h, w.zy, w.zr, w.nu, alphas=alphas, delta=delta, tau=1.1, sources=src)
+    H = F.kernel_transform(32, w.x0, w.h, w.zr, w.zy, w.nu)
+    idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    res = torch.zeros(alphas.size, dtype=torch.float64, device="cuda")
+    xi = torch.empty((4, 32, 32), device="cuda")
+    F.invert(H, dev(U), 1, xi, F.Opts(alphas=alphas, delta=delta, tau=1.1, points=src, alpha_idx=idx, residuals=res))
+    r = host(res)
+    assert np.max(np.abs(r - ref["res2"]) / ref["res2"]) <= 1e-5
+    k = int(idx.item())
+    assert _choice_ok(k, ref["alpha_index"], ref["res2"], (1.1 * delta) ** 2)
+    if k == ref["alpha_index"]:
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+    more = np.logspace(-8, -1, F.MAX_ALPHAS + 1)
+    with pytest.raises(F.Fr3dError):
+        F.invert(H, dev(U), 1, xi, F.Opts(alphas=more, delta=delta, tau=1.1, points=src))
+
+
+def test_largest_band_count_and_one_more(F):
+    nb = 16
+    w, src, U, delta = _problem(64, 5, 2, seed=302, n_alpha=24)
+    ref = O.invert(U, 64, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=delta, tau=1.1, sources=src,
+                   n_bands=nb)
+    H = F.kernel_transform(64, w.x0, w.h, w.zr, w.zy, w.nu)
+    idx = torch.zeros(nb, dtype=torch.int32, device="cuda")
+    res = torch.zeros((nb, w.alphas.size), dtype=torch.float64, device="cuda")
+    xi = torch.empty((5, 64, 64), device="cuda")
+    F.invert(H, dev(U), 2, xi, F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=src, alpha_idx=idx,
+                                      residuals=res, n_bands=nb))
+    r = host(res)
+    assert np.max(np.abs(r - ref["res2"]) / np.maximum(ref["res2"], 1e-300)) <= 1e-5
+    count = np.bincount(O.radial_bands(64, nb), minlength=nb)
+    got = [int(v) for v in idx.cpu().numpy()]
+    for b in range(nb):
+        thr2 = (1.1 * delta) ** 2 * count[b] / (64 * 64)
+        assert _choice_ok(got[b], ref["alpha_index"][b], ref["res2"][b], thr2), b
+    if got == list(ref["alpha_index"]):
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+    with pytest.raises(F.Fr3dError):
+        F.invert(H, dev(U), 2, xi, F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=src, n_bands=nb + 1))
+
+
+def test_single_candidate_and_single_depth(F):
+    w, src, U, delta = _problem(48, 1, 1, seed=303)
+    H = F.kernel_transform(48, w.x0, w.h, w.zr, w.zy, w.nu)
+    one = np.array([1e-3])
+    ref = O.invert(U, 48, w.x0, w.h, w.zy, w.zr, w.nu, alphas=one, delta=delta, tau=1.1, sources=src)
+    idx = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    xi = torch.empty((1, 48, 48), device="cuda")
+    F.invert(H, dev(U), 1, xi, F.Opts(alphas=one, delta=delta, tau=1.1, points=src, alpha_idx=idx, info=info))
+    assert int(idx.item()) == 0
+    # the one candidate either meets the bound (all satisfy) or not (none satisfies)
+    assert int(info.item()) in (F.INFO_ALPHA_ALL_SATISFY, F.INFO_ALPHA_NONE_SATISFIES)
+    assert rel(host(xi), ref["xi"]) <= 1e-4
+
+
+def test_largest_source_point_set_and_one_more(F):
+    q, L = 64, 4                                     # 256 points in all
+    rng = np.random.default_rng(304)
+    w0 = I.make_workload(32, 3, q=1, seed=304)
+    pts = np.empty((q, L, 3))
+    pts[:, :, :2] = rng.uniform(-1.0, 1.0, (q, L, 2))
+    pts[:, :, 2] = -0.1 - 0.01 * np.arange(q)[:, None]   # planes above the observation plane
+    w, src, U, delta = _problem(32, 3, q, seed=304, points=pts)
+    ref = O.invert(U, 32, w.x0, w.h, w.zy, w.zr, w.nu, alpha=1e-3, sources=src)
+    H = F.kernel_transform(32, w.x0, w.h, w.zr, w.zy, w.nu)
+    xi = torch.empty((3, 32, 32), device="cuda")
+    F.invert(H, dev(U), q, xi, F.Opts(alpha=1e-3, points=src))
+    assert rel(host(xi), ref["xi"]) <= 1e-4
+    more = np.concatenate([pts, pts[:, :1] + 0.003], axis=1)   # 64 x 5 = 320 points
+    with pytest.raises(F.Fr3dError):
+        F.invert(H, dev(U), q, xi, F.Opts(alpha=1e-3, points=more))
+    del w0
+
+
+def test_zero_data_gives_zero_and_every_candidate_admissible(F):
+    w, src, U, delta = _problem(64, 6, 3, seed=305)
+    H = F.kernel_transform(64, w.x0, w.h, w.zr, w.zy, w.nu)
+    idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    res = torch.full((w.alphas.size,), -1.0, dtype=torch.float64, device="cuda")
+    for output, shape in ((F.OUT_XI, (6, 64, 64)), (F.OUT_ZETA, (3, 6, 64, 64))):
+        out = torch.full(shape, float("nan"), device="cuda")
+        F.invert(H, torch.zeros((3, 1, 64, 64), device="cuda"), 3, out,
+                 F.Opts(alphas=w.alphas, delta=0.0, tau=1.1, output=output, points=src, alpha_idx=idx, info=info,
+                        residuals=res))
+        assert torch.count_nonzero(out).item() == 0 and not torch.isnan(out).any()
+        assert int(idx.item()) == w.alphas.size - 1 and int(info.item()) == F.INFO_ALPHA_ALL_SATISFY
+        assert np.all(host(res) == 0.0)
