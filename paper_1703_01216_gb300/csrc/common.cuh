@@ -92,9 +92,9 @@ struct Handle {
   int cband_nb = 0;
   std::vector<double> band_count; // grid frequencies per band (sum of the classes' member weights)
   unsigned char* bbin = nullptr;  // [n/2+1][n] radial band of every half-spectrum bin for cband_nb bands
-  // several observation depths (M > 1): per class the Gram eigenvalues, U^T and W = U^T A (multi.cu)
+  // several observation depths (M > 1): per class the Gram eigenvalues, eigenvectors U and W = U^T A (multi.cu)
   double* mlam = nullptr;      // [C][M]
-  float* mUt = nullptr;        // [C][M][M]
+  float* mUt = nullptr;        // [C][k][i]: the eigenvectors (component i along observation depth k)
   float* mW = nullptr;         // [C][M][M']
   int m_sweeps = 0;            // Jacobi sweeps the slowest class needed
   // right-hand side of Eq. (7): the handle of the box Pi's geometry (same grid, Pi's depths as the

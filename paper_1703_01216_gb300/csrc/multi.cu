@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_class_eig(const double* __restrict__ A6
   // W[i][j] = sum_k U[k][i] A[k][j]
   for (int i = tid; i < M; i += nt) lam[(long)c * M + i] = fmax(G[i * Me + i], 0.0);
   for (int e = tid; e < M * M; e += nt) {
-    const int i = e / M, k = e % M;
+    const int k = e / M, i = e % M;   // stored [k][i]: component i's eigenvector, contiguous over i
     Ut[(long)c * M * M + e] = (float)U[k * Me + i];
   }
   for (int e = tid; e < M * Mp; e += nt) {
@@ -155,24 +155,6 @@ __global__ void __launch_bounds__(256) k_class_eig(const double* __restrict__ A6
     W[(long)c * M * Mp + e] = (float)s;
   }
   if (tid == 0 && sweeps_out) atomicMax(sweeps_out, sweep);
-}
-
-// dst[e] = src(e) for e < count by the whole CTA, eight loads of a thread in flight at a time
-template <class Src>
-__device__ __forceinline__ void stage(float* dst, int count, Src src, int tid, int nt) {
-  for (int e0 = tid; e0 < count; e0 += 8 * nt) {
-    float v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * nt;
-      v[u] = e < count ? src(e) : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * nt;
-      if (e < count) dst[e] = v[u];
-    }
-  }
 }
 
 // members (kx, ky) of class c in the stored half spectrum and their weights (1 on the kx = 0 and
@@ -192,58 +174,79 @@ __device__ inline int class_members(int c, int n, int* kxs, int* kys, float* wts
 
 // Projection p = U_c^T U~ in place for every member bin and plane set q, and the class powers
 // P_ci = sum over members and q of wt |p_i|^2 (FP32 terms in a fixed order, stored in FP64).
-// One CTA per class; Uh planes are [q][i] (plane q M + i).
-__global__ void __launch_bounds__(256) k_project(float2* __restrict__ Uh, long ps, int Q, int M, int n,
+// Uh planes are [q][i] (plane q M + i).  One warp per class: the class's member values of a plane set
+// are gathered into the warp's shared-memory slice, lane l owns components i = l, l + 32, and the
+// eigenvector table (stored [k][i]) streams from global memory in coalesced rows, each element
+// feeding every member.  Classes own disjoint bins, so the in-place writes never meet another
+// class's reads.
+constexpr int kPerCta = 8;                      // warps (classes) per CTA
+constexpr int kRows = (kMaxM + 31) / 32;        // components (or depths) per lane
+__global__ void __launch_bounds__(256) k_project(float2* __restrict__ Uh, long ps, int Q, int M, int n, int Cn,
                                                  const float* __restrict__ Ut, double* __restrict__ Pc) {
-  __shared__ float ut[kMaxM * kMaxM];
-  __shared__ float2 x[4 * kMaxM], y[4 * kMaxM];
-  __shared__ float pw[kMaxM];
-  __shared__ int kxs[4], kys[4];
-  __shared__ float wts[4];
-  __shared__ int nm_s;
-  const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    int kx[4], ky[4];
-    float wt[4];
-    const int nm = class_members(c, n, kx, ky, wt);
-    for (int m = 0; m < nm; ++m) {
-      kxs[m] = kx[m];
-      kys[m] = ky[m];
-      wts[m] = wt[m];
-    }
-    nm_s = nm;
-  }
-  const float* utc = Ut + (long)c * M * M;
-  stage(ut, M * M, [&](int e) { return __ldg(utc + e); }, tid, nt);
-  for (int i = tid; i < M; i += nt) pw[i] = 0.f;
-  __syncthreads();
-  const int nm = nm_s;
+  __shared__ float2 xs[kPerCta][4 * kMaxM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kPerCta + warp;
+  if (c >= Cn) return;   // a whole warp; the kernel synchronises warps only
+  int kxs[4], kys[4];
+  float wts[4];
+  const int nm = class_members(c, n, kxs, kys, wts);
+  long bin[4];
+  for (int m = 0; m < 4; ++m) bin[m] = m < nm ? (long)kxs[m] * n + kys[m] : 0;
+  float2* x = xs[warp];
+  const float* Uc = Ut + (long)c * M * M;
+  float pw[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) pw[r] = 0.f;
   for (int q = 0; q < Q; ++q) {
-    for (int e = tid; e < nm * M; e += nt) {
-      const int m = e / M, k = e % M;
-      x[e] = Uh[((long)q * M + k) * ps + (long)kxs[m] * n + kys[m]];
+    for (int e = lane; e < nm * M; e += 32) {
+      const int m = e / M, k = e - m * M;
+      x[e] = Uh[((long)q * M + k) * ps + bin[m]];
     }
-    __syncthreads();
-    for (int e = tid; e < nm * M; e += nt) {
-      const int m = e / M, i = e % M;
-      float2 s = make_float2(0.f, 0.f);
-      for (int k = 0; k < M; ++k) {
-        const float u = ut[i * M + k];
-        s.x = fmaf(u, x[m * M + k].x, s.x);
-        s.y = fmaf(u, x[m * M + k].y, s.y);
+    __syncwarp();
+    float2 y[kRows][4];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) y[r][m] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int k = 0; k < M; ++k) {
+      float u[kRows];
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const int i = lane + 32 * r;
+        u[r] = i < M ? __ldg(Uc + (long)k * M + i) : 0.f;
       }
-      y[e] = s;
-      Uh[((long)q * M + i) * ps + (long)kxs[m] * n + kys[m]] = s;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (m < nm) {
+          const float2 xv = x[m * M + k];
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) {
+            y[r][m].x = fmaf(u[r], xv.x, y[r][m].x);
+            y[r][m].y = fmaf(u[r], xv.y, y[r][m].y);
+          }
+        }
+      }
     }
-    __syncthreads();
-    for (int i = tid; i < M; i += nt) {
-      float s = pw[i];
-      for (int m = 0; m < nm; ++m) s = fmaf(wts[m], y[m * M + i].x * y[m * M + i].x + y[m * M + i].y * y[m * M + i].y, s);
-      pw[i] = s;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int i = lane + 32 * r;
+      if (i < M) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (m < nm) {
+            Uh[((long)q * M + i) * ps + bin[m]] = y[r][m];
+            pw[r] = fmaf(wts[m], y[r][m].x * y[r][m].x + y[r][m].y * y[r][m].y, pw[r]);
+          }
+      }
     }
-    __syncthreads();
+    __syncwarp();   // the x reads are done before the next plane set is gathered
   }
-  for (int i = tid; i < M; i += nt) Pc[(long)c * M + i] = (double)pw[i];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const int i = lane + 32 * r;
+    if (i < M) Pc[(long)c * M + i] = (double)pw[r];
+  }
 }
 
 struct MAlphas {
@@ -353,68 +356,85 @@ __global__ void __launch_bounds__(256) k_alpha_m_finish(const double* __restrict
 }
 
 // zeta~_j(bin, q) = sum_i W_c[i][j] g_i p_i(bin, q) / n^2 with g_i of the class's band alpha, written to
-// the spectra Zs [q][j][bin].  One CTA per class: W_c is staged in shared memory by depth chunks (all
-// loads of a thread in flight), the projected data of the members by chunks of source parameters, and
-// every thread computes outputs (q, member, j) with j fastest.
-constexpr int kSolveQC = 8;     // source parameters per chunk
-constexpr int kSolveWC = 4096;  // floats of W_c per depth chunk
+// the spectra Zs [q][j][bin].  One warp per class: the scaled projected data g_i p_i of the members
+// for one q sit in the warp's shared-memory slice, lane l owns depths j = j0 + l, j0 + l + 32 of a
+// 64-depth chunk, and W_c (stored [i][j]) streams from global memory in coalesced rows, each element
+// feeding every member.
 __global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, long ps, int Q, int M, int Mp, int n,
-                                                 const double* __restrict__ lam, const float* __restrict__ W,
+                                                 int Cn, const double* __restrict__ lam, const float* __restrict__ W,
                                                  const unsigned char* __restrict__ cband, int nb,
                                                  const int* __restrict__ aidx, int na, MAlphas al,
                                                  const double* __restrict__ s2, int ra, double inv_n2,
                                                  float2* __restrict__ Zs) {
-  __shared__ float Ws[kSolveWC];
-  __shared__ float2 x[kSolveQC * 4 * kMaxM];
-  __shared__ float g[kMaxM];
-  __shared__ long ob[4];
-  __shared__ int nm_s;
-  const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    int kx[4], ky[4];
-    float wt[4];
-    const int nm = class_members(c, n, kx, ky, wt);
-    for (int m = 0; m < nm; ++m) ob[m] = (long)kx[m] * n + ky[m];
-    nm_s = nm;
-  }
-  if (tid < M) {
+  constexpr int kJ = 2;   // depths per lane in a chunk of 64
+  __shared__ float2 xs[kPerCta][4 * kMaxM];
+  __shared__ float gs[kPerCta][kMaxM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kPerCta + warp;
+  if (c >= Cn) return;   // a whole warp; the kernel synchronises warps only
+  int kxs[4], kys[4];
+  float wts[4];
+  const int nm = class_members(c, n, kxs, kys, wts);
+  long bin[4];
+  for (int m = 0; m < 4; ++m) bin[m] = m < nm ? (long)kxs[m] * n + kys[m] : 0;
+  float2* x = xs[warp];
+  float* g = gs[warp];
+  {
     const int k = min(max(aidx[nb > 1 ? (int)cband[c] : 0], 0), na - 1);   // caller-given indices stay in range
     const double t = al.a[k] * (*s2);
-    const double l = lam[(long)c * M + tid];
-    double gi;
-    if (ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? 1.0 / l : 0.0;
-    else gi = 1.0 / (l + t);
-    g[tid] = (float)(gi * inv_n2);
-  }
-  __syncthreads();
-  const int nm = nm_s;
-  const float* Wc = W + (long)c * M * Mp;
-  const int JC = min(Mp, kSolveWC / M);
-  for (int j0 = 0; j0 < Mp; j0 += JC) {
-    const int jc = min(JC, Mp - j0);
-    stage(Ws, M * jc, [&](int e) { return __ldg(Wc + (long)(e / jc) * Mp + j0 + e % jc); }, tid, nt);
-    for (int q0 = 0; q0 < Q; q0 += kSolveQC) {
-      const int qc = min(kSolveQC, Q - q0);
-      for (int e = tid; e < qc * nm * M; e += nt) {
-        const int qq = e / (nm * M), m = (e / M) % nm, i = e % M;
-        const float2 v = P[((long)(q0 + qq) * M + i) * ps + ob[m]];
-        x[e] = make_float2(v.x * g[i], v.y * g[i]);
-      }
-      __syncthreads();
-      for (int o = tid; o < qc * nm * jc; o += nt) {
-        const int jj = o % jc, qm = o / jc;
-        const float2* xr = x + qm * M;
-        float2 z = make_float2(0.f, 0.f);
-        for (int i = 0; i < M; ++i) {
-          const float w = Ws[i * jc + jj];
-          z.x = fmaf(w, xr[i].x, z.x);
-          z.y = fmaf(w, xr[i].y, z.y);
-        }
-        const int qq = qm / nm, m = qm % nm;
-        Zs[((long)(q0 + qq) * Mp + j0 + jj) * ps + ob[m]] = z;
-      }
-      __syncthreads();
+    for (int i = lane; i < M; i += 32) {
+      const double l = lam[(long)c * M + i];
+      double gi;
+      if (ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? 1.0 / l : 0.0;
+      else gi = 1.0 / (l + t);
+      g[i] = (float)(gi * inv_n2);
     }
+  }
+  __syncwarp();
+  const float* Wc = W + (long)c * M * Mp;
+  for (int q = 0; q < Q; ++q) {
+    for (int e = lane; e < nm * M; e += 32) {
+      const int m = e / M, i = e - m * M;
+      const float2 v = P[((long)q * M + i) * ps + bin[m]];
+      x[e] = make_float2(v.x * g[i], v.y * g[i]);
+    }
+    __syncwarp();
+    for (int j0 = 0; j0 < Mp; j0 += 32 * kJ) {
+      float2 z[kJ][4];
+#pragma unroll
+      for (int t = 0; t < kJ; ++t)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) z[t][m] = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int i = 0; i < M; ++i) {
+        float w[kJ];
+#pragma unroll
+        for (int t = 0; t < kJ; ++t) {
+          const int jj = j0 + lane + 32 * t;
+          w[t] = jj < Mp ? __ldg(Wc + (long)i * Mp + jj) : 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          if (m < nm) {
+            const float2 xv = x[m * M + i];
+#pragma unroll
+            for (int t = 0; t < kJ; ++t) {
+              z[t][m].x = fmaf(w[t], xv.x, z[t][m].x);
+              z[t][m].y = fmaf(w[t], xv.y, z[t][m].y);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kJ; ++t) {
+        const int jj = j0 + lane + 32 * t;
+        if (jj < Mp)
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            if (m < nm) Zs[((long)q * Mp + jj) * ps + bin[m]] = z[t][m];
+      }
+    }
+    __syncwarp();   // the x reads are done before the next q is gathered
   }
 }
 
@@ -494,7 +514,7 @@ int multi_data(Handle* H, const float* U, int Q, const MultiWs& w, int* launches
   prof_mark(H, kStRowR2C, st);
   FR3D_TRY(Ops<float>::col_plain(H, w.Uh, w.Uh, Q * H->M, false, st));
   prof_mark(H, kStColFwd, st);
-  k_project<<<H->C, 256, 0, st>>>(w.Uh, ps, Q, H->M, H->n, H->mUt, w.Pc);
+  k_project<<<(H->C + kPerCta - 1) / kPerCta, 32 * kPerCta, 0, st>>>(w.Uh, ps, Q, H->M, H->n, H->C, H->mUt, w.Pc);
   FR3D_CUDA_TRY(cudaGetLastError());
   prof_mark(H, kStOther, st);
   *launches += 3;
@@ -554,8 +574,9 @@ int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, fl
   }
   const long ps = (long)(H->n / 2 + 1) * H->n;
   const int na = o->alpha_mode == FR3D_ALPHA_FIXED ? 1 : o->n_alpha;
-  k_solve_m<<<H->C, 256, 0, st>>>(w.Uh, ps, Q, H->M, H->Mp, H->n, H->mlam, H->mW, H->cband, nb, aidx, na, al, H->s2,
-                                  o->ra, 1.0 / ((double)H->n * H->n), w.Zs);
+  k_solve_m<<<(H->C + kPerCta - 1) / kPerCta, 32 * kPerCta, 0, st>>>(
+      w.Uh, ps, Q, H->M, H->Mp, H->n, H->C, H->mlam, H->mW, H->cband, nb, aidx, na, al, H->s2, o->ra,
+      1.0 / ((double)H->n * H->n), w.Zs);
   FR3D_CUDA_TRY(cudaGetLastError());
   prof_mark(H, kStColSolve, st);
   FR3D_TRY(inv_fused_presolved_f32(H, w.Zs, H->wtab, out, Q, o->output, st));
