@@ -181,6 +181,7 @@ __device__ inline int class_members(int c, int n, int* kxs, int* kys, float* wts
 // class's reads.
 constexpr int kPerCta = 8;                      // warps (classes) per CTA
 constexpr int kRows = (kMaxM + 31) / 32;        // components (or depths) per lane
+constexpr int kBatch = 4;                       // table rows per batch of the double-buffered stream
 __global__ void __launch_bounds__(256) k_project(float2* __restrict__ Uh, long ps, int Q, int M, int n, int Cn,
                                                  const float* __restrict__ Ut, double* __restrict__ Pc) {
   __shared__ float2 xs[kPerCta][4 * kMaxM];
@@ -197,7 +198,19 @@ __global__ void __launch_bounds__(256) k_project(float2* __restrict__ Uh, long p
   float pw[kRows];
 #pragma unroll
   for (int r = 0; r < kRows; ++r) pw[r] = 0.f;
+  // table rows k0 .. k0 + kBatch - 1 into buffer b (zeros past M); the arithmetic of a batch in k order
+  float ub[2][kBatch][kRows];
+  auto load = [&](int b, int k0) {
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const int k = k0 + j, i = lane + 32 * r;
+        ub[b][j][r] = (k < M && i < M) ? __ldg(Uc + (long)k * M + i) : 0.f;
+      }
+  };
   for (int q = 0; q < Q; ++q) {
+    load(0, 0);   // the first batch is in flight during the gather
     for (int e = lane; e < nm * M; e += 32) {
       const int m = e / M, k = e - m * M;
       x[e] = Uh[((long)q * M + k) * ps + bin[m]];
@@ -208,25 +221,31 @@ __global__ void __launch_bounds__(256) k_project(float2* __restrict__ Uh, long p
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
       for (int m = 0; m < 4; ++m) y[r][m] = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int k = 0; k < M; ++k) {
-      float u[kRows];
+    auto fma_batch = [&](int b, int k0) {
 #pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const int i = lane + 32 * r;
-        u[r] = i < M ? __ldg(Uc + (long)k * M + i) : 0.f;
-      }
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j;
+        if (k < M) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if (m < nm) {
-          const float2 xv = x[m * M + k];
+          for (int m = 0; m < 4; ++m) {
+            if (m < nm) {
+              const float2 xv = x[m * M + k];
 #pragma unroll
-          for (int r = 0; r < kRows; ++r) {
-            y[r][m].x = fmaf(u[r], xv.x, y[r][m].x);
-            y[r][m].y = fmaf(u[r], xv.y, y[r][m].y);
+              for (int r = 0; r < kRows; ++r) {
+                y[r][m].x = fmaf(ub[b][j][r], xv.x, y[r][m].x);
+                y[r][m].y = fmaf(ub[b][j][r], xv.y, y[r][m].y);
+              }
+            }
           }
         }
       }
+    };
+    // double-buffered stream: the next batch is requested before the current one is used
+    for (int k0 = 0; k0 < M; k0 += 2 * kBatch) {
+      load(1, k0 + kBatch);
+      fma_batch(0, k0);
+      load(0, k0 + 2 * kBatch);
+      fma_batch(1, k0 + kBatch);
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
@@ -400,30 +419,48 @@ __global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, l
     }
     __syncwarp();
     for (int j0 = 0; j0 < Mp; j0 += 32 * kJ) {
+      // rows i0 .. i0 + kBatch - 1 of this depth chunk into buffer b (zeros past M or M')
+      float wb[2][kBatch][kJ];
+      auto load = [&](int b, int i0) {
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+#pragma unroll
+          for (int t = 0; t < kJ; ++t) {
+            const int i = i0 + u, jj = j0 + lane + 32 * t;
+            wb[b][u][t] = (i < M && jj < Mp) ? __ldg(Wc + (long)i * Mp + jj) : 0.f;
+          }
+      };
       float2 z[kJ][4];
 #pragma unroll
       for (int t = 0; t < kJ; ++t)
 #pragma unroll
         for (int m = 0; m < 4; ++m) z[t][m] = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int i = 0; i < M; ++i) {
-        float w[kJ];
+      auto fma_batch = [&](int b, int i0) {
 #pragma unroll
-        for (int t = 0; t < kJ; ++t) {
-          const int jj = j0 + lane + 32 * t;
-          w[t] = jj < Mp ? __ldg(Wc + (long)i * Mp + jj) : 0.f;
-        }
+        for (int u = 0; u < kBatch; ++u) {
+          const int i = i0 + u;
+          if (i < M) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          if (m < nm) {
-            const float2 xv = x[m * M + i];
+            for (int m = 0; m < 4; ++m) {
+              if (m < nm) {
+                const float2 xv = x[m * M + i];
 #pragma unroll
-            for (int t = 0; t < kJ; ++t) {
-              z[t][m].x = fmaf(w[t], xv.x, z[t][m].x);
-              z[t][m].y = fmaf(w[t], xv.y, z[t][m].y);
+                for (int t = 0; t < kJ; ++t) {
+                  z[t][m].x = fmaf(wb[b][u][t], xv.x, z[t][m].x);
+                  z[t][m].y = fmaf(wb[b][u][t], xv.y, z[t][m].y);
+                }
+              }
             }
           }
         }
+      };
+      // double-buffered stream: the next batch is requested before the current one is used
+      load(0, 0);
+      for (int i0 = 0; i0 < M; i0 += 2 * kBatch) {
+        load(1, i0 + kBatch);
+        fma_batch(0, i0);
+        load(0, i0 + 2 * kBatch);
+        fma_batch(1, i0 + kBatch);
       }
 #pragma unroll
       for (int t = 0; t < kJ; ++t) {
