@@ -125,21 +125,34 @@ def whole_job_rate(units_per_rank: float, world: int, steps: int, seconds: float
     return units_per_rank * world * steps / seconds
 
 
-def kernel_source_hash():
+# the sources each profiled kernel is built and launched from: a row of profiles/traffic.md stays valid
+# while these files are unchanged
+STAGE_SOURCES = {
+    "inv_fused": ("common.cuh", "fft_engine.cuh", "fft2d.cuh", "fused.cuh", "fused_f32.cu", "fused_v0.cu", "ops.cuh",
+                  "fused_v1.cu", "fused_v2.cu", "fused_v3.cu"),
+    "alpha": ("common.cuh", "fft_engine.cuh", "fft2d.cuh", "ops.cuh", "ops_impl.cuh", "ops_f32.cu"),
+}
+
+
+def kernel_source_hash(stage: str = None):
+    """Hash of the kernel sources of `stage` (every file under csrc when the stage has no list)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1703_01216_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    files = STAGE_SOURCES.get(stage) or sorted(os.listdir(csrc))
+    for f in files:
+        h.update(f.encode())
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(stage: str):
-    """DRAM bytes per launch of ``stage`` from the committed ncu summary, if it was taken on the
-    current kernel sources (profiles/traffic.md lines: `stage | source hash | bytes per launch | ...`)."""
+    """DRAM bytes per launch of ``stage`` (e.g. "inv_fused/v3") from the committed ncu summary, if it
+    was taken on the current sources of that kernel (profiles/traffic.md lines:
+    `stage | source hash | bytes per launch | ...`)."""
     p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(stage.split("/")[0])
     for line in open(p):
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
         if len(cells) >= 3 and cells[0] == stage and cells[1] == cur:
