@@ -401,12 +401,14 @@ __global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, l
   {
     const int k = min(max(aidx[nb > 1 ? (int)cband[c] : 0], 0), na - 1);   // caller-given indices stay in range
     const double t = al.a[k] * (*s2);
+    // the TSVD keep decision in FP64 (against the candidate's level), the reciprocal in FP32 (the
+    // weights multiply FP32 data and tables)
     for (int i = lane; i < M; i += 32) {
       const double l = lam[(long)c * M + i];
-      double gi;
-      if (ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? 1.0 / l : 0.0;
-      else gi = 1.0 / (l + t);
-      g[i] = (float)(gi * inv_n2);
+      float gi;
+      if (ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? __frcp_rn((float)l) : 0.f;
+      else gi = __frcp_rn((float)(l + t));
+      g[i] = gi * (float)inv_n2;
     }
   }
   __syncwarp();
