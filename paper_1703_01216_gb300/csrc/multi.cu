@@ -280,10 +280,10 @@ __device__ inline float resid_weight(float lam, float t, int ra) {
 }
 
 constexpr int kMCPB = 64;   // classes per block of the residual sums
-constexpr int kMThreads = 256;
+constexpr int kMThreads = 1024;   // threads of the residual-sum blocks
 
 // Block partials of r_b^2(alpha_k) * n^2 = sum_{c in b} sum_i F(lambda_ci, alpha_k) P_ci: the sum over
-// i in FP32 (M terms), over classes in FP64; S = 256 / n_alpha threads per candidate take every S-th
+// i in FP32 (M terms), over classes in FP64; S = kMThreads / n_alpha threads per candidate take every S-th
 // class, their sums are added in a fixed order.
 __global__ void __launch_bounds__(kMThreads) k_alpha_m_partial(
     const double* __restrict__ lam, const double* __restrict__ Pc, int M, int Cn,
