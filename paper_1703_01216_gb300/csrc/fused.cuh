@@ -123,7 +123,7 @@ template <int N, int MODE, int V, bool PRE = false>
 __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
   using G = FusedGeom<N, V>;
   constexpr int CL = G::CL, NT = G::NT, RB = G::RB, L = G::L;
-  constexpr int CPC = G::CPC, NRW = G::NRW, NB = G::NB, SSC = G::SSC, SSR = G::SSR, EPT = G::EPT;
+  constexpr int CPC = G::CPC, NRW = G::NRW, NB = G::NB, SSC = G::SSC, SSR = G::SSR;
   constexpr int CLD = CPC * N / NT;           // column elements per thread
   constexpr int CB = divisor_at_most(CLD, 8);  // loads in flight per batch
   static_assert(CLD % CB == 0, "load batches");
