@@ -534,22 +534,24 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
     return res
 
 
-def bench_paper_geometry(args, dev, flush, n=256, m=51, mp=51, n_alpha=32):
-    """The paper's own experiment shape (Sec. 6: M = M' = 51 observation and unknown depths), here at
-    n = 256 on the periodic box, one source, 10 inclusions, 1 % noise: truncated SVD (the paper's best
-    regularising algorithm) and Tikhonov, alpha by the discrepancy principle; one graph replay per step,
-    L2 flushed before each.  Cold = kernel transform + the per-class eigen tables of the first call."""
+def bench_paper_geometry(args, dev, flush, n=512, m=51, mp=51, n_alpha=32):
+    """The paper's own experiment (Sec. 6) in its coordinates: R = [-10, 10]^2 x [1, 2] with M' = 51
+    depths, Y = [-10, 10]^2 x [6, 7] with M = 51 planes, its ten point sources and model solution, at
+    its timing example's n = 512 on the periodic box, 1e-4 relative noise: truncated SVD (the paper's
+    best regularising algorithm) and Tikhonov, alpha by the discrepancy principle; one graph replay per
+    step, L2 flushed before each.  Cold = kernel transform + the per-class eigen tables of the first
+    call."""
     import torch
     from paper_1703_01216_gb300 import fr3d
     from paper_1703_01216_gb300 import inputs as I
-    w = I.make_workload(n, mp, q=1, m_obs=m, n_incl=10, kinds=("gauss", "ellipsoid"), noise_level=0.01,
-                        n_alpha=n_alpha, seed=6000)
+    w = I.paper_workload(n, m, mp, n_alpha=n_alpha)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     H, U, delta = setup_gpu(w, dev)
     out = torch.empty((mp, n, n), device=dev)
     xi_true = torch.tensor(w.xi_true, device=dev)
-    res = {"workload": f"{n}^2 x {mp} unknown depths, {m} observation depths, 1 source, {n_alpha} alphas",
+    res = {"workload": (f"{n}^2 x {mp} unknown depths, {m} observation depths, the paper's ten point sources "
+                        f"and model solution (Sec. 6), {n_alpha} alphas"),
            "voxels": n * n * mp}
     st = torch.cuda.current_stream(dev)
     for name, ra in (("tsvd", fr3d.RA_TSVD), ("tikhonov", fr3d.RA_TIKHONOV)):

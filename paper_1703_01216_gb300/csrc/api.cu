@@ -163,9 +163,10 @@ InvertPlan plan_invert(const Handle* H, int Q, bool host_io, int output) {
   size_t off = align_up(ps_b * Q * H->M);
   const size_t per_j = ps_b * Q;
   const bool fused = sizeof(T) == 4 && fused_supported(n);
+  const bool multi = sizeof(T) == 4 && H->M > 1;      // the M > 1 path lays out its own workspace first
   int chunk = fused ? 0 : (int)std::max<size_t>(1, std::min<size_t>(H->Mp, kChunkBytes / per_j));
-  if (fused && H->M > 1) off = multi_ws_bytes(H, Q);   // the M > 1 path lays out its own workspace first
-  if (fused) {
+  if (multi) off = multi_ws_bytes(H, Q);
+  if (fused || multi) {
     p.chunk = H->Mp;
     p.t_off = off;
     p.uin_off = p.out_off = 0;
@@ -199,8 +200,8 @@ int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
   if (!valid_precision(o->precision)) return FR3D_ERR_INVALID_ARG;
   if (H->M > FR3D_MAX_OBS_DEPTHS) return FR3D_ERR_UNSUPPORTED_SIZE;
   if (H->M > 1) {
-    // several observation depths: FP32 path with the fused inverse (eigen tables, multi.cu)
-    if (o->precision != FR3D_PREC_FP32 || !fused_supported(H->n)) return FR3D_ERR_UNSUPPORTED_SIZE;
+    // several observation depths: FP32 path (eigen tables, multi.cu)
+    if (o->precision != FR3D_PREC_FP32) return FR3D_ERR_UNSUPPORTED_SIZE;
     if (o->alpha_mode == FR3D_ALPHA_LEARNED) return FR3D_ERR_INVALID_ARG;
   }
   if (o->output != FR3D_OUT_XI && o->output != FR3D_OUT_ZETA) return FR3D_ERR_INVALID_ARG;
@@ -237,8 +238,9 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
   using C = typename Ops<T>::C;
   if constexpr (sizeof(T) == 4) {
     if (H->M > 1) {
-      if (o->output == FR3D_OUT_XI) FR3D_TRY(ensure_wtab(H, o->sources, st));
-      return invert_multi(H, U, Q, o, out, st);
+      if (o->output == FR3D_OUT_XI && fused_supported(H->n)) FR3D_TRY(ensure_wtab(H, o->sources, st));
+      const SrcHost src = o->output == FR3D_OUT_XI ? src_host(H, FR3D_PREC_FP32, o->sources) : SrcHost{};
+      return invert_multi(H, U, Q, o, out, src, st);
     }
   }
   C* Uh = reinterpret_cast<C*>((char*)H->ws + p.uh_off);

@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(256) k_alpha_m_finish(const double* __restrict
 }
 
 // zeta~_j(bin, q) = sum_i W_c[i][j] g_i p_i(bin, q) / n^2 with g_i of the class's band alpha, written to
-// the spectra Zs [q][j][bin].  One warp per class: the scaled projected data g_i p_i of the members
+// the spectra Zs [q][j][bin] (jq = 0: the fused inverse's order) or [j][q][bin] (jq = 1: the order of the
+// two-pass inverse).  One warp per class: the scaled projected data g_i p_i of the members
 // for one q sit in the warp's shared-memory slice, lane l owns depths j = j0 + l, j0 + l + 32 of a
 // 64-depth chunk, and W_c (stored [i][j]) streams from global memory in coalesced rows, each element
 // feeding every member.
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, l
                                                  const unsigned char* __restrict__ cband, int nb,
                                                  const int* __restrict__ aidx, int na, MAlphas al,
                                                  const double* __restrict__ s2, int ra, double inv_n2,
-                                                 float2* __restrict__ Zs) {
+                                                 float2* __restrict__ Zs, int jq) {
   constexpr int kJ = 2;   // depths per lane in a chunk of 64
   __shared__ float2 xs[kPerCta][4 * kMaxM];
   __shared__ float gs[kPerCta][kMaxM];
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(256) k_solve_m(const float2* __restrict__ P, l
         if (jj < Mp)
 #pragma unroll
           for (int m = 0; m < 4; ++m)
-            if (m < nm) Zs[((long)q * Mp + jj) * ps + bin[m]] = z[t][m];
+            if (m < nm) Zs[(jq ? (long)jj * Q + q : (long)q * Mp + jj) * ps + bin[m]] = z[t][m];
       }
     }
     __syncwarp();   // the x reads are done before the next q is gathered
@@ -580,7 +581,8 @@ int multi_alpha(Handle* H, const MultiWs& w, const double* alphas, int na, int r
 
 // Algorithm 1 for M > 1 (FP32 data and FFTs, FP64 eigen tables and residual sums).
 // The combination table (XI) is built by the caller.
-int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, float* out, cudaStream_t st) {
+int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, float* out, const SrcHost& src,
+                 cudaStream_t st) {
   FR3D_TRY(ensure_multi_tables(H, st));
   const int nb = o->n_bands > 1 ? o->n_bands : 1;
   std::vector<double> count;
@@ -613,14 +615,28 @@ int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, fl
   }
   const long ps = (long)(H->n / 2 + 1) * H->n;
   const int na = o->alpha_mode == FR3D_ALPHA_FIXED ? 1 : o->n_alpha;
+  const bool fused = fused_supported(H->n);
   k_solve_m<<<(H->C + kPerCta - 1) / kPerCta, 32 * kPerCta, 0, st>>>(
       w.Uh, ps, Q, H->M, H->Mp, H->n, H->C, H->mlam, H->mW, H->cband, nb, aidx, na, al, H->s2, o->ra,
-      1.0 / ((double)H->n * H->n), w.Zs);
+      1.0 / ((double)H->n * H->n), w.Zs, fused ? 0 : 1);
   FR3D_CUDA_TRY(cudaGetLastError());
   prof_mark(H, kStColSolve, st);
-  FR3D_TRY(inv_fused_presolved_f32(H, w.Zs, H->wtab, out, Q, o->output, st));
-  prof_mark(H, kStFused, st);
-  H->last_launches = launches + 2;
+  if (fused) {
+    FR3D_TRY(inv_fused_presolved_f32(H, w.Zs, H->wtab, out, Q, o->output, st));
+    prof_mark(H, kStFused, st);
+    H->last_launches = launches + 2;
+    return FR3D_OK;
+  }
+  // other sizes: the inverse column pass in place, then the row pass with the source combination (XI)
+  // or per source (ZETA); the solved spectra already carry 1/n^2
+  FR3D_TRY(Ops<float>::col_plain(H, w.Zs, w.Zs, Q * H->Mp, true, st));
+  prof_mark(H, kStColInv, st);
+  if (o->output == FR3D_OUT_XI)
+    FR3D_TRY(Ops<float>::row_c2r_xi(H, w.Zs, out, H->Mp, Q, 0, src, st));
+  else
+    FR3D_TRY(Ops<float>::row_c2r_plain(H, w.Zs, out, H->Mp * Q, Q, 0, H->Mp, st));
+  prof_mark(H, kStRowC2R, st);
+  H->last_launches = launches + 3;
   return FR3D_OK;
 }
 

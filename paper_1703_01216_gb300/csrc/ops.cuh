@@ -65,7 +65,9 @@ int learned_alpha(Handle* H, const float2* Uh, int nplanes, int nb, double delta
 // choice, and the workspace bytes the inversion lays out from the start of the handle's workspace
 int ensure_multi_tables(Handle* H, cudaStream_t st);
 size_t multi_ws_bytes(const Handle* H, int Q);
-int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, float* out, cudaStream_t st);
+// src: the point sources of the combination (XI output; used at sizes without the fused inverse)
+int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, float* out, const SrcHost& src,
+                 cudaStream_t st);
 int choose_multi(Handle* H, const float* U, int Q, const double* alphas, int na, double delta, double tau, int* aidx,
                  double* residuals, int* info, cudaStream_t st);
 void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double* thr2);

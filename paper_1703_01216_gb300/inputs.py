@@ -125,6 +125,47 @@ def make_workload(n: int, mp: int, *, q: int = 1, m_obs: int = 1, n_incl: int = 
                     noise=noise, noise_level=noise_level, alphas=alphas, seed=seed)
 
 
+def paper_model_xi(n: int, x0: float, h: float, zr) -> np.ndarray:
+    """The model solution of Sec. 6 on the voxel-centred grid, [M', n, n], with the readings of its
+    garbled terms: a2 and a3 take the depth z (printed with the source height z0, which would make a2
+    vanish), a3's exponent takes +(y + 4)^2 (printed with a minus, indefinite and growing in y), and
+    a3's envelope is max{1 - (z - 1.7)^2, 0}^2."""
+    c = x0 + (np.arange(n) + 0.5) * h
+    X = c[None, None, :]
+    Y = c[None, :, None]
+    Z = np.asarray(zr, np.float64)[:, None, None]
+    a1 = (1.0 - 4.0 * (Z - 1.5) ** 2) ** 2
+    a2 = 0.4 * np.maximum(1.0 - (Z - 1.3) ** 2, 0.0)
+    a3 = 0.2 * np.maximum(1.0 - (Z - 1.7) ** 2, 0.0) ** 2
+    return (a1 * np.exp(-X ** 2 - 2.0 * Y ** 2)
+            + a2 * np.exp(-3.0 * (X + 4.0) ** 2 - (Y - 5.0) ** 2 + (X + 4.0) * (Y - 5.0))
+            + a3 * np.exp(-0.9 * ((X - 4.0) ** 2 + (Y + 4.0) ** 2 + (X - 4.0) * (Y + 4.0))))
+
+
+def paper_workload(n: int = 512, m: int = 51, mp: int = 51, *, noise_level: float = 1e-4, n_alpha: int = 32,
+                   seed: int = 7000):
+    """The experiment of Sec. 6 in the paper's own coordinates: R = [-10, 10]^2 x [1, 2] with mp depths,
+    Y = [-10, 10]^2 x [6, 7] with m observation planes (both voxel-centred), the ten point sources of
+    one experiment (the cross (0, 0), (+-8, 0), (0, +-8) on the planes z0 = 3 and z0 = 5: Q = 1, L = 10),
+    A0 = 1 (g = exp(-t)), and the model solution (paper_model_xi).  Noise: i.i.d. Gaussian of relative
+    level noise_level (the paper's 'errors of order 1e-8' lie below the FP32 data's own precision)."""
+    rng = np.random.default_rng(seed)
+    h = 20.0 / n
+    x0 = -10.0
+    zr, nu = slab_depths(mp, 1.0, 2.0)
+    zy, _ = slab_depths(m, 6.0, 7.0)
+    cross = np.array([(0.0, 0.0), (-8.0, 0.0), (8.0, 0.0), (0.0, -8.0), (0.0, 8.0)])
+    sources = np.zeros((1, 10, 3))
+    for k, z0 in enumerate((3.0, 5.0)):
+        sources[0, 5 * k:5 * k + 5, :2] = cross
+        sources[0, 5 * k:5 * k + 5, 2] = z0
+    xi = paper_model_xi(n, x0, h, zr)
+    noise = rng.standard_normal((1, m, n, n))
+    alphas = np.logspace(-8.0, -1.0, n_alpha)
+    return Workload(n=n, x0=x0, h=h, zr=zr, nu=nu, zy=zy, sources=sources, xi_true=xi,
+                    noise=noise, noise_level=noise_level, alphas=alphas, seed=seed)
+
+
 # The five workload shapes (sizes, counts and ranges) of the benchmark suite.
 def config_workload(k: int, seed: int | None = None, instance: int = 0):
     """k = 1: 32^2 x 16, single source, 2 Gaussians, 1 % noise, 16 alphas.
