@@ -16,7 +16,9 @@
  *   step 4  xi = zeta / V0, xi = 1/c0^2 - 1/c^2 (c = (1/c0^2 - xi)^(-1/2)).
  *
  * Conventions.  Horizontal grid: n x n voxel-centred points x_a = x0 + (a + 1/2) h
- * (same in y); the box is periodic (pad = 1, the paper's discrete model of Sec. 5).
+ * (same in y).  The box is periodic (pad = 1, the paper's discrete model of Sec. 5) or the
+ * zero-padded box of twice the side (pad = 2: volumes stay n x n, the transforms run on 2n x 2n
+ * with the inputs in the low corner and zeros elsewhere, and results are cropped to n x n).
  * Real volumes are row-major [plane][y][x] (x fastest).  The forward DFT is
  * unnormalised, the inverse carries 1/n^2; the continuous transform is
  * approximated by h^2 * DFT.  Depth grids: M' depths z'_j of R with quadrature
@@ -86,13 +88,14 @@ extern "C" {
 #define FR3D_MAX_ALPHAS 128
 #define FR3D_MAX_BANDS 16
 #define FR3D_MAX_SOURCE_POINTS 256 /* total points over all source parameters q */
-#define FR3D_MAX_OBS_DEPTHS 64     /* M (observation depths) of fr3d_invert; M > 1 needs FP32 and n <= 384 */
+#define FR3D_MAX_OBS_DEPTHS 64     /* M (observation depths) of fr3d_invert; M > 1 needs FP32 */
 
 /* Flat-layer geometry (Sec. 3: R = R^2 x [h, H], Y = R^2 x [h_Y, H_Y]; Sec. 5 grids). */
 typedef struct fr3d_geometry {
   int nx, ny;              /* horizontal grid; nx == ny == n, n = 2^a 3^b with 16 <= n <= 512 */
   double x0, y0, hx, hy;   /* voxel-centred grid x_a = x0 + (a + 1/2) hx; hx == hy > 0 */
-  int pad;                 /* box factor P; only 1 (periodic box of side n h) is supported */
+  int pad;                 /* box factor P: 1 (periodic box of side n h) or 2 (zero-padded box of side
+                              2 n h; 2n must itself be a supported size, so n <= 256) */
   int nzr;                 /* M' >= 1: depths of R */
   const double* zr;        /* host [M'] depths z'_j */
   const double* nu;        /* host [M'] quadrature weights nu_j (NULL: midpoint, |z'_1 - z'_0|, or 1 if M' = 1) */
@@ -142,7 +145,14 @@ typedef struct fr3d_invert_opts {
 /* Step 1 for the kernel (Algorithm 1, Sec. 5): samples K at the periodic lags for every
  * z_i - z'_j, transforms them in FP64 and builds the tables A^(m) = [nu_j K~(w^(m), z_i - z'_j)]
  * of Eq. (6), ||A^(m)||_F^2 and s^2.  Allocates the handle (free with fr3d_handle_destroy).
- * The geometry's host arrays are copied; they may be freed after the call returns. */
+ * The geometry's host arrays are copied; they may be freed after the call returns.
+ * pad = 2: the tables are those of the 2n x 2n box (lags wrapped at 2n, frequencies 2 pi k/(2 n h),
+ * s^2 of the box), so the box's circular sums equal the aperiodic sums over the n x n grid.
+ * fr3d_fwd_apply, fr3d_zeta_from_xi, fr3d_choose_alpha, fr3d_invert and fr3d_invert_host take and
+ * return n x n volumes on such a handle; the residuals and the discrepancy rule are those of the
+ * box (A zeta against the zero-padded data over all (2n)^2 points, the data's zeros included);
+ * fr3d_fwd_apply_noalloc, fr3d_assemble_rhs, fr3d_band_features, fr3d_band_alpha_targets and the
+ * batched plan take periodic-box handles only and return FR3D_ERR_UNSUPPORTED_SIZE for pad = 2. */
 int fr3d_kernel_transform(const fr3d_geometry* geom, fr3d_handle** out, void* stream);
 void fr3d_handle_destroy(fr3d_handle* h);
 

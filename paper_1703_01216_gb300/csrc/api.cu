@@ -367,6 +367,7 @@ using fr3d::Handle;
 
 extern "C" int fr3d_fwd_apply(fr3d_handle* h, const void* zeta, int Q, void* U, int precision, void* stream) {
   if (!h || !zeta || !U || Q < 1 || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return fr3d::padded_fwd_apply(h, zeta, Q, U, precision, (cudaStream_t)stream);
   Handle* H = &h->h;
   cudaStream_t st = (cudaStream_t)stream;
   if (precision == FR3D_PREC_FP64) return fr3d::fwd_impl<double>(H, (const double*)zeta, Q, (double*)U, st);
@@ -376,6 +377,7 @@ extern "C" int fr3d_fwd_apply(fr3d_handle* h, const void* zeta, int Q, void* U, 
 extern "C" int fr3d_zeta_from_xi(fr3d_handle* h, const void* xi, const fr3d_sources* sources, void* zeta,
                                  int precision, void* stream) {
   if (!h || !xi || !zeta || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return fr3d::padded_zeta_from_xi(h, xi, sources, zeta, precision, (cudaStream_t)stream);
   Handle* H = &h->h;
   FR3D_TRY(fr3d::ensure_sources(H, sources));
   cudaStream_t st = (cudaStream_t)stream;
@@ -391,6 +393,9 @@ extern "C" int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const dou
                                  int* info, void* stream) {
   if (!h || !U || Q < 1 || !alpha_idx || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
   FR3D_TRY(fr3d::check_alphas(alphas, n_alpha));
+  if (h->padded)
+    return fr3d::padded_choose_alpha(h, U, Q, alphas, n_alpha, delta, tau, precision, alpha_idx, residuals, info,
+                                     (cudaStream_t)stream);
   if (!(delta >= 0) || !isfinite(delta) || !(tau > 0) || !isfinite(tau)) return FR3D_ERR_INVALID_ARG;
   Handle* H = &h->h;
   cudaStream_t st = (cudaStream_t)stream;
@@ -408,6 +413,10 @@ extern "C" int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const dou
 extern "C" int fr3d_invert(fr3d_handle* h, const void* U, int Q, const fr3d_invert_opts* opts, void* out,
                            void* stream) {
   if (!h || !U || !out) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) {
+    FR3D_TRY(fr3d::check_invert_args(&h->padded->h, Q, opts));
+    return fr3d::padded_invert(h, U, Q, opts, out, (cudaStream_t)stream);
+  }
   Handle* H = &h->h;
   FR3D_TRY(fr3d::check_invert_args(H, Q, opts));
   cudaStream_t st = (cudaStream_t)stream;
@@ -467,6 +476,10 @@ static int invert_host_t(Handle* H, const void* U_host, int Q, const fr3d_invert
 extern "C" int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_invert_opts* opts,
                                 void* out_host, void* stream) {
   if (!h || !U_host || !out_host) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) {
+    FR3D_TRY(fr3d::check_invert_args(&h->padded->h, Q, opts));
+    return fr3d::padded_invert_host(h, U_host, Q, opts, out_host, (cudaStream_t)stream);
+  }
   Handle* H = &h->h;
   FR3D_TRY(fr3d::check_invert_args(H, Q, opts));
   cudaStream_t st = (cudaStream_t)stream;
@@ -477,6 +490,7 @@ extern "C" int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const
 extern "C" int fr3d_assemble_rhs(fr3d_handle* h, const float* dV2dz, int Q, const fr3d_sources* sources, double A2,
                                  double c0, int n_pi, double pi_half, float* U, void* stream) {
   if (!h || !dV2dz || !U || Q < 1 || !sources || sources->q != Q) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return FR3D_ERR_UNSUPPORTED_SIZE;   // periodic box only
   if (n_pi < 2 || (n_pi & 1) || !(pi_half > 0) || !isfinite(pi_half) || !isfinite(A2) || !(c0 > 0) || !isfinite(c0))
     return FR3D_ERR_INVALID_ARG;
   Handle* H = &h->h;
@@ -540,6 +554,7 @@ extern "C" int fr3d_last_launch_count(fr3d_handle* h) { return h ? h->h.last_lau
 
 extern "C" int fr3d_profile_enable(fr3d_handle* h, int enable) {
   if (!h) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return fr3d_profile_enable(h->padded, enable);   // the stages of the box's calls
   Handle* H = &h->h;
   if (enable && !H->ev[0]) {
     for (int i = 0; i < Handle::kMaxEv; ++i) FR3D_CUDA_TRY(cudaEventCreate(&H->ev[i]));
@@ -551,6 +566,7 @@ extern "C" int fr3d_profile_enable(fr3d_handle* h, int enable) {
 
 extern "C" int fr3d_profile_read(fr3d_handle* h, int* kinds, float* ms, int cap) {
   if (!h || (cap > 0 && (!kinds || !ms))) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return fr3d_profile_read(h->padded, kinds, ms, cap);
   Handle* H = &h->h;
   if (H->n_ev < 2) return 0;
   FR3D_CUDA_TRY(cudaEventSynchronize(H->ev[H->n_ev - 1]));

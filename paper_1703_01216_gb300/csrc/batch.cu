@@ -123,6 +123,7 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
   for (int i = 0; i < n; ++i) {
     const fr3d_instance& I = inst[i];
     if (!I.handle || !I.U || !I.out || !I.opts || I.Q < 1) return FR3D_ERR_INVALID_ARG;
+    if (I.handle->padded) return FR3D_ERR_UNSUPPORTED_SIZE;   // periodic box only
     for (int k = 0; k < i; ++k)
       if (inst[k].handle == I.handle) return FR3D_ERR_INVALID_ARG;   // one workspace per handle
     if (I.opts->output != output || I.opts->precision != FR3D_PREC_FP32) return FR3D_ERR_INVALID_ARG;

@@ -178,4 +178,7 @@ int twiddle_offset(const Handle* H, int L);
 
 struct fr3d_handle {
   fr3d::Handle h;
+  // pad = 2: the handle of the 2n x 2n box (pad.cu); h then carries the n x n geometry's sizes and the
+  // workspace of the embedded inputs and results
+  fr3d_handle* padded = nullptr;
 };

@@ -277,6 +277,7 @@ extern "C" int fr3d_autotune_mode(int mode) {
 
 extern "C" int fr3d_autotune_query(fr3d_handle* h, int* variant, float* ms, int cap) {
   if (!h) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return fr3d_autotune_query(h->padded, variant, ms, cap);
   const fr3d::Handle* H = &h->h;
   if (variant) *variant = H->fused_var;
   if (ms)

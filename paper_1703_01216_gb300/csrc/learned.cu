@@ -657,6 +657,7 @@ extern "C" int fr3d_band_features(fr3d_handle* h, const float* U, int Q, int n_b
                                   void* stream) {
   if (!h || !U || Q < 1 || !feat || n_bands < 1 || n_bands > FR3D_MAX_BANDS || !(delta > 0) || !isfinite(delta))
     return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return FR3D_ERR_UNSUPPORTED_SIZE;   // periodic box only
   fr3d::Handle* H = &h->h;
   if (H->M != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
   cudaStream_t st = (cudaStream_t)stream;
@@ -671,6 +672,7 @@ extern "C" int fr3d_band_features(fr3d_handle* h, const float* U, int Q, int n_b
 extern "C" int fr3d_band_alpha_targets(fr3d_handle* h, const float* U, const float* zeta_true, int Q,
                                        const double* alphas, int n_alpha, int n_bands, int* idx, float* target,
                                        double* err, void* stream) {
+  if (h && h->padded) return FR3D_ERR_UNSUPPORTED_SIZE;   // periodic box only
   if (!h || !U || !zeta_true || Q < 1 || !alphas || n_alpha < 1 || n_alpha > FR3D_MAX_ALPHAS || n_bands < 1 ||
       n_bands > FR3D_MAX_BANDS || !idx)
     return FR3D_ERR_INVALID_ARG;

@@ -47,6 +47,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 extern "C" int fr3d_fwd_apply_noalloc(fr3d_handle* h, const float* zeta, int Q, float* U, void* stream) {
   using namespace fr3d;
   if (!h || !zeta || !U || Q < 1) return FR3D_ERR_INVALID_ARG;
+  if (h->padded) return FR3D_ERR_UNSUPPORTED_SIZE;   // periodic box only
   Handle* H = &h->h;
   const int n = H->n;
   const long ps = (long)(n / 2 + 1) * n;

@@ -87,4 +87,15 @@ int alpha_tables(Handle* H, const double* alphas, int n_alpha, int ra, cudaStrea
 int fixed_table(Handle* H, double alpha, int ra, cudaStream_t st);
 int build_dense64(Handle* H, cudaStream_t st);
 
+// pad = 2 handles (pad.cu): inputs embedded in the low corner of the 2n x 2n box, the inner handle's
+// call, results cropped to n x n
+int padded_fwd_apply(fr3d_handle* h, const void* zeta, int Q, void* U, int precision, cudaStream_t st);
+int padded_zeta_from_xi(fr3d_handle* h, const void* xi, const fr3d_sources* sources, void* zeta, int precision,
+                        cudaStream_t st);
+int padded_choose_alpha(fr3d_handle* h, const void* U, int Q, const double* alphas, int n_alpha, double delta,
+                        double tau, int precision, int* alpha_idx, double* residuals, int* info, cudaStream_t st);
+int padded_invert(fr3d_handle* h, const void* U, int Q, const fr3d_invert_opts* o, void* out, cudaStream_t st);
+int padded_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_invert_opts* o, void* out_host,
+                       cudaStream_t st);
+
 }  // namespace fr3d

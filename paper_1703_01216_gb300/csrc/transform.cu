@@ -309,7 +309,8 @@ int validate_geometry(const fr3d_geometry* g) {
   if (!g || !g->zr || !g->zy || g->nzr < 1 || g->nzy < 1) return FR3D_ERR_INVALID_ARG;
   if (g->kernel_kind != FR3D_K_DZ_INV_R && g->kernel_kind != FR3D_K_INV_R) return FR3D_ERR_INVALID_ARG;
   if (g->nx != g->ny || !supported_n(g->nx)) return FR3D_ERR_UNSUPPORTED_SIZE;
-  if (g->pad != 1) return FR3D_ERR_UNSUPPORTED_SIZE;
+  if (g->pad != 1 && g->pad != 2) return FR3D_ERR_UNSUPPORTED_SIZE;
+  if (g->pad == 2 && !supported_n(2 * g->nx)) return FR3D_ERR_UNSUPPORTED_SIZE;
   if (!(g->hx > 0) || g->hx != g->hy || !isfinite(g->x0) || !isfinite(g->y0)) return FR3D_ERR_BAD_GEOMETRY;
   for (int i = 0; i < g->nzy; ++i)
     for (int j = 0; j < g->nzr; ++j) {
@@ -331,6 +332,25 @@ extern "C" int fr3d_kernel_transform(const fr3d_geometry* geom, fr3d_handle** ou
   if (rc != FR3D_OK) return rc;
   fr3d_handle* h = new (std::nothrow) fr3d_handle();
   if (!h) return FR3D_ERR_OOM;
+  if (geom->pad == 2) {
+    // the zero-padded box: an inner handle of the 2n x 2n grid with the same spacing and origin; this
+    // handle keeps the n x n sizes (pad.cu)
+    fr3d_geometry g2 = *geom;
+    g2.nx = g2.ny = 2 * geom->nx;
+    g2.pad = 1;
+    rc = fr3d_kernel_transform(&g2, &h->padded, stream);
+    if (rc != FR3D_OK) {
+      delete h;
+      return rc;
+    }
+    h->h.n = geom->nx;
+    h->h.M = geom->nzy;
+    h->h.Mp = geom->nzr;
+    h->h.dev = h->padded->h.dev;
+    h->h.s2_host = h->padded->h.s2_host;
+    *out = h;
+    return FR3D_OK;
+  }
   rc = fr3d::kernel_transform_impl(geom, &h->h, (cudaStream_t)stream);
   if (rc != FR3D_OK) {
     fr3d::handle_free(&h->h);
@@ -344,6 +364,7 @@ extern "C" int fr3d_kernel_transform(const fr3d_geometry* geom, fr3d_handle** ou
 extern "C" void fr3d_handle_destroy(fr3d_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  if (h->padded) fr3d_handle_destroy(h->padded);
   fr3d::handle_free(&h->h);
   delete h;
 }

@@ -172,7 +172,7 @@ def make_sources(points, A0: float = 1.0):
 class Handle:
     """Owns an fr3d_handle (fr3d_kernel_transform ... fr3d_handle_destroy)."""
 
-    def __init__(self, n, x0, h, zr, zy, nu=None, stream=None, kind=K_DZ_INV_R):
+    def __init__(self, n, x0, h, zr, zy, nu=None, stream=None, kind=K_DZ_INV_R, pad=1):
         lib = load()
         self._zr, zrp = _f64(zr)
         self._zy, zyp = _f64(zy)
@@ -180,7 +180,7 @@ class Handle:
             self._nu, nup = None, None
         else:
             self._nu, nup = _f64(nu)
-        g = Geometry(int(n), int(n), float(x0), float(x0), float(h), float(h), 1, self._zr.size, zrp, nup,
+        g = Geometry(int(n), int(n), float(x0), float(x0), float(h), float(h), int(pad), self._zr.size, zrp, nup,
                      self._zy.size, zyp, int(kind))
         hp = ct.c_void_p()
         _check(lib.fr3d_kernel_transform(ct.byref(g), ct.byref(hp), _stream(stream)), "fr3d_kernel_transform")
@@ -201,8 +201,9 @@ class Handle:
             pass
 
 
-def kernel_transform(n, x0, h, zr, zy, nu=None, stream=None, kind=K_DZ_INV_R) -> Handle:
-    return Handle(n, x0, h, zr, zy, nu, stream, kind)
+def kernel_transform(n, x0, h, zr, zy, nu=None, stream=None, kind=K_DZ_INV_R, pad=1) -> Handle:
+    """pad = 1: the periodic box of the n x n grid (Sec. 5); pad = 2: the zero-padded 2n x 2n box."""
+    return Handle(n, x0, h, zr, zy, nu, stream, kind, pad)
 
 
 def fwd_apply(handle: Handle, zeta, Q: int, U, precision: int = PREC_FP32, stream=None):

@@ -55,7 +55,8 @@ def _geom(fr3d, n=32, h=1.0 / 16, zr=(0.5, 0.75), zy=(0.0,), nu=None, pad=1, ny=
     (dict(n=1024), -3),                        # above the largest supported grid
     (dict(ny=64), -3),                         # non-square grid
     (dict(hy=0.1), -2),                        # non-square cells
-    (dict(pad=2), -3),                         # only the periodic box is implemented
+    (dict(pad=3), -3),                         # the periodic box (1) or the zero-padded one (2)
+    (dict(pad=2, n=512), -3),                  # the padded box 2n = 1024 is above the largest grid
 ])
 def test_geometry_checks_happen_on_the_host(lib, kw, code):
     from paper_1703_01216_gb300 import fr3d
