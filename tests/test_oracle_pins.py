@@ -191,6 +191,32 @@ def test_algorithm1_equals_dense_tikhonov_of_full_operator(zy):
     assert rel(out["zeta"].ravel(), np.linalg.pinv(Aop) @ U.ravel()) < 1e-6
 
 
+def test_pad2_inversion_is_dense_tikhonov_on_the_box_with_zero_data_outside_R():
+    """pad = 2: Algorithm 1 on the 2n x 2n box equals Tikhonov of the box's whole discrete operator
+    (brute force from the direct quadrature on the box) with the data zero-padded and the unknown free
+    over the box, cropped to R; the discrepancy residual is the spatial one over the whole box, the
+    padded zeros included."""
+    n, h, zy, zr, nu = 4, 0.3, [0.0, -0.15], [0.5, 0.8], [0.25, 0.25]
+    L = 2 * n
+    Abox = _operator_matrix(L, h, zy, zr, nu)
+    rng = np.random.default_rng(11)
+    U = rng.standard_normal((1, len(zy), n, n))
+    Ubox = np.zeros((len(zy), L, L))
+    Ubox[:, :n, :n] = U[0]
+    s2 = O.alpha_scale(O.A_matrices(n, h, zy, zr, nu, pad=2))
+    assert abs(s2 - O.alpha_scale(O.A_matrices(L, h, zy, zr, nu))) < 1e-14 * s2
+    for alpha in [1e-6, 1e-2]:
+        out = O.invert(U, n, -0.6, h, zy, zr, nu, pad=2, alpha=alpha, output="zeta")
+        stacked = np.vstack([Abox, np.sqrt(alpha * s2) * np.eye(Abox.shape[1])])
+        z = np.linalg.lstsq(stacked, np.concatenate([Ubox.ravel(), np.zeros(Abox.shape[1])]), rcond=None)[0]
+        z = z.reshape(len(zr), L, L)
+        assert rel(out["zeta"][0], z[:, :n, :n]) < 1e-9
+    out = O.invert(U, n, -0.6, h, zy, zr, nu, pad=2, alphas=[1e-6, 1e-2], delta=1.0, tau=1.1, output="zeta")
+    zfull = np.linalg.lstsq(np.vstack([Abox, np.sqrt(1e-2 * s2) * np.eye(Abox.shape[1])]),
+                            np.concatenate([Ubox.ravel(), np.zeros(Abox.shape[1])]), rcond=None)[0]
+    assert abs(out["res2"][1] - np.sum((Abox @ zfull - Ubox.ravel()) ** 2)) < 1e-10 * np.sum(U ** 2)
+
+
 def test_frequency_residual_equals_spatial_residual():
     """Parseval: the residual summed over frequencies / L^2 is the spatial residual ||A zeta - U||^2."""
     n, h, zy, zr, nu = 6, 0.3, [0.0], [0.5, 0.8], [0.25, 0.25]
