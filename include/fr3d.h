@@ -150,9 +150,10 @@ typedef struct fr3d_invert_opts {
  * s^2 of the box), so the box's circular sums equal the aperiodic sums over the n x n grid.
  * fr3d_fwd_apply, fr3d_zeta_from_xi, fr3d_choose_alpha, fr3d_invert and fr3d_invert_host take and
  * return n x n volumes on such a handle; the residuals and the discrepancy rule are those of the
- * box (A zeta against the zero-padded data over all (2n)^2 points, the data's zeros included);
- * fr3d_fwd_apply_noalloc, fr3d_assemble_rhs, fr3d_band_features, fr3d_band_alpha_targets and the
- * batched plan take periodic-box handles only and return FR3D_ERR_UNSUPPORTED_SIZE for pad = 2. */
+ * box (A zeta against the zero-padded data over all (2n)^2 points, the data's zeros included), and the
+ * per-band rules use the box's radial bands.  fr3d_fwd_apply_noalloc, fr3d_assemble_rhs,
+ * fr3d_band_features, fr3d_band_alpha_targets, the batched plan and FR3D_ALPHA_LEARNED take
+ * periodic-box handles only and return FR3D_ERR_UNSUPPORTED_SIZE for pad = 2. */
 int fr3d_kernel_transform(const fr3d_geometry* geom, fr3d_handle** out, void* stream);
 void fr3d_handle_destroy(fr3d_handle* h);
 

@@ -415,6 +415,8 @@ extern "C" int fr3d_invert(fr3d_handle* h, const void* U, int Q, const fr3d_inve
   if (!h || !U || !out) return FR3D_ERR_INVALID_ARG;
   if (h->padded) {
     FR3D_TRY(fr3d::check_invert_args(&h->padded->h, Q, opts));
+    // the learned rule's features and training targets exist for the periodic box only
+    if (opts->alpha_mode == FR3D_ALPHA_LEARNED) return FR3D_ERR_UNSUPPORTED_SIZE;
     return fr3d::padded_invert(h, U, Q, opts, out, (cudaStream_t)stream);
   }
   Handle* H = &h->h;
@@ -478,6 +480,7 @@ extern "C" int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const
   if (!h || !U_host || !out_host) return FR3D_ERR_INVALID_ARG;
   if (h->padded) {
     FR3D_TRY(fr3d::check_invert_args(&h->padded->h, Q, opts));
+    if (opts->alpha_mode == FR3D_ALPHA_LEARNED) return FR3D_ERR_UNSUPPORTED_SIZE;
     return fr3d::padded_invert_host(h, U_host, Q, opts, out_host, (cudaStream_t)stream);
   }
   Handle* H = &h->h;

@@ -124,3 +124,30 @@ def test_padded_box_differs_from_the_periodic_one_and_unsupported_calls_are_reje
         F.fwd_apply_noalloc(Hp, zeta, 1, u2)
     with pytest.raises(F.Fr3dError):
         F.band_features(Hp, dev(U), 1, 4, delta, torch.empty(4, device="cuda"))
+
+
+def test_per_band_discrepancy_uses_the_box_bands(F):
+    nb = 4
+    w, A, U, delta = _problem(32, 6, 1, 1, seed=1500)
+    H = F.kernel_transform(32, w.x0, w.h, w.zr, w.zy, w.nu, pad=2)
+    ref = O.invert(U, 32, w.x0, w.h, w.zy, w.zr, w.nu, pad=2, alphas=w.alphas, delta=delta, tau=1.1,
+                   sources=w.sources, A=A, n_bands=nb)
+    idx = torch.zeros(nb, dtype=torch.int32, device="cuda")
+    res = torch.zeros((nb, w.alphas.size), dtype=torch.float64, device="cuda")
+    xi = torch.empty((6, 32, 32), device="cuda")
+    F.invert(H, dev(U), 1, xi, F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx,
+                                      residuals=res, n_bands=nb))
+    assert np.max(np.abs(host(res) - ref["res2"]) / np.maximum(ref["res2"], 1e-300)) <= 1e-5
+    got = [int(v) for v in idx.cpu().numpy()]
+    count = np.bincount(O.radial_bands(64, nb), minlength=nb)          # the bands of the 64 x 64 box
+    for b in range(nb):
+        if got[b] != ref["alpha_index"][b]:
+            thr2 = (1.1 * delta) ** 2 * count[b] / 64 ** 2
+            lo, hi = sorted((got[b], ref["alpha_index"][b]))
+            assert np.all(np.abs(ref["res2"][b][lo:hi + 1] - thr2) <= 1e-4 * thr2)
+    if got == ref["alpha_index"]:
+        assert rel(host(xi), ref["xi"]) <= 1e-4
+    # the learned rule has no padded-box features: rejected before any launch
+    net = F.Mlp(nb, 16, nb, seed=1)
+    with pytest.raises(F.Fr3dError):
+        F.invert(H, dev(U), 1, xi, F.Opts(alphas=w.alphas, delta=delta, points=w.sources, n_bands=nb, net=net))
