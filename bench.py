@@ -383,6 +383,8 @@ def run_fr3d(args):
     # reconstruction quality of the last step (not timed)
     xi_true = torch.tensor(w.xi_true, device=dev)
     rel_truth = float((out.double() - xi_true).norm() / xi_true.norm())
+    xi_proj = projection_xi(fr3d, H, w, dev)
+    rel_proj = rel_l2(out, xi_proj)
 
     # roofline of the dominant kernel (largest summed time over the timed region)
     dom = max(stage_ms, key=stage_ms.get)
@@ -429,11 +431,14 @@ def run_fr3d(args):
                                    "autotuned on the first call (1 warm-up + 3 timed launches per variant)")},
         "alpha_index": int(idx.item()), "info": int(info.item()),
         "rel_l2_vs_truth": round(rel_truth, 4),
+        "rel_l2_vs_projection": round(rel_proj, 4),
+        "projection_rel_l2_vs_truth": round(rel_l2(xi_proj, xi_true), 4),
     }
     clocks = clk.summary()
     result["clocks"] = clocks
     if not args.no_learned:
-        result["learned"] = bench_learned(args, dev, flush, w, H, U, delta, rel_truth, dist)
+        result["learned"] = bench_learned(args, dev, flush, w, H, U, delta, rel_truth, dist, xi_proj=xi_proj,
+                                          plain_rel_proj=rel_proj)
     if rank == 0 and not args.no_batch:
         result["batched"] = bench_batched(args, dev, flush)
     if rank == 0 and not args.no_paper_geometry:
@@ -454,7 +459,31 @@ def run_fr3d(args):
         dist.destroy_process_group()
 
 
-def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, pairs=1024, train_steps=3000):
+def projection_xi(fr3d, H, w, dev):
+    """The part of the phantom that the data determine (M = 1 leaves M' - 1 directions per frequency
+    unseen, so the error against the phantom itself stays near 0.9 whatever the alpha rule): the
+    library's FP64 forward operator applied to zeta_q = xi_true V0_q, inverted in FP64 at alpha = 1e-14
+    without noise -- per frequency the projection of zeta_q onto the row space of A^(m) (up to the
+    filter 1 - O(alpha s^2 / |a|^2)), combined over q like the reconstruction.  Not timed."""
+    import torch
+    xi64 = torch.tensor(w.xi_true, dtype=torch.float64, device=dev)
+    zeta = torch.empty((w.Q, w.Mp, w.n, w.n), dtype=torch.float64, device=dev)
+    fr3d.zeta_from_xi(H, xi64, w.sources, zeta, precision=fr3d.PREC_FP64)
+    U0 = torch.empty((w.Q, w.M, w.n, w.n), dtype=torch.float64, device=dev)
+    fr3d.fwd_apply(H, zeta, w.Q, U0, fr3d.PREC_FP64)
+    del zeta
+    out = torch.empty((w.Mp, w.n, w.n), dtype=torch.float64, device=dev)
+    fr3d.invert(H, U0, w.Q, out, fr3d.Opts(alpha=1e-14, precision=fr3d.PREC_FP64, points=w.sources))
+    torch.cuda.synchronize()
+    return out
+
+
+def rel_l2(a, b):
+    return float((a.double() - b.double()).norm() / b.double().norm())
+
+
+def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, pairs=1024, train_steps=3000,
+                  xi_proj=None, plain_rel_proj=None):
     """The learned per-band alpha rule on the same workload: a network trained on pairs made by the
     library's forward operator at this geometry (seeds disjoint from the workload's), then the
     inversion with FR3D_ALPHA_LEARNED timed exactly like the plain one (one CUDA graph replay per
@@ -510,6 +539,7 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
     world = dist.get_world_size() if dist else 1
     xi_true = torch.tensor(w.xi_true, device=dev)
     rel = float((out.double() - xi_true).norm() / xi_true.norm())
+    rel_proj = rel_l2(out, xi_proj) if xi_proj is not None else None
     # the ceiling of a per-band rule: the error-optimal candidate of every band (needs the true zeta)
     zeta = torch.empty((Q, Mp, n, n), device=dev)
     fr3d.zeta_from_xi(H, xi_true.float(), w.sources, zeta)
@@ -519,12 +549,16 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
     fr3d.invert(H, U, Q, out, fr3d.Opts(alphas=w.alphas, points=w.sources, alpha_idx=best, n_bands=n_bands,
                                         given=True))
     rel_best = float((out.double() - xi_true).norm() / xi_true.norm())
+    rel_best_proj = rel_l2(out, xi_proj) if xi_proj is not None else None
     res = {"value": whole_job_rate(n * n * Mp, world, args.steps, total_s), "unit": "voxels/s",
            "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_ms.items()},
            "band_optimal_rel_l2_vs_truth": round(rel_best, 4),
            "band_optimal_alpha_index": [int(v) for v in best.cpu().numpy()],
            "ms_per_step": 1e3 * total_s / args.steps, "gpu_launches": launches_per_step * args.steps,
            "rel_l2_vs_truth": round(rel, 4), "plain_rel_l2_vs_truth": round(plain_rel, 4),
+           "rel_l2_vs_projection": None if rel_proj is None else round(rel_proj, 4),
+           "plain_rel_l2_vs_projection": None if plain_rel_proj is None else round(plain_rel_proj, 4),
+           "band_optimal_rel_l2_vs_projection": None if rel_best_proj is None else round(rel_best_proj, 4),
            "alpha_index_per_band": [int(v) for v in idx.cpu().numpy()], "info": int(info.item()),
            "n_bands": n_bands, "network": f"{n_bands}-64-64-{n_bands} tanh MLP, BF16 weights",
            "train_pairs": pairs, "train_steps": train_steps, "pairs_s": round(t_pairs, 2),
