@@ -687,9 +687,21 @@ def bench_batched(args, dev, flush, count=64):
             tot += a.elapsed_time(b)
         res[mode] = voxels * reps / (tot * 1e-3)
     launches_looped = sum(4 for _ in items)
+    # HBM view of the whole batch (3.6 GB of two-pass bytes, far above L2): the inverse's
+    # two-pass algorithmic bytes of every instance over the batched replay's time; the data FFT and
+    # the alpha rule run inside that time too, so this is a lower bound of the step's bandwidth
+    algo = sum(fused_algorithmic_bytes(w.n, w.Mp, w.Q)["two_pass"] for w in wls)
+    ms = voxels / res["batched"] * 1e3
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
     out = {"workload": f"{count} uneven instances (n 64-256, M' 16-64, Q 1-8, 32 alphas)", "voxels": voxels,
            "value": res["batched"], "looped_value": res["looped"], "unit": "voxels/s",
-           "launches_batched": B.launches, "launches_looped": launches_looped, "reps": reps}
+           "launches_batched": B.launches, "launches_looped": launches_looped, "reps": reps,
+           "ms_per_step": round(ms, 4),
+           "hbm": {"two_pass_bytes": algo, "achieved": round(algo / (ms * 1e-3) / 1e9, 1), "peak": peak,
+                   "unit": "GB/s", "frac": round(algo / (ms * 1e-3) / 1e9 / peak, 4),
+                   "basis": "inverse two-pass algorithmic bytes of all instances / whole batched step"}}
     B.close()
     return out
 
