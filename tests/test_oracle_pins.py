@@ -332,6 +332,36 @@ def test_band_residuals_partition_the_global_residual():
     assert np.allclose(one["zeta"], fix["zeta"], rtol=0, atol=1e-13 * np.abs(fix["zeta"]).max())
 
 
+def test_radial_bands_are_symmetric_monotone_and_hand_evaluated():
+    """The bands depend only on the folded |k| (so every 8-fold symmetry class lies in one band), grow
+    with it, start at DC and end at the corner; two values by hand: L = 16, 4 bands, band width
+    sqrt(2) * 8 / 4 = 2.83 in |k'|."""
+    L, nb = 16, 4
+    B = O.radial_bands(L, nb).reshape(L, L)
+    neg = (-np.arange(L)) % L
+    assert np.array_equal(B, B.T) and np.array_equal(B, B[neg]) and np.array_equal(B, B[:, neg])
+    kf = np.minimum(np.arange(L), L - np.arange(L))
+    rho = np.sqrt(kf[None, :] ** 2 + kf[:, None] ** 2).ravel()
+    order = np.argsort(rho, kind="stable")
+    assert np.all(np.diff(B.ravel()[order]) >= 0)
+    assert B[0, 0] == 0 and B[L // 2, L // 2] == nb - 1
+    assert B[0, 3] == 1                      # |k'| = 3: 3 / 2.83 = 1.06
+    assert B[5, 5] == 2                      # |k'| = 7.07: 2.5
+
+
+def test_alpha_scale_is_the_dc_norm_in_closed_form():
+    """At M = 1 the kernel samples of one depth difference share one sign, so the DC bin has the largest
+    modulus of its transform (triangle inequality) and s^2 = sum_j (nu_j K~(0, dz_j))^2, with K~(0, dz)
+    the box integral of the kernel: minus the sign of dz times the solid angle of the box's square."""
+    n, h = 256, 0.01
+    zr, nu = [0.3, 0.5], [0.2, 0.1]
+    A = O.A_matrices(n, h, [0.0], zr, nu)
+    lo, hi = -(n / 2 + 0.5) * h, (n / 2 - 0.5) * h
+    exact = sum((v * _rect_solid_angle(lo, hi, lo, hi, -z)) ** 2 for z, v in zip(zr, nu))
+    assert abs(O.alpha_scale(A) - exact) <= 1e-3 * exact
+    assert np.argmax(np.sum(A * A, axis=(-2, -1))) == 0
+
+
 # ------------------------------------------------------------------ truncated SVD (Sec. 5, the paper's best RA)
 def test_tsvd_matches_library_pseudo_inverse_and_limits():
     """tsvd_solve against numpy.linalg.pinv with the matching cut-off, and its two limits."""
