@@ -165,10 +165,10 @@ def recorded_traffic(stage: str):
 
 def fused_algorithmic_bytes(n: int, mp: int, q: int) -> dict:
     """Algorithmic bytes of one launch of the fused inverse (steps 2-4 for all M' depths and Q sources,
-    M = 1) in the accounting of the hot-path table: the data spectra (8 Q (n/2+1) n), the kernel table as
-    FP64 frequency classes (8 C M'), the xi output (4 n^2 M') and, for the two-pass form the target is
-    judged against, the half-spectrum intermediate written and read once per source (8 Q n^2 M');
-    "minimum" leaves the intermediate out."""
+    M = 1): the data spectra (8 Q (n/2+1) n), the kernel table as FP64 frequency classes (8 C M'), the xi
+    output (4 n^2 M') and, for a two-pass inverse (a solve that writes the half spectra, an inverse
+    transform that reads them), the half-spectrum intermediate written and read once per source
+    (8 Q n^2 M'); "minimum" leaves the intermediate out.  The roofline is quoted on the two-pass figure."""
     ps = (n // 2 + 1) * n
     C = (n // 2 + 1) * (n // 2 + 2) // 2
     minimum = q * ps * 8.0 + C * mp * 8.0 + mp * n * n * 4.0
@@ -402,7 +402,7 @@ def run_fr3d(args):
     roof = {"kernel": dom_key, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom_key),
             "algorithmic_bytes_per_launch": algo,
-            "algorithmic_basis": ("two-pass figure of the hot-path table: data spectra + FP64 class table + xi + "
+            "algorithmic_basis": ("two-pass figure: data spectra + FP64 class table + xi + "
                                   "8 B per voxel per source of half-spectrum intermediate" if fab else
                                   "every input read once, every output written once"),
             "minimum_bytes_per_launch": fab["minimum"] if fab else None,
