@@ -196,12 +196,16 @@ def stage_bytes(stage: str, n: int, mp: int, q: int, nj: int) -> float:
 
 
 # ---------------------------------------------------------------- CPU oracle (bounded sample)
-def oracle_sample(w, A, U, delta, budget_bins=96):
+def oracle_sample(w, A, U, delta, budget_bins=768):
     """Time the FP64 oracle on a bounded sample of one step and scale it to the whole step.
 
     Sample: the data DFT (all Q planes, full), the Tikhonov QR solves and residuals for all 64
     alphas on ``budget_bins`` of the n^2 frequencies (scaled by n^2 / budget_bins), and the inverse
-    DFT plus combination for one of the M' depths (scaled by M')."""
+    DFT plus combination for one of the M' depths (scaled by M').  The oracle solves its frequencies
+    in batches of 4096, and a batch's cost per frequency grows with its size (the stacked systems
+    leave the caches): measured on one host, about 150 us per frequency and candidate at 32-96
+    frequencies, 246 at 768, 253 at 2048.  The default 768 keeps the scaled estimate within a few
+    per cent of the oracle's own batching; smaller samples make it look faster than it is."""
     import oracle as O
     n, Q, Mp = w.n, w.Q, w.Mp
     rng = np.random.default_rng(0)
@@ -721,12 +725,15 @@ def run_reference(args):
     nz = w.noise * (w.noise_level * np.linalg.norm(U) / np.linalg.norm(w.noise))
     U = U + nz
     delta = float(np.linalg.norm(nz))
+    # each step a bounded sample: about 3000 sampled frequencies over the whole run (a few minutes on
+    # 16 cores); fewer per step than the main line's 768, so the estimate is optimistic (oracle_sample)
+    per_step = int(min(768, max(32, 3000 // max(1, args.steps))))
     for _ in range(max(0, min(args.warmup, 1))):
         oracle_sample(w, A, U, delta, budget_bins=16)
     ests = []
     sample = None
     for _ in range(args.steps):
-        s = oracle_sample(w, A, U, delta, budget_bins=32)
+        s = oracle_sample(w, A, U, delta, budget_bins=per_step)
         ests.append(s["seconds_per_step_est"])
         sample = s["sample"]
     sec = float(np.mean(ests))
