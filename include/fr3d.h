@@ -136,7 +136,7 @@ typedef struct fr3d_invert_opts {
                               2..FR3D_MAX_BANDS: radial bands of |k| (band b holds the frequencies with
                               b <= n_bands |k| / (sqrt(2) n/2) < b + 1), each with its own alpha; the
                               discrepancy bound of band b is tau delta sqrt(frequencies in b / n^2)
-                              (white noise).  DISCREPANCY, GIVEN and LEARNED only, M = 1. */
+                              (white noise).  DISCREPANCY and GIVEN (any M) and LEARNED (M = 1). */
   const fr3d_mlp* net;     /* LEARNED: the network (n_in == n_out == max(1, n_bands)); NULL otherwise */
   int ra;                  /* FR3D_RA_TIKHONOV (0, default) or FR3D_RA_TSVD: alpha (or each candidate) is
                               then the truncation level relative to s^2; every alpha mode but LEARNED */
