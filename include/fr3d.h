@@ -55,7 +55,9 @@ extern "C" {
 #define FR3D_OK 0
 #define FR3D_ERR_INVALID_ARG (-1)      /* NULL pointer, negative count, bad enum */
 #define FR3D_ERR_BAD_GEOMETRY (-2)     /* some z_i - z'_j == 0 (R and Y overlap), h <= 0 */
-#define FR3D_ERR_UNSUPPORTED_SIZE (-3) /* n not 2^a 3^b in [16, 512], nx != ny, too many alphas/sources */
+#define FR3D_ERR_UNSUPPORTED_SIZE (-3) /* n not 2^a 3^b in [16, 512], nx != ny, too many alphas/sources,
+                                          pad not 1 or 2 (pad 2: 2n too), a call that keeps the
+                                          periodic box made on a pad-2 handle */
 #define FR3D_ERR_OOM (-4)              /* device allocation failed */
 #define FR3D_ERR_CUDA (-5)             /* a CUDA runtime call failed */
 #define FR3D_ERR_TIMEOUT (-6)          /* a bounded device wait gave up */
