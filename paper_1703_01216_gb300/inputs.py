@@ -148,7 +148,7 @@ def paper_workload(n: int = 512, m: int = 51, mp: int = 51, *, noise_level: floa
     Y = [-10, 10]^2 x [6, 7] with m observation planes (both voxel-centred), the ten point sources of
     one experiment (the cross (0, 0), (+-8, 0), (0, +-8) on the planes z0 = 3 and z0 = 5: Q = 1, L = 10),
     A0 = 1 (g = exp(-t)), and the model solution (paper_model_xi).  Noise: i.i.d. Gaussian of relative
-    level noise_level (the paper's 'errors of order 1e-8' lie below the FP32 data's own precision)."""
+    level noise_level (the paper's data errors, about 1e-8, lie below the FP32 data's own precision)."""
     rng = np.random.default_rng(seed)
     h = 20.0 / n
     x0 = -10.0
