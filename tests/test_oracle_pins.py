@@ -404,6 +404,27 @@ def test_tsvd_matches_library_pseudo_inverse_and_limits():
     assert np.all(O.tsvd_solve(A, Uh, 10 * sig.max() ** 2) == 0)
 
 
+def test_single_observation_depth_has_closed_form_solutions():
+    """M = 1: A^(m) is one row a, so the Tikhonov minimiser is a (a . u) / (|a|^2 + alpha s^2) (the
+    Sherman-Morrison form of (a^T a + c I)^-1 a^T) and the truncated SVD keeps a u / |a|^2 when
+    |a|^2 >= t, else 0; the squared residual of the Tikhonov solution is (c / (|a|^2 + c))^2 |u|^2."""
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((30, 1, 7)) * np.exp(-rng.uniform(0, 4, (30, 1, 1)))
+    u = rng.standard_normal((30, 1, 3)) + 1j * rng.standard_normal((30, 1, 3))
+    a2 = np.sum(A[:, 0, :] ** 2, axis=1)
+    for c in (1e-3, 0.2):
+        x = O.tikhonov_qr(A, u, c)
+        closed = A[:, 0, :, None] * u[:, :, :] / (a2 + c)[:, None, None]
+        assert rel(x, closed) < 1e-12
+        r2 = np.sum(np.abs(A @ x - u) ** 2, axis=(1, 2))
+        assert np.allclose(r2, (c / (a2 + c)) ** 2 * np.sum(np.abs(u) ** 2, axis=(1, 2)), rtol=1e-10)
+    t = float(np.median(a2))
+    x = O.tsvd_solve(A, u, t)
+    keep = a2 >= t
+    closed = np.where(keep[:, None, None], A[:, 0, :, None] * u / a2[:, None, None], 0.0)
+    assert rel(x, closed) < 1e-12
+
+
 def test_tsvd_inversion_residual_is_monotone_and_reaches_the_data_norm():
     """The squared residual grows with the truncation level; with every singular value truncated it is
     ||U||^2 (the zero solution), and at M = 1 with none truncated it is 0 (an exact fit)."""
