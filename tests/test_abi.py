@@ -72,3 +72,19 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fr3d_invert(None, None, 1, None, None, None) == -1
     assert lib.fr3d_fwd_apply(None, None, 1, None, 0, None) == -1
     assert lib.fr3d_status_string(-2).decode().startswith("bad geometry")
+
+
+def test_without_a_gpu_the_library_reports_an_error_and_computes_nothing(lib):
+    """No CPU fallback: on a host without a CUDA device a valid geometry returns a CUDA or allocation
+    error from fr3d_kernel_transform and no handle, and the Python binding raises (the library's error,
+    or torch's when it looks up the current CUDA stream first)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1703_01216_gb300 import fr3d
+    g, keep = _geom(fr3d)
+    hp = ct.c_void_p()
+    rc = lib.fr3d_kernel_transform(ct.byref(g), ct.byref(hp), None)
+    assert rc in (-4, -5) and not hp.value, rc
+    with pytest.raises((fr3d.Fr3dError, RuntimeError)):
+        fr3d.kernel_transform(32, -1.0, 1 / 16, [0.6, 0.8], [0.0])
