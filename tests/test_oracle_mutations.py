@@ -230,6 +230,33 @@ def _features_natural_log(mp):
     _plant(mp, LO, "band_features", lambda U, n_bands, delta: orig(U, n_bands, delta) * np.log(10.0))
 
 
+def _band_errors_normalised(mp):
+    orig = LO.band_error_curves
+    _plant(mp, LO, "band_error_curves",
+           lambda A, U, zeta_true, alphas, n_bands: orig(A, U, zeta_true, alphas, n_bands) / U.shape[-1] ** 2)
+
+
+def _second_layer_linear(mp):
+    def bad(p, X, nin, nh, nout):
+        W1, b1, W2, b2, W3, b3 = LO.mlp_unpack(p, nin, nh, nout)
+        h1 = np.tanh(np.asarray(X, np.float64) @ W1.T + b1)
+        h2 = h1 @ W2.T + b2                                   # tanh dropped
+        return h2 @ W3.T + b3, (h1, h2)
+    _plant(mp, LO, "mlp_forward", bad)
+
+
+def _candidate_below_instead_of_nearest(mp):
+    def bad(p, feat, alphas, nh):
+        feat = np.asarray(feat, np.float64)
+        nb = feat.size
+        y, _ = LO.mlp_forward(p, (feat * LO.FEAT_SCALE)[None, :], nb, nh, nb)
+        la = y[0] * LO.LOG_SCALE - LO.LOG_SHIFT
+        lg = np.log10(np.asarray(alphas, np.float64))
+        idx = np.clip(np.searchsorted(lg, la) - 1, 0, lg.size - 1)   # the candidate below, not the nearest
+        return y[0], la, idx
+    _plant(mp, LO, "learned_alpha_index", bad)
+
+
 MUTATIONS = {
     "kernel sign": (_kernel_sign, [P.test_kernel_is_z_derivative_of_inverse_distance]),
     "kernel power": (_kernel_power, [P.test_kernel_is_z_derivative_of_inverse_distance]),
@@ -259,6 +286,9 @@ MUTATIONS = {
     "Adam without bias correction": (_adam_without_bias_correction, [LP.test_adam_first_step_is_signed_learning_rate]),
     "BF16 truncation": (_bf16_truncates, [LP.test_bf16_rounding_ties_to_even]),
     "features in natural log": (_features_natural_log, [LP.test_features_single_cosine_closed_form]),
+    "band errors divided by L^2": (_band_errors_normalised, [LP.test_band_errors_equal_spatial_errors_of_the_full_inversion]),
+    "second layer without tanh": (_second_layer_linear, [LP.test_mlp_forward_by_hand_and_zero_output_layer]),
+    "candidate below, not nearest": (_candidate_below_instead_of_nearest, [LP.test_nearest_candidate_rule]),
 }
 
 
