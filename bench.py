@@ -145,6 +145,18 @@ def kernel_source_hash(stage: str = None):
     return h.hexdigest()[:16]
 
 
+def hbm_peak():
+    """(GB/s, source) of the roofline's denominator: the measured copy bandwidth ``hbm_gbs`` of
+    MEASURED_PEAKS.json when the file is there, else the fallback figure of one earlier GB300
+    measurement, 6800 GB/s."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
+        if "hbm_gbs" in peaks:
+            return float(peaks["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    return 6800.0, "fallback 6800 GB/s"
+
+
 def recorded_traffic(stage: str):
     """DRAM bytes per launch of ``stage`` (e.g. "inv_fused/v3") from the committed ncu summary, if it
     was taken on the current sources of that kernel (profiles/traffic.md lines:
@@ -398,9 +410,7 @@ def run_fr3d(args):
     design = stage_bytes(dom, n, Mp, Q, nj)
     fab = fused_algorithmic_bytes(n, Mp, Q) if dom == "inv_fused" else None
     algo = fab["two_pass"] if fab else design
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak, peak_source = hbm_peak()
     achieved = algo / (per_launch_ms * 1e-3) / 1e9
     dom_key = f"{dom}/v{tuned_variant}" if dom == "inv_fused" else dom
     roof = {"kernel": dom_key, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -411,7 +421,7 @@ def run_fr3d(args):
                                   "every input read once, every output written once"),
             "minimum_bytes_per_launch": fab["minimum"] if fab else None,
             "design_bytes_per_launch": design, "ms_per_launch": round(per_launch_ms, 5),
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"}
+            "peak_source": peak_source}
 
     result = {
         "metric": "voxels/s of FFT-Tikhonov inversion at 256^2x64 (plain discrepancy-principle method)",
@@ -696,9 +706,7 @@ def bench_batched(args, dev, flush, count=64):
     # the alpha rule run inside that time too, so this is a lower bound of the step's bandwidth
     algo = sum(fused_algorithmic_bytes(w.n, w.Mp, w.Q)["two_pass"] for w in wls)
     ms = voxels / res["batched"] * 1e3
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak, _ = hbm_peak()
     out = {"workload": f"{count} uneven instances (n 64-256, M' 16-64, Q 1-8, 32 alphas)", "voxels": voxels,
            "value": res["batched"], "looped_value": res["looped"], "unit": "voxels/s",
            "launches_batched": B.launches, "launches_looped": launches_looped, "reps": reps,

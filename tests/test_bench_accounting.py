@@ -62,3 +62,13 @@ def test_source_hash_changes_with_any_listed_file(tmp_path, monkeypatch):
     h0 = bench.kernel_source_hash("alpha")
     (csrc / bench.STAGE_SOURCES["alpha"][-1]).write_text("// changed\n")
     assert bench.kernel_source_hash("alpha") != h0
+
+
+def test_hbm_peak_reads_the_measured_copy_bandwidth_or_falls_back(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.hbm_peak() == (6800.0, "fallback 6800 GB/s")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6792.4, "bf16_tflops": 1932.2}')
+    peak, src = bench.hbm_peak()
+    assert peak == 6792.4 and "measured" in src
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"bf16_tflops": 1932.2}')
+    assert bench.hbm_peak()[0] == 6800.0
