@@ -48,3 +48,23 @@ def test_model_solution_at_hand_evaluated_points():
     assert abs(xi[0, idx[0.0], idx[0.0]] - 1.0) < 1e-6           # a1 = 1 at z = 1.5, the others ~0
     assert abs(xi[1, idx[5.0], idx[-4.0]] - 0.4) < 1e-3           # a2 = 0.4 at z = 1.3 (a1 tiny there)
     assert abs(xi[2, idx[-4.0], idx[4.0]] - 0.2) < 1e-3           # a3 = 0.2 at z = 1.7
+
+
+def test_synthetic_geometry_follows_the_stated_readings():
+    """The synthetic workloads' geometry (readings 3, 4, 8): voxel-centred depths of R = [0.5, 1] with
+    midpoint weights, one observation plane z = 0 disjoint from R, and source q the scaled cross
+    (0, 0), (+-0.8, 0), (0, +-0.8) on the plane z = -0.1 (q + 1)."""
+    w = I.config_workload(3)
+    assert (w.n, w.Mp, w.Q, w.M, w.alphas.size) == (256, 64, 8, 1, 64)
+    dz = 0.5 / 64
+    assert np.allclose(w.zr, 0.5 + (np.arange(64) + 0.5) * dz) and np.allclose(w.nu, dz)
+    assert np.array_equal(w.zy, [0.0]) and np.all(w.zr > 0)
+    assert w.x0 == -1.0 and abs(w.x0 + w.n * w.h - 1.0) < 1e-15
+    S = I.cross_sources(8)
+    cross = {(0.0, 0.0), (-0.8, 0.0), (0.8, 0.0), (0.0, -0.8), (0.0, 0.8)}
+    for q in range(8):
+        assert {tuple(np.round(p[:2], 12)) for p in S[q]} == cross
+        assert np.allclose(S[q, :, 2], -0.1 * (q + 1))
+    assert np.allclose(np.log10(w.alphas), np.linspace(-8, -1, 64))
+    # the phantom is the negative contrast and the data noise is unit-free (scaled by the level later)
+    assert w.noise.shape == (8, 1, 256, 256) and w.noise_level == 0.01
