@@ -476,6 +476,21 @@ def test_rhs_source_term_is_the_z_derivative_of_the_inverse_distances():
         assert rel(S[0, i], (field(z + e) - field(z - e)) / (2 * e)) < 1e-8
 
 
+def test_pi_depth_grid_is_the_midpoint_rule_of_the_box_height():
+    """Pi's vertical grid: n_pi cells of equal height covering [-half, half] once, one node at each cell's
+    centre, so it integrates polynomials of degree 1 exactly and z^2 with the midpoint rule's known
+    defect, (2 half) dz^2 / 12 too little."""
+    for n_pi, half in [(4, 0.75), (16, 1.28), (2, 3.0)]:
+        zp, nup = O.pi_depths(n_pi, half)
+        dz = 2 * half / n_pi
+        assert zp.size == nup.size == n_pi and np.allclose(nup, dz)
+        assert np.allclose(np.sort(zp), zp) and np.allclose(zp + zp[::-1], 0.0)
+        assert abs(zp[0] - (-half + dz / 2)) < 1e-15 and abs(np.sum(nup) - 2 * half) < 1e-14
+        assert abs(np.sum(nup * zp)) < 1e-14                                   # odd moment
+        exact2 = 2 * half ** 3 / 3
+        assert abs(np.sum(nup * zp ** 2) - (exact2 - 2 * half * dz ** 2 / 12)) < 1e-12
+
+
 def test_pi_integral_of_a_constant_density_is_a_sum_of_solid_angles():
     """The discrete operator on Pi's depth grid applied to a constant density: each layer contributes
     -sgn(z - z') times the solid angle of the periodic square seen from distance |z - z'| (midpoint rule,
