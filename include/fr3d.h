@@ -168,12 +168,13 @@ int fr3d_handle_query(fr3d_handle* h, int* n, int* m, int* mp, double* s2);
 int fr3d_fwd_apply(fr3d_handle* h, const void* zeta, int Q, void* U, int precision, void* stream);
 
 /* fr3d_fwd_apply (FP32 only) for callers that cannot allocate device memory at the point of the
- * call: for example code running while a CUDA graph is being captured, a real-time loop that
- * must not wait on the allocator, or a host framework that owns all device memory.  The paper
- * has no counterpart; this is a deployment variant.  It allocates nothing: its scratch is a
- * static 4 MiB device array that the library holds on every GPU until the process exits, so
+ * call: for example a real-time loop that cannot afford the allocator's latency or its implicit
+ * synchronisation, or a host framework that owns all device memory through its own allocator.
+ * The paper has no counterpart; this is a deployment variant.  It allocates nothing: its scratch
+ * is a static 4 MiB device array that the library holds on every GPU until the process exits, so
  * the request must satisfy 8 * (M' + M) * (n/2 + 1) * n <= 4 MiB (each term rounded up to
- * 256 bytes); larger requests return FR3D_ERR_UNSUPPORTED_SIZE before any launch.  The first
+ * 256 bytes; at n = 256, M' + M <= 15); larger requests return FR3D_ERR_UNSUPPORTED_SIZE before
+ * any launch.  The current device must be the handle's (else FR3D_ERR_INVALID_ARG).  The first
  * call on a device looks up the array's device address (no allocation); make that first call
  * before any stream capture.  All calls share the one array, so calls that overlap on the GPU
  * (other streams, other threads) race and corrupt each other; serialise them.  Nothing in the

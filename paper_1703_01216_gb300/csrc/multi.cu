@@ -50,15 +50,13 @@ __global__ void __launch_bounds__(256) k_class_eig(const double* __restrict__ A6
   __shared__ double red[256][2];
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* A = A64 + (long)c * M * Mp;
-  // G = A A^T (padded with an identity row/column when M is odd: the pad never couples)
+  // G = A A^T; when M is odd the pad is a zero row/column in G and an identity row/column in U (the
+  // pad never couples)
   for (int e = tid; e < Me * Me; e += nt) {
     const int a = e / Me, b = e % Me;
     double s = 0.0;
-    if (a < M && b < M) {
+    if (a < M && b < M)
       for (int j = 0; j < Mp; ++j) s = fma(A[(long)a * Mp + j], A[(long)b * Mp + j], s);
-    } else if (a == b) {
-      s = 0.0;
-    }
     G[e] = s;
     U[e] = a == b ? 1.0 : 0.0;
   }

@@ -1,12 +1,11 @@
 // fr3d_fwd_apply_noalloc: the forward operator with a fixed, statically allocated scratch area.
 //
 // Who needs this: code that must not call cudaMalloc at the point where it applies the operator,
-// for example a caller running inside a region that is being captured into a CUDA graph (an
-// allocation there breaks the capture), a real-time loop that forbids allocator latency, or a
-// host framework that owns all device memory through its own allocator and forbids side
-// allocations.  Such a caller creates the handle during set-up and afterwards only calls this
-// entry point, which allocates nothing: its scratch lives in the file-scope device array below,
-// loaded with the library on every GPU and held until the process exits.
+// for example a real-time loop that cannot afford the allocator's latency or its implicit
+// synchronisation, or a host framework that owns all device memory through its own allocator and
+// forbids side allocations.  Such a caller creates the handle during set-up and afterwards only
+// calls this entry point, which allocates nothing: its scratch lives in the file-scope device array
+// below, loaded with the library on every GPU and held until the process exits.
 #include <mutex>
 
 #include "ops.cuh"
@@ -49,6 +48,11 @@ extern "C" int fr3d_fwd_apply_noalloc(fr3d_handle* h, const float* zeta, int Q, 
   if (!h || !zeta || !U || Q < 1) return FR3D_ERR_INVALID_ARG;
   if (h->padded) return FR3D_ERR_UNSUPPORTED_SIZE;   // periodic box only
   Handle* H = &h->h;
+  // the handle's tables live on the device it was created on; the scratch address is looked up for
+  // the current device, so both must be the same device
+  int cur = -1;
+  FR3D_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != H->dev) return FR3D_ERR_INVALID_ARG;
   const int n = H->n;
   const long ps = (long)(n / 2 + 1) * n;
   const size_t zb = align256(sizeof(float2) * ps * H->Mp), ub = align256(sizeof(float2) * ps * H->M);

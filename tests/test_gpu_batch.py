@@ -61,8 +61,13 @@ def test_batch_matches_single_calls_and_oracle(F):
     w, U, d, idx = ws[3]
     ref = O.invert(U, w.n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=d, tau=1.1, sources=w.sources)
     got = items[3][4].double().cpu().numpy()
-    if ref["alpha_index"] == int(idx.item()):
-        assert np.linalg.norm(got - ref["xi"]) <= 1e-4 * np.linalg.norm(ref["xi"])
+    k = int(idx.item())
+    if ref["alpha_index"] != k:   # only a near-tie at the bound may differ; then compare at the GPU's choice
+        thr2 = (1.1 * d) ** 2
+        lo, hi = sorted((k, ref["alpha_index"]))
+        assert np.any(np.abs(ref["res2"][lo:hi + 1] - thr2) <= 1e-4 * thr2)
+        ref = O.invert(U, w.n, w.x0, w.h, w.zy, w.zr, w.nu, alpha=w.alphas[k], sources=w.sources)
+    assert np.linalg.norm(got - ref["xi"]) <= 1e-4 * np.linalg.norm(ref["xi"])
     B.close()
 
 

@@ -70,8 +70,9 @@ def test_largest_candidate_list_and_one_more(F):
     assert np.max(np.abs(r - ref["res2"]) / ref["res2"]) <= 1e-5
     k = int(idx.item())
     assert _choice_ok(k, ref["alpha_index"], ref["res2"], (1.1 * delta) ** 2)
-    if k == ref["alpha_index"]:
-        assert rel(host(xi), ref["xi"]) <= 1e-4
+    ref_k = ref if k == ref["alpha_index"] else O.invert(U, 32, w.x0, w.h, w.zy, w.zr, w.nu, alpha=alphas[k],
+                                                        sources=src)
+    assert rel(host(xi), ref_k["xi"]) <= 1e-4
     more = np.logspace(-8, -1, F.MAX_ALPHAS + 1)
     with pytest.raises(F.Fr3dError):
         F.invert(H, dev(U), 1, xi, F.Opts(alphas=more, delta=delta, tau=1.1, points=src))

@@ -145,8 +145,10 @@ def test_per_band_discrepancy_uses_the_box_bands(F):
             thr2 = (1.1 * delta) ** 2 * count[b] / 64 ** 2
             lo, hi = sorted((got[b], ref["alpha_index"][b]))
             assert np.all(np.abs(ref["res2"][b][lo:hi + 1] - thr2) <= 1e-4 * thr2)
-    if got == ref["alpha_index"]:
-        assert rel(host(xi), ref["xi"]) <= 1e-4
+    if got != ref["alpha_index"]:   # a proven near-tie: the oracle at the GPU's per-band choice
+        ref = O.invert(U, 32, w.x0, w.h, w.zy, w.zr, w.nu, pad=2, alphas=w.alphas, sources=w.sources, A=A,
+                       n_bands=nb, band_alpha_index=got)
+    assert rel(host(xi), ref["xi"]) <= 1e-4
     # the learned rule has no padded-box features: rejected before any launch
     net = F.Mlp(nb, 16, nb, seed=1)
     with pytest.raises(F.Fr3dError):

@@ -200,6 +200,32 @@ def _rhs_integral_sign(mp):
     _plant(mp, FO, "assemble_rhs", bad)
 
 
+def _rhs_source_coefficient_in_both(mp):
+    """A2 instead of A2 / 2 in both the assembly and the simulated measurement: the round trip still closes."""
+    def bad_assemble(dV2dz, n, x0, h, zy, sources, A0, A2, c0, n_pi, half):
+        S, I = FO.rhs_terms(n, x0, h, zy, sources, n_pi, half)
+        return 2.0 * np.pi * np.asarray(dV2dz, np.float64) + A2 * S - A0 / (4.0 * np.pi * c0 * c0) * I
+
+    def bad_simulate(U, n, x0, h, zy, sources, A0, A2, c0, n_pi, half):
+        S, I = FO.rhs_terms(n, x0, h, zy, sources, n_pi, half)
+        return (np.asarray(U, np.float64) - A2 * S + A0 / (4.0 * np.pi * c0 * c0) * I) / (2.0 * np.pi)
+    _plant(mp, FO, "assemble_rhs", bad_assemble)
+    _plant(mp, FO, "simulate_dV2dz", bad_simulate)
+
+
+def _rhs_integral_coefficient_in_both(mp):
+    """1/(4 pi c0^2) without its 4 pi in both functions: the round trip still closes."""
+    def bad_assemble(dV2dz, n, x0, h, zy, sources, A0, A2, c0, n_pi, half):
+        S, I = FO.rhs_terms(n, x0, h, zy, sources, n_pi, half)
+        return 2.0 * np.pi * np.asarray(dV2dz, np.float64) + 0.5 * A2 * S - A0 / (c0 * c0) * I
+
+    def bad_simulate(U, n, x0, h, zy, sources, A0, A2, c0, n_pi, half):
+        S, I = FO.rhs_terms(n, x0, h, zy, sources, n_pi, half)
+        return (np.asarray(U, np.float64) - 0.5 * A2 * S + A0 / (c0 * c0) * I) / (2.0 * np.pi)
+    _plant(mp, FO, "assemble_rhs", bad_assemble)
+    _plant(mp, FO, "simulate_dV2dz", bad_simulate)
+
+
 def _gradient_sign(mp):
     orig = LO.mlp_loss_grad
 
@@ -282,6 +308,12 @@ MUTATIONS = {
     "TSVD cut on sigma": (_tsvd_cut_on_sigma, [P.test_tsvd_matches_library_pseudo_inverse_and_limits]),
     "bands of unfolded k": (_bands_unfolded, [P.test_radial_bands_are_symmetric_monotone_and_hand_evaluated]),
     "RHS integral sign": (_rhs_integral_sign, [P.test_rhs_integral_term_equals_brute_force_quadrature_and_round_trip]),
+    "RHS A2 coefficient in both": (_rhs_source_coefficient_in_both,
+                                   [P.test_rhs_integral_term_equals_brute_force_quadrature_and_round_trip,
+                                    P.test_rhs_coefficients_follow_from_the_wave_equation_moments]),
+    "RHS Pi coefficient in both": (_rhs_integral_coefficient_in_both,
+                                   [P.test_rhs_integral_term_equals_brute_force_quadrature_and_round_trip,
+                                    P.test_rhs_coefficients_follow_from_the_wave_equation_moments]),
     "MLP gradient sign": (_gradient_sign, [LP.test_mlp_gradient_matches_central_differences]),
     "Adam without bias correction": (_adam_without_bias_correction, [LP.test_adam_first_step_is_signed_learning_rate]),
     "BF16 truncation": (_bf16_truncates, [LP.test_bf16_rounding_ties_to_even]),

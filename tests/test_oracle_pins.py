@@ -520,3 +520,35 @@ def test_rhs_integral_term_equals_brute_force_quadrature_and_round_trip():
     U = np.random.default_rng(3).standard_normal((2, 1, n, n))
     d = O.simulate_dV2dz(U, n, x0, h, zy, src, 1.0, 2.0, 0.5, n_pi, half)
     assert rel(O.assemble_rhs(d, n, x0, h, zy, src, 1.0, 2.0, 0.5, n_pi, half), U) < 1e-12
+
+
+def test_rhs_coefficients_follow_from_the_wave_equation_moments():
+    """The coefficients of Eq. (7) (2 pi, A2 / 2 and -A0 / (4 pi c0^2)) pinned without their printed form.
+    The time moments of the wave equation (Sec. 2) give Delta V0 = A0 phi (the zeroth moment, whatever c is)
+    and Delta V2 = 2 V0 / c^2 + A2 phi (the second, with int t^2 u_tt dt = 2 V0 and int t^2 g dt = A2).
+    Inverting the Laplacian with its Green function -1/(4 pi |x|), with 1/c^2 = 1/c0^2 - xi and zeta = xi V0:
+        V2 = -(1/(4 pi)) [ (2 / c0^2) int V0 / |x - x'| - 2 int zeta / |x - x'| + A2 sum_l 1/|x - x_l| ],
+    so d/dx3 V2 is built here from three independent pieces: the forward operator of zeta over R, the same
+    operator over the box Pi (R^3 replaced by Pi, Sec. 5) applied to the Poisson-pinned V0, and a central
+    difference of the sources' 1/r field.  Assembling Eq. (7) from that measurement must return the
+    left-hand side, the forward operator of zeta."""
+    n, x0, h, half, n_pi = 6, -0.75, 0.25, 0.75, 4
+    zy = [0.2, 0.35]
+    zr, nu = np.array([-0.6, -0.45]), np.array([0.15, 0.15])
+    A0, A2, c0 = 1.3, 2.0, 0.7
+    src = np.array([[[0.03, 0.01, -0.33], [-0.2, 0.3, -0.52]]])
+    rng = np.random.default_rng(11)
+    zeta = rng.standard_normal((1, zr.size, n, n))
+    c = x0 + (np.arange(n) + 0.5) * h
+    Xc, Yc = c[None, None, :], c[None, :, None]
+    lhs = O.forward_direct(zeta, n, h, zy, zr, nu)                          # int_R d/dx3(1/|x - x'|) zeta
+    zp, nup = O.pi_depths(n_pi, half)
+    v0 = O.V0(src[0], Xc, Yc, np.asarray(zp)[:, None, None], A0)            # V0 on Pi's grid
+    j_v0 = O.forward_direct(v0[None], n, h, zy, zp, nup)                    # int_Pi d/dx3(1/|x - x'|) V0
+    e = 1e-5
+    inv_r = lambda z: sum(1.0 / np.sqrt((Xc - p[0]) ** 2 + (Yc - p[1]) ** 2 + (z - p[2]) ** 2) for p in src[0])
+    zyc = np.asarray(zy)[:, None, None]
+    dsrc = ((inv_r(zyc + e) - inv_r(zyc - e)) / (2 * e))[None]              # sum_l d/dx3 (1/|x - x_l|)
+    dV2dz = -(1.0 / (4.0 * np.pi)) * ((2.0 / c0 ** 2) * j_v0 - 2.0 * lhs + A2 * dsrc)
+    U = O.assemble_rhs(dV2dz, n, x0, h, zy, src, A0, A2, c0, n_pi, half)
+    assert rel(U, lhs) < 1e-6                    # the central difference's error; a wrong coefficient is O(1)
