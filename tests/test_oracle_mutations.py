@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle import fr3d_oracle as FO
 from oracle import learned_oracle as LO
+from oracle import unet_oracle as UO
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -26,6 +27,7 @@ def _load(name):
 
 P = _load("test_oracle_pins")
 LP = _load("test_learned_pins")
+UP = _load("test_unet_pins")
 
 
 def _plant(monkeypatch, module, name, fn):
@@ -283,6 +285,44 @@ def _candidate_below_instead_of_nearest(mp):
     _plant(mp, LO, "learned_alpha_index", bad)
 
 
+def _unet_skip_gradient_dropped(mp):
+    """the encoder output's gradient takes the pooled path only: the decoder convolution's input gradient
+    loses its skip-connection half (the input has more channels than the output only there)"""
+    orig = UO.conv3_backward
+
+    def bad(x, w, dy):
+        dx, dw, db = orig(x, w, dy)
+        if x.shape[1] > w.shape[0]:
+            dx = dx.copy()
+            dx[:, x.shape[1] - w.shape[0]:] = 0.0
+        return dx, dw, db
+    mp.setattr(UO, "conv3_backward", bad)
+
+
+def _unet_pool_backward_unscaled(mp):
+    mp.setattr(UO, "pool2_backward", lambda dy: UO.up2(dy))
+
+
+def _unet_leaky_backward_identity(mp):
+    mp.setattr(UO, "leaky_backward", lambda y, dy: np.asarray(dy, np.float64))
+
+
+def _unet_conv_dx_unflipped(mp):
+    """the input gradient taken as the forward correlation of dy with the weights (not their adjoint)"""
+    orig = UO.conv3_backward
+
+    def bad(x, w, dy):
+        _, dw, db = orig(x, w, dy)
+        wt = np.transpose(w, (1, 0, 2, 3, 4))
+        return UO.conv3(dy, wt, np.zeros(wt.shape[0])), dw, db
+    mp.setattr(UO, "conv3_backward", bad)
+
+
+def _unet_loss_gradient_halved(mp):
+    orig = UO.loss_and_grad
+    mp.setattr(UO, "loss_and_grad", lambda y, t: (orig(y, t)[0], 0.5 * orig(y, t)[1]))
+
+
 MUTATIONS = {
     "kernel sign": (_kernel_sign, [P.test_kernel_is_z_derivative_of_inverse_distance]),
     "kernel power": (_kernel_power, [P.test_kernel_is_z_derivative_of_inverse_distance]),
@@ -321,6 +361,13 @@ MUTATIONS = {
     "band errors divided by L^2": (_band_errors_normalised, [LP.test_band_errors_equal_spatial_errors_of_the_full_inversion]),
     "second layer without tanh": (_second_layer_linear, [LP.test_mlp_forward_by_hand_and_zero_output_layer]),
     "candidate below, not nearest": (_candidate_below_instead_of_nearest, [LP.test_nearest_candidate_rule]),
+    "U-Net skip gradient dropped": (_unet_skip_gradient_dropped, [UP.test_network_gradient_matches_central_differences]),
+    "U-Net pool backward without 1/8": (_unet_pool_backward_unscaled,
+                                        [UP.test_pool_and_upsample_adjoints_and_round_trip]),
+    "U-Net leaky backward identity": (_unet_leaky_backward_identity, [UP.test_leaky_and_its_derivative]),
+    "U-Net conv input gradient unflipped": (_unet_conv_dx_unflipped,
+                                            [UP.test_conv3_backward_is_the_adjoint_and_the_weight_derivative]),
+    "U-Net loss gradient halved": (_unet_loss_gradient_halved, [UP.test_network_gradient_matches_central_differences]),
 }
 
 
