@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--fused-variant", type=int, default=None,
                     help="force the fused inverse's tile variant (default: autotuned on the first call)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg at the same workload")
     ap.add_argument("--no-paper-geometry", action="store_true", help="skip the M = M' = 51 leg")
     return ap.parse_args()
 
@@ -239,9 +240,33 @@ def oracle_sample(w, A, U, delta, budget_bins=768):
     est = (t1 - t0) + t_solve * (n * n / budget_bins) + (t4 - t3) * Mp
     wall = t4 - t0
     return {"seconds_per_step_est": est, "sample_wall_s": wall,
+            "scale_factors": {"solve": n * n / budget_bins, "inverse_dft": Mp},
             "sample": f"data DFT of all {Q} planes; QR Tikhonov solves + residuals for all {w.alphas.size} alphas on "
                       f"{budget_bins} of {n * n} frequencies (x{n * n / budget_bins:.0f}); inverse DFT + xi for 1 of "
                       f"{Mp} depths (x{Mp})"}
+
+
+def oracle_anchor(budget_bins=64):
+    """The sampled estimate checked against a full oracle step: the 32 x 32 x 16 workload (one source,
+    16 alphas, discrepancy rule, xi) timed once end to end (unsampled) and estimated by oracle_sample
+    with the same kind of frequency sample as the main workload's.  Their ratio is the extrapolation's
+    error at the size where the whole step fits in about a second."""
+    import oracle as O
+    from paper_1703_01216_gb300 import inputs as I
+    w = I.config_workload(1)
+    A = O.A_matrices(w.n, w.h, w.zy, w.zr, w.nu)
+    zeta = O.zeta_from_xi(w.xi_true, w.sources, w.n, w.x0, w.h, w.zr)
+    U = O.forward_dft(zeta, w.n, w.h, w.zy, w.zr, w.nu, A=A)
+    nz = w.noise * (w.noise_level * np.linalg.norm(U) / np.linalg.norm(w.noise))
+    U = U + nz
+    delta = float(np.linalg.norm(nz))
+    t0 = time.perf_counter()
+    O.invert(U, w.n, w.x0, w.h, w.zy, w.zr, w.nu, alphas=w.alphas, delta=delta, tau=1.1, sources=w.sources, A=A)
+    full = time.perf_counter() - t0
+    est = oracle_sample(w, A, U, delta, budget_bins=budget_bins)["seconds_per_step_est"]
+    return {"workload": "32x32x16, Q = 1, 16 alphas", "full_step_s": round(full, 4),
+            "sampled_estimate_s": round(est, 4), "estimate_over_full": round(est / full, 3),
+            "sample_bins": budget_bins}
 
 
 def cpu_cores():
@@ -450,6 +475,8 @@ def run_fr3d(args):
     }
     clocks = clk.summary()
     result["clocks"] = clocks
+    if not args.no_fp64:
+        result["fp64"] = bench_fp64(args, dev, flush, w, H, U, delta, out)
     if not args.no_learned:
         result["learned"] = bench_learned(args, dev, flush, w, H, U, delta, rel_truth, dist, xi_proj=xi_proj,
                                           plain_rel_proj=rel_proj)
@@ -457,7 +484,8 @@ def run_fr3d(args):
         result["batched"] = bench_batched(args, dev, flush)
     if rank == 0 and not args.no_paper_geometry:
         result["paper_geometry"] = bench_paper_geometry(args, dev, flush)
-        result["paper_geometry_pad2"] = bench_paper_geometry(args, dev, flush, n=256, pad=2, ras=("tsvd",))
+        result["paper_geometry_pad2"] = bench_paper_geometry(args, dev, flush, n=256, pad=2, ras=("tsvd",),
+                                                             precs=("fp32",))
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -466,7 +494,8 @@ def run_fr3d(args):
         s = oracle_sample(w, A, Uc, delta)
         result["cpu_baseline"] = {"value": voxels / s["seconds_per_step_est"], "unit": "voxels/s",
                                   "cores": cpu_cores(), "kind": "oracle", "sample": s["sample"],
-                                  "sample_wall_s": round(s["sample_wall_s"], 2)}
+                                  "estimated": True, "scale_factors": s["scale_factors"],
+                                  "sample_wall_s": round(s["sample_wall_s"], 2), "anchor": oracle_anchor()}
     if rank == 0:
         print(json.dumps(result))
     if dist:
@@ -583,14 +612,54 @@ def bench_learned(args, dev, flush, w, H, U, delta, plain_rel, dist, n_bands=8, 
     return res
 
 
-def bench_paper_geometry(args, dev, flush, n=512, m=51, mp=51, n_alpha=32, pad=1, ras=("tsvd", "tikhonov")):
+def bench_fp64(args, dev, flush, w, H, U, delta, out32):
+    """The same step in the paper's arithmetic (Sec. 6 computes in double precision): FP64 data, FFTs,
+    solve, alpha rule and xi (FR3D_PREC_FP64, the two-pass path), graph-captured and timed like the main
+    line; its xi against the FP32 line's."""
+    import torch
+    from paper_1703_01216_gb300 import fr3d
+    n, Mp, Q = w.n, w.Mp, w.Q
+    U64 = U.double()
+    out = torch.empty((Mp, n, n), dtype=torch.float64, device=dev)
+    idx = torch.zeros(1, dtype=torch.int32, device=dev)
+    opts = fr3d.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx,
+                     precision=fr3d.PREC_FP64)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        flush.fill_(1.0)
+        fr3d.invert(H, U64, Q, out, opts)
+    torch.cuda.synchronize()
+    graph = capture_step(fr3d, H, dev, st, lambda: fr3d.invert(H, U64, Q, out, opts), False)
+    launches = fr3d.last_launch_count(H)
+    for _ in range(3):
+        flush.fill_(1.0)
+        graph.replay()
+    steps = max(5, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.fill_(1.0)
+        ev[k][0].record(st)
+        graph.replay()
+        ev[k][1].record(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return {"value": n * n * Mp / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": round(ms, 5), "steps": steps,
+            "dtype": "f64", "launches_per_step": launches, "alpha_index": int(idx.item()),
+            "rel_l2_fp32_vs_fp64": round(rel_l2(out32, out), 8)}
+
+
+def bench_paper_geometry(args, dev, flush, n=512, m=51, mp=51, n_alpha=32, pad=1, ras=("tsvd", "tikhonov"),
+                         precs=("fp32", "bf16x3", "bf16tc")):
     """The paper's own experiment (Sec. 6) in its coordinates: R = [-10, 10]^2 x [1, 2] with M' = 51
     depths, Y = [-10, 10]^2 x [6, 7] with M = 51 planes, its ten point sources and model solution, 1e-4
     relative noise: truncated SVD (the paper's best regularising algorithm) and Tikhonov, alpha by the
     discrepancy principle; one graph replay per step, L2 flushed before each.  pad = 1: the periodic
     box at the timing example's n = 512; pad = 2: the zero-padded box of twice the side (data made by
     the aperiodic operator over R), n = 256 so that the box has the same 512 points.  Cold = kernel
-    transform + the per-class eigen tables of the first call."""
+    transform + the per-class eigen tables of the first call.  Precisions: FP32 (the per-class products
+    on CUDA cores) and, on the tensor cores, BF16X3 (split BF16) and BF16TC (plain BF16), each with its
+    xi against the FP32 one."""
     import torch
     from paper_1703_01216_gb300 import fr3d
     from paper_1703_01216_gb300 import inputs as I
@@ -610,11 +679,14 @@ def bench_paper_geometry(args, dev, flush, n=512, m=51, mp=51, n_alpha=32, pad=1
                        "(info bit 1) and the reconstruction error is the model error of zero padding (the oracle "
                        "gives the same at small n); this leg measures the padded path's speed")
     st = torch.cuda.current_stream(dev)
-    for name in ras:
+    pmap = {"fp32": fr3d.PREC_FP32, "bf16x3": fr3d.PREC_BF16X3, "bf16tc": fr3d.PREC_BF16TC}
+    ref32 = {}
+    for name, pname in [(r, p) for r in ras for p in precs]:
         ra = fr3d.RA_TSVD if name == "tsvd" else fr3d.RA_TIKHONOV
         idx = torch.zeros(1, dtype=torch.int32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
-        opts = fr3d.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx, info=info, ra=ra)
+        opts = fr3d.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, alpha_idx=idx, info=info, ra=ra,
+                         precision=pmap[pname])
         fr3d.invert(H, U, 1, out, opts)            # builds the eigen tables, tunes the fused variant
         torch.cuda.synchronize()
         if "cold_s" not in res:
@@ -639,10 +711,15 @@ def bench_paper_geometry(args, dev, flush, n=512, m=51, mp=51, n_alpha=32, pad=1
             b.synchronize()
             tot += a.elapsed_time(b)
         stages, _ = traced_stage_ms(fr3d, H, g_tr, flush, reps)
-        res[name] = {"value": n * n * mp * reps / (tot * 1e-3), "unit": "voxels/s", "ms_per_step": tot / reps,
-                     "stages_ms_per_step": {k: round(v / reps, 5) for k, v in stages.items()},
-                     "alpha_index": int(idx.item()), "info": int(info.item()), "launches": fr3d.last_launch_count(H),
-                     "rel_l2_vs_truth": round(float((out.double() - xi_true).norm() / xi_true.norm()), 4)}
+        key = name if pname == "fp32" else f"{name}_{pname}"
+        res[key] = {"value": n * n * mp * reps / (tot * 1e-3), "unit": "voxels/s", "ms_per_step": tot / reps,
+                    "stages_ms_per_step": {k: round(v / reps, 5) for k, v in stages.items()},
+                    "alpha_index": int(idx.item()), "info": int(info.item()), "launches": fr3d.last_launch_count(H),
+                    "rel_l2_vs_truth": round(float((out.double() - xi_true).norm() / xi_true.norm()), 4)}
+        if pname == "fp32":
+            ref32[name] = out.clone()
+        elif name in ref32:
+            res[key]["rel_l2_vs_fp32"] = round(rel_l2(out, ref32[name]), 7)
     return res
 
 
@@ -740,10 +817,13 @@ def run_reference(args):
         oracle_sample(w, A, U, delta, budget_bins=16)
     ests = []
     sample = None
+    walls = []
     for _ in range(args.steps):
         s = oracle_sample(w, A, U, delta, budget_bins=per_step)
         ests.append(s["seconds_per_step_est"])
+        walls.append(s["sample_wall_s"])
         sample = s["sample"]
+        scale = s["scale_factors"]
     sec = float(np.mean(ests))
     value = n * n * Mp / sec
     print(json.dumps({
@@ -752,8 +832,15 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "m_prime": Mp, "m": 1, "q_sources": Q, "n_alpha": int(w.alphas.size)},
-        "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+                         "estimated": True, "scale_factors": scale,
+                         "measured_sample_wall_s_per_step": round(float(np.mean(walls)), 3),
+                         "anchor": oracle_anchor()},
         "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "estimated": True,
+        "estimate": "value and ms_per_step extrapolate each step's measured sample (measured_sample_wall_s_per_step) "
+                    "by the scale factors; a whole oracle step at this size takes minutes; anchor: a full step at "
+                    "32x32x16 against the same kind of estimate",
     }))
 
 

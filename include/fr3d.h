@@ -70,6 +70,8 @@ extern "C" {
 #define FR3D_INFO_LEARNED_OUT_OF_RANGE 8 /* LEARNED: a band's predicted log10 alpha lay more than half a
                                             decade outside the candidate grid (the nearest end was used;
                                             the discrepancy rule is the fallback to run) */
+#define FR3D_INFO_TIMEOUT 16             /* a bounded device wait (tensor-core copy or MMA completion)
+                                            gave up: the outputs of this call are incomplete */
 
 /* ---- enums ---- */
 #define FR3D_K_DZ_INV_R 0 /* K = d/dz (1/r), Eq. (4) (the equation the paper solves) */
@@ -77,6 +79,13 @@ extern "C" {
                              z-derivative; the periodic box keeps every bin finite, including k = 0 */
 #define FR3D_PREC_FP32 0  /* FP32 FFTs, FP64 alpha rule; data and outputs are float */
 #define FR3D_PREC_FP64 1  /* FP64 throughout; data and outputs are double */
+#define FR3D_PREC_BF16TC 2 /* M > 1 only: as FP32, but the per-class dense products of Eq. (6) (projection
+                              onto the Gram eigenvectors, the solve, the forward operator) run on the
+                              tensor cores with BF16 tables and right-hand sides and FP32 accumulation;
+                              data and outputs are float.  Relative error per product ~ 2^-9. */
+#define FR3D_PREC_BF16X3 3 /* as BF16TC with every table and right-hand side split into two BF16 numbers
+                              (hi + lo) and three products (hi hi + hi lo + lo hi) per contraction:
+                              relative error per product ~ 2^-16 */
 #define FR3D_ALPHA_FIXED 0
 #define FR3D_ALPHA_DISCREPANCY 1
 #define FR3D_ALPHA_GIVEN 2        /* per-band indices into `alphas` supplied in alpha_idx (no sweep) */

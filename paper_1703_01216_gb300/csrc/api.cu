@@ -65,6 +65,14 @@ SrcHost src_host(const Handle* H, int precision, const fr3d_sources* s) {
 }
 
 bool valid_precision(int p) { return p == FR3D_PREC_FP32 || p == FR3D_PREC_FP64; }
+// the calls with per-class dense products (forward operator, alpha rule, inversion) also take the
+// tensor-core precisions, which exist for several observation depths only (M = 1 has no contraction)
+bool valid_contract_precision(int p) { return valid_precision(p) || tc_precision(p); }
+int check_tc(const Handle* H, int p, int Q) {
+  if (!tc_precision(p)) return FR3D_OK;
+  if (H->M < 2 || H->M > 64 || H->Mp > 64 || Q > tc_max_q()) return FR3D_ERR_UNSUPPORTED_SIZE;
+  return FR3D_OK;
+}
 
 // combination weights W_q = V0_q / sum_q' V0_q'^2 for the cached sources (rebuilt when they change)
 int ensure_wtab(Handle* H, const fr3d_sources* s, cudaStream_t st) {
@@ -105,6 +113,28 @@ int fwd_impl(Handle* H, const T* zeta, int Q, T* U, cudaStream_t st) {
     FR3D_TRY(Ops<T>::contract_fwd(H, Zh, Uh, A, 1, st));
     FR3D_TRY(Ops<T>::col_plain(H, Uh, Uh, H->M, true, st));
     FR3D_TRY(Ops<T>::row_c2r_plain(H, Uh, U + (long)q * H->M * n * n, H->M, 1, 0, 0, st));
+    launches += 5;
+  }
+  H->last_launches = launches;
+  return FR3D_OK;
+}
+
+// the forward operator with the per-class products on the tensor cores (M > 1)
+int fwd_impl_tc(Handle* H, const float* zeta, int Q, float* U, int precision, cudaStream_t st) {
+  const int n = H->n;
+  const long ps = (long)(n / 2 + 1) * n;
+  FR3D_TRY(ensure_tc_tables(H, 2, st));
+  const size_t zb = align_up(sizeof(float2) * ps * H->Mp), ub = align_up(sizeof(float2) * ps * H->M);
+  FR3D_TRY(ensure_ws(H, zb + ub));
+  float2* Zh = reinterpret_cast<float2*>(H->ws);
+  float2* Uh = reinterpret_cast<float2*>((char*)H->ws + zb);
+  int launches = 0;
+  for (int q = 0; q < Q; ++q) {
+    FR3D_TRY(Ops<float>::row_r2c(H, zeta + (long)q * H->Mp * n * n, (long)n * n, Zh, H->Mp, st));
+    FR3D_TRY(Ops<float>::col_plain(H, Zh, Zh, H->Mp, false, st));
+    FR3D_TRY(tc_forward(H, Zh, Uh, precision == FR3D_PREC_BF16X3, st));
+    FR3D_TRY(Ops<float>::col_plain(H, Uh, Uh, H->M, true, st));
+    FR3D_TRY(Ops<float>::row_c2r_plain(H, Uh, U + (long)q * H->M * n * n, H->M, 1, 0, 0, st));
     launches += 5;
   }
   H->last_launches = launches;
@@ -197,11 +227,12 @@ InvertPlan plan_invert(const Handle* H, int Q, bool host_io, int output) {
 
 int check_invert_args(Handle* H, int Q, const fr3d_invert_opts* o) {
   if (!o || Q < 1) return FR3D_ERR_INVALID_ARG;
-  if (!valid_precision(o->precision)) return FR3D_ERR_INVALID_ARG;
+  if (!valid_contract_precision(o->precision)) return FR3D_ERR_INVALID_ARG;
   if (H->M > FR3D_MAX_OBS_DEPTHS) return FR3D_ERR_UNSUPPORTED_SIZE;
+  FR3D_TRY(check_tc(H, o->precision, Q));
   if (H->M > 1) {
-    // several observation depths: FP32 path (eigen tables, multi.cu)
-    if (o->precision != FR3D_PREC_FP32) return FR3D_ERR_UNSUPPORTED_SIZE;
+    // several observation depths: FP32 data (eigen tables, multi.cu; products on CUDA or tensor cores)
+    if (o->precision == FR3D_PREC_FP64) return FR3D_ERR_UNSUPPORTED_SIZE;
     if (o->alpha_mode == FR3D_ALPHA_LEARNED) return FR3D_ERR_INVALID_ARG;
   }
   if (o->output != FR3D_OUT_XI && o->output != FR3D_OUT_ZETA) return FR3D_ERR_INVALID_ARG;
@@ -366,11 +397,13 @@ int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** U
 using fr3d::Handle;
 
 extern "C" int fr3d_fwd_apply(fr3d_handle* h, const void* zeta, int Q, void* U, int precision, void* stream) {
-  if (!h || !zeta || !U || Q < 1 || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  if (!h || !zeta || !U || Q < 1 || !fr3d::valid_contract_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  FR3D_TRY(fr3d::check_tc(h->padded ? &h->padded->h : &h->h, precision, 1));
   if (h->padded) return fr3d::padded_fwd_apply(h, zeta, Q, U, precision, (cudaStream_t)stream);
   Handle* H = &h->h;
   cudaStream_t st = (cudaStream_t)stream;
   if (precision == FR3D_PREC_FP64) return fr3d::fwd_impl<double>(H, (const double*)zeta, Q, (double*)U, st);
+  if (fr3d::tc_precision(precision)) return fr3d::fwd_impl_tc(H, (const float*)zeta, Q, (float*)U, precision, st);
   return fr3d::fwd_impl<float>(H, (const float*)zeta, Q, (float*)U, st);
 }
 
@@ -391,7 +424,8 @@ extern "C" int fr3d_zeta_from_xi(fr3d_handle* h, const void* xi, const fr3d_sour
 extern "C" int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const double* alphas, int n_alpha,
                                  double delta, double tau, int precision, int* alpha_idx, double* residuals,
                                  int* info, void* stream) {
-  if (!h || !U || Q < 1 || !alpha_idx || !fr3d::valid_precision(precision)) return FR3D_ERR_INVALID_ARG;
+  if (!h || !U || Q < 1 || !alpha_idx || !fr3d::valid_contract_precision(precision))
+    return FR3D_ERR_INVALID_ARG;
   FR3D_TRY(fr3d::check_alphas(alphas, n_alpha));
   if (h->padded)
     return fr3d::padded_choose_alpha(h, U, Q, alphas, n_alpha, delta, tau, precision, alpha_idx, residuals, info,
@@ -399,9 +433,11 @@ extern "C" int fr3d_choose_alpha(fr3d_handle* h, const void* U, int Q, const dou
   if (!(delta >= 0) || !isfinite(delta) || !(tau > 0) || !isfinite(tau)) return FR3D_ERR_INVALID_ARG;
   Handle* H = &h->h;
   cudaStream_t st = (cudaStream_t)stream;
+  FR3D_TRY(fr3d::check_tc(H, precision, Q));
   if (H->M > 1) {
-    if (H->M > FR3D_MAX_OBS_DEPTHS || precision != FR3D_PREC_FP32) return FR3D_ERR_UNSUPPORTED_SIZE;
-    return fr3d::choose_multi(H, (const float*)U, Q, alphas, n_alpha, delta, tau, alpha_idx, residuals, info, st);
+    if (H->M > FR3D_MAX_OBS_DEPTHS || precision == FR3D_PREC_FP64) return FR3D_ERR_UNSUPPORTED_SIZE;
+    return fr3d::choose_multi(H, (const float*)U, Q, alphas, n_alpha, delta, tau, precision, alpha_idx, residuals,
+                              info, st);
   }
   if (precision == FR3D_PREC_FP64)
     return fr3d::choose_impl<double>(H, (const double*)U, Q, alphas, n_alpha, delta, tau, alpha_idx, residuals,

@@ -97,6 +97,12 @@ struct Handle {
   float* mUt = nullptr;        // [C][k][i]: the eigenvectors (component i along observation depth k)
   float* mW = nullptr;         // [C][M][M']
   int m_sweeps = 0;            // Jacobi sweeps the slowest class needed
+  // tensor-core tables (tc_contract.cu), per kind (0 projection U^T, 1 solve W^T, 2 forward A): BF16
+  // class blobs in the MMA operand's shared-memory image, and the BF16 remainders (split mode)
+  uint16_t* tc_hi[3] = {nullptr, nullptr, nullptr};
+  uint16_t* tc_lo[3] = {nullptr, nullptr, nullptr};
+  int tc_blob[3] = {0, 0, 0};
+  int tc_kc[3] = {0, 0, 0};
   // right-hand side of Eq. (7): the handle of the box Pi's geometry (same grid, Pi's depths as the
   // unknown depths) and its buffers (density on Pi, integral term on Y)
   fr3d_handle* pi = nullptr;

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "classes.cuh"
 #include "fused.cuh"
 #include "ops.cuh"
 
@@ -27,13 +28,6 @@ namespace {
 
 constexpr int kMaxM = FR3D_MAX_OBS_DEPTHS;  // observation depths handled by the M > 1 path
 constexpr int kSweeps = 30;                // Jacobi sweep limit (convergence is checked every sweep)
-
-__device__ inline void class_pq_m(int c, int& p, int& q) {
-  p = (int)((sqrtf(8.f * (float)c + 1.f) - 1.f) * 0.5f);
-  while ((p + 1) * (p + 2) / 2 <= c) ++p;
-  while (p * (p + 1) / 2 > c) --p;
-  q = c - p * (p + 1) / 2;
-}
 
 // One CTA per class.  Shared memory: G [Me][Me], U [Me][Me] (Me = M rounded up to even), FP64.
 __global__ void __launch_bounds__(256) k_class_eig(const double* __restrict__ A64, int M, int Mp, int Cn,
@@ -153,21 +147,6 @@ __global__ void __launch_bounds__(256) k_class_eig(const double* __restrict__ A6
     W[(long)c * M * Mp + e] = (float)s;
   }
   if (tid == 0 && sweeps_out) atomicMax(sweeps_out, sweep);
-}
-
-// members (kx, ky) of class c in the stored half spectrum and their weights (1 on the kx = 0 and
-// kx = n/2 rows, whose mirror bins are stored too, 2 elsewhere)
-__device__ inline int class_members(int c, int n, int* kxs, int* kys, float* wts) {
-  int p, q, nm = 0;
-  class_pq_m(c, p, q);
-  kxs[nm] = p; kys[nm++] = q;
-  if (q != 0 && 2 * q != n) { kxs[nm] = p; kys[nm++] = n - q; }
-  if (p != q) {
-    kxs[nm] = q; kys[nm++] = p;
-    if (p != 0 && 2 * p != n) { kxs[nm] = q; kys[nm++] = n - p; }
-  }
-  for (int m = 0; m < nm; ++m) wts[m] = (kxs[m] == 0 || 2 * kxs[m] == n) ? 1.f : 2.f;
-  return nm;
 }
 
 // Projection p = U_c^T U~ in place for every member bin and plane set q, and the class powers
@@ -326,7 +305,8 @@ struct MThr {
 };
 __global__ void __launch_bounds__(256) k_alpha_m_finish(const double* __restrict__ partials, int nblk, int nb, int na,
                                                         double inv_n2, MThr thr, int* __restrict__ aidx,
-                                                        double* __restrict__ res_out, int* __restrict__ info) {
+                                                        double* __restrict__ res_out, int* __restrict__ info,
+                                                        int keep) {
   __shared__ double r2[FR3D_MAX_BANDS * FR3D_MAX_ALPHAS];
   __shared__ int flg[FR3D_MAX_BANDS];
   const int tid = threadIdx.x, O = nb * na;
@@ -368,7 +348,7 @@ __global__ void __launch_bounds__(256) k_alpha_m_finish(const double* __restrict
   if (tid == 0) {
     int flags = 0;
     for (int b = 0; b < nb; ++b) flags |= flg[b];
-    if (info) *info = flags;
+    if (info) *info = flags | (*info & keep);   // keep: bits set earlier in this call (cleared at its start)
   }
 }
 
@@ -546,21 +526,26 @@ int multi_ws(Handle* H, int Q, bool with_zs, MultiWs* w) {
 }
 
 // data spectra of every (q, i) plane and their projection onto the class eigenvectors
-int multi_data(Handle* H, const float* U, int Q, const MultiWs& w, int* launches, cudaStream_t st) {
+int multi_data(Handle* H, const float* U, int Q, const MultiWs& w, int precision, int* info, int* launches,
+               cudaStream_t st) {
   const long ps = (long)(H->n / 2 + 1) * H->n;
   FR3D_TRY(Ops<float>::row_r2c(H, U, (long)H->n * H->n, w.Uh, Q * H->M, st));
   prof_mark(H, kStRowR2C, st);
   FR3D_TRY(Ops<float>::col_plain(H, w.Uh, w.Uh, Q * H->M, false, st));
   prof_mark(H, kStColFwd, st);
-  k_project<<<(H->C + kPerCta - 1) / kPerCta, 32 * kPerCta, 0, st>>>(w.Uh, ps, Q, H->M, H->n, H->C, H->mUt, w.Pc);
-  FR3D_CUDA_TRY(cudaGetLastError());
+  if (tc_precision(precision)) {
+    FR3D_TRY(tc_project(H, w.Uh, Q, w.Pc, precision == FR3D_PREC_BF16X3, info, st));
+  } else {
+    k_project<<<(H->C + kPerCta - 1) / kPerCta, 32 * kPerCta, 0, st>>>(w.Uh, ps, Q, H->M, H->n, H->C, H->mUt, w.Pc);
+    FR3D_CUDA_TRY(cudaGetLastError());
+  }
   prof_mark(H, kStOther, st);
   *launches += 3;
   return FR3D_OK;
 }
 
 int multi_alpha(Handle* H, const MultiWs& w, const double* alphas, int na, int ra, int nb, const double* thr2,
-                int* aidx, double* residuals, int* info, cudaStream_t st) {
+                int* aidx, double* residuals, int* info, int keep, cudaStream_t st) {
   FR3D_TRY(ensure_partials(H));
   MAlphas al;
   for (int k = 0; k < na; ++k) al.a[k] = alphas[k];
@@ -569,7 +554,7 @@ int multi_alpha(Handle* H, const MultiWs& w, const double* alphas, int na, int r
   MThr t;
   for (int b = 0; b < nb; ++b) t.t[b] = thr2[b];
   k_alpha_m_finish<<<1, 256, 0, st>>>(H->partials, nblk, nb, na, 1.0 / ((double)H->n * H->n), t, aidx, residuals,
-                                      info);
+                                      info, keep);
   FR3D_CUDA_TRY(cudaGetLastError());
   prof_mark(H, kStAlpha, st);
   return FR3D_OK;
@@ -587,37 +572,53 @@ int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, fl
   FR3D_TRY(ensure_bands(H, nb, &count));
   MultiWs w;
   FR3D_TRY(multi_ws(H, Q, true, &w));
+  const bool tcp = tc_precision(o->precision);
+  if (tcp) {
+    FR3D_TRY(ensure_tc_tables(H, 0, st));
+    FR3D_TRY(ensure_tc_tables(H, 1, st));
+  }
   int launches = 0;
   prof_begin(H, st);
-  FR3D_TRY(multi_data(H, U, Q, w, &launches, st));
+  // the tensor-core kernels OR a time-out bit into info: clear it first
+  if (tcp && o->info) {
+    FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
+    ++launches;
+  }
+  FR3D_TRY(multi_data(H, U, Q, w, o->precision, o->info, &launches, st));
   MAlphas al;
   const int* aidx;
   if (o->alpha_mode == FR3D_ALPHA_FIXED) {
     al.a[0] = o->alpha;
     aidx = H->zero_idx;
     if (o->alpha_idx) FR3D_CUDA_TRY(cudaMemsetAsync(o->alpha_idx, 0, sizeof(int), st));
-    if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
+    if (o->info && !tcp) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
   } else {
     for (int k = 0; k < o->n_alpha; ++k) al.a[k] = o->alphas[k];
     if (o->alpha_mode == FR3D_ALPHA_DISCREPANCY) {
       int* idx = o->alpha_idx ? o->alpha_idx : H->idx_scratch;
       double thr2[FR3D_MAX_BANDS];
       band_thresholds(H, o, nb, thr2);
-      FR3D_TRY(multi_alpha(H, w, o->alphas, o->n_alpha, o->ra, nb, thr2, idx, o->residuals, o->info, st));
+      FR3D_TRY(multi_alpha(H, w, o->alphas, o->n_alpha, o->ra, nb, thr2, idx, o->residuals, o->info,
+                           tcp ? FR3D_INFO_TIMEOUT : 0, st));
       launches += 2;
       aidx = idx;
     } else {
       aidx = o->alpha_idx;
-      if (o->info) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
+      if (o->info && !tcp) FR3D_CUDA_TRY(cudaMemsetAsync(o->info, 0, sizeof(int), st));
     }
   }
   const long ps = (long)(H->n / 2 + 1) * H->n;
   const int na = o->alpha_mode == FR3D_ALPHA_FIXED ? 1 : o->n_alpha;
   const bool fused = fused_supported(H->n);
-  k_solve_m<<<(H->C + kPerCta - 1) / kPerCta, 32 * kPerCta, 0, st>>>(
-      w.Uh, ps, Q, H->M, H->Mp, H->n, H->C, H->mlam, H->mW, H->cband, nb, aidx, na, al, H->s2, o->ra,
-      1.0 / ((double)H->n * H->n), w.Zs, fused ? 0 : 1);
-  FR3D_CUDA_TRY(cudaGetLastError());
+  if (tcp) {
+    FR3D_TRY(tc_solve(H, w.Uh, Q, aidx, al.a, na, o->ra, nb, w.Zs, fused ? 0 : 1, o->precision == FR3D_PREC_BF16X3,
+                      o->info, st));
+  } else {
+    k_solve_m<<<(H->C + kPerCta - 1) / kPerCta, 32 * kPerCta, 0, st>>>(
+        w.Uh, ps, Q, H->M, H->Mp, H->n, H->C, H->mlam, H->mW, H->cband, nb, aidx, na, al, H->s2, o->ra,
+        1.0 / ((double)H->n * H->n), w.Zs, fused ? 0 : 1);
+    FR3D_CUDA_TRY(cudaGetLastError());
+  }
   prof_mark(H, kStColSolve, st);
   if (fused) {
     FR3D_TRY(inv_fused_presolved_f32(H, w.Zs, H->wtab, out, Q, o->output, st));
@@ -640,16 +641,23 @@ int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, fl
 
 // Discrepancy choice alone for M > 1 (fr3d_choose_alpha): data FFT, projection, residual sums.
 int choose_multi(Handle* H, const float* U, int Q, const double* alphas, int na, double delta, double tau,
-                 int* aidx, double* residuals, int* info, cudaStream_t st) {
+                 int precision, int* aidx, double* residuals, int* info, cudaStream_t st) {
   FR3D_TRY(ensure_multi_tables(H, st));
   FR3D_TRY(ensure_bands(H, 1, nullptr));
+  const bool tcp = tc_precision(precision);
+  if (tcp) FR3D_TRY(ensure_tc_tables(H, 0, st));
   MultiWs w;
   FR3D_TRY(multi_ws(H, Q, false, &w));
   int launches = 0;
   prof_begin(H, st);
-  FR3D_TRY(multi_data(H, U, Q, w, &launches, st));
+  if (tcp && info) {
+    FR3D_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
+    ++launches;
+  }
+  FR3D_TRY(multi_data(H, U, Q, w, precision, info, &launches, st));
   const double thr2 = (tau * delta) * (tau * delta);
-  FR3D_TRY(multi_alpha(H, w, alphas, na, FR3D_RA_TIKHONOV, 1, &thr2, aidx, residuals, info, st));
+  FR3D_TRY(multi_alpha(H, w, alphas, na, FR3D_RA_TIKHONOV, 1, &thr2, aidx, residuals, info,
+                       tcp ? FR3D_INFO_TIMEOUT : 0, st));
   H->last_launches = launches + 2;
   return FR3D_OK;
 }

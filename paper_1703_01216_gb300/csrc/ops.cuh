@@ -68,12 +68,22 @@ size_t multi_ws_bytes(const Handle* H, int Q);
 // src: the point sources of the combination (XI output; used at sizes without the fused inverse)
 int invert_multi(Handle* H, const float* U, int Q, const fr3d_invert_opts* o, float* out, const SrcHost& src,
                  cudaStream_t st);
-int choose_multi(Handle* H, const float* U, int Q, const double* alphas, int na, double delta, double tau, int* aidx,
-                 double* residuals, int* info, cudaStream_t st);
+int choose_multi(Handle* H, const float* U, int Q, const double* alphas, int na, double delta, double tau,
+                 int precision, int* aidx, double* residuals, int* info, cudaStream_t st);
 void band_thresholds(const Handle* H, const fr3d_invert_opts* o, int nb, double* thr2);
 // fused inverse DFT + combination of already solved spectra Zs [Q][M'][n/2+1][n] (1/n^2 folded in)
 int inv_fused_presolved_f32(const Handle* H, const float2* Zs, const float* W, float* out, int Q, int output,
                             cudaStream_t st);
+
+// per-class dense products on the tensor cores (tc_contract.cu; M > 1, BF16 operands, FP32 accumulation;
+// split = the hi + lo form of FR3D_PREC_BF16X3)
+bool tc_precision(int precision);
+int tc_max_q();
+int ensure_tc_tables(Handle* H, int kind, cudaStream_t st);
+int tc_project(Handle* H, float2* Uh, int Q, double* Pc, bool split, int* info, cudaStream_t st);
+int tc_solve(Handle* H, const float2* P, int Q, const int* aidx, const double* alphas, int na, int ra, int nb,
+             float2* Zs, int jq, bool split, int* info, cudaStream_t st);
+int tc_forward(Handle* H, const float2* Zh, float2* Uh, bool split, cudaStream_t st);
 
 // right-hand side of Eq. (7) (rhs.cu): the density sum_l 1/|x' - x_l| on the box Pi, and the combination
 // U = 2 pi d + (A2 / 2) sum_l d/dx3 (1/|x - x_l|) - coef I on the observation grid

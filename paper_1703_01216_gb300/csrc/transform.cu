@@ -299,6 +299,10 @@ void handle_free(Handle* H) {
                   H->info_scratch, H->partials, H->cband, H->bbin, H->mlam, H->mUt, H->mW, H->rhs_buf, H->ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int k = 0; k < 3; ++k) {
+    if (H->tc_hi[k]) cudaFree(H->tc_hi[k]);
+    if (H->tc_lo[k]) cudaFree(H->tc_lo[k]);
+  }
   for (int i = 0; i < Handle::kMaxEv; ++i)
     if (H->ev[i]) cudaEventDestroy(H->ev[i]);
   if (H->pi) fr3d_handle_destroy(H->pi);

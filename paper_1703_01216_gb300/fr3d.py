@@ -17,12 +17,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libfr3d.so")
 
 OK = 0
-PREC_FP32, PREC_FP64 = 0, 1
+PREC_FP32, PREC_FP64, PREC_BF16TC, PREC_BF16X3 = 0, 1, 2, 3
 ALPHA_FIXED, ALPHA_DISCREPANCY, ALPHA_GIVEN, ALPHA_LEARNED = 0, 1, 2, 3
 MAX_BANDS = 16
 OUT_ZETA, OUT_XI = 0, 1
 RA_TIKHONOV, RA_TSVD = 0, 1
 INFO_ALPHA_NONE_SATISFIES, INFO_ALPHA_ALL_SATISFY, INFO_NONFINITE, INFO_LEARNED_OUT_OF_RANGE = 1, 2, 4, 8
+INFO_TIMEOUT = 16
 MAX_HIDDEN = 96
 K_DZ_INV_R, K_INV_R = 0, 1
 MAX_ALPHAS = 128
