@@ -50,6 +50,9 @@ def parse():
                     help="force the fused inverse's tile variant (default: autotuned on the first call)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg at the same workload")
+    ap.add_argument("--no-unet", action="store_true", help="skip the U-Net post-corrector leg")
+    ap.add_argument("--unet-pairs", type=int, default=20000, help="training pairs of the U-Net leg")
+    ap.add_argument("--unet-held-out", type=int, default=1000, help="held-out seeds of the U-Net leg")
     ap.add_argument("--no-paper-geometry", action="store_true", help="skip the M = M' = 51 leg")
     return ap.parse_args()
 
@@ -477,6 +480,8 @@ def run_fr3d(args):
     result["clocks"] = clocks
     if not args.no_fp64:
         result["fp64"] = bench_fp64(args, dev, flush, w, H, U, delta, out)
+    if rank == 0 and not args.no_unet:
+        result["learned_unet"] = bench_unet(args, dev, flush, pairs=args.unet_pairs, held_out=args.unet_held_out)
     if not args.no_learned:
         result["learned"] = bench_learned(args, dev, flush, w, H, U, delta, rel_truth, dist, xi_proj=xi_proj,
                                           plain_rel_proj=rel_proj)
@@ -647,6 +652,78 @@ def bench_fp64(args, dev, flush, w, H, U, delta, out32):
     return {"value": n * n * Mp / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": round(ms, 5), "steps": steps,
             "dtype": "f64", "launches_per_step": launches, "alpha_index": int(idx.item()),
             "rel_l2_fp32_vs_fp64": round(rel_l2(out32, out), 8)}
+
+
+def bench_unet(args, dev, flush, pairs=20000, held_out=1000, batch=8):
+    """The learned post-corrector of the learned configuration: a 4-level 3D U-Net (base width 16,
+    1 902 081 parameters, BF16 tensor-core kernels with FP32 accumulation) trained on ``pairs`` fresh
+    seeded pairs at 128 x 128 x 32 (1-12 Gaussian/ellipsoidal inclusions, 0.5-5 % noise, one source,
+    the plain discrepancy inversion as its input) and evaluated on ``held_out`` seeds against the plain
+    inversion's error; both paths timed per volume (the plain one as one CUDA graph replay, the learned
+    one as the same replay plus the network's forward pass), L2 flushed before each."""
+    import torch
+    from paper_1703_01216_gb300 import fr3d
+    from paper_1703_01216_gb300 import inputs as I
+    from paper_1703_01216_gb300 import postcorrect as PC
+    w = I.make_workload(128, 32, q=1, n_alpha=32, seed=5000, noise_level=0.02)
+    stream = PC.PairStream.create(w, dev)
+    # input scale: the plain reconstructions' RMS on a few training samples, so the network sees O(1)
+    x = torch.empty((batch, 32, 128, 128), device=dev)
+    t = torch.empty_like(x)
+    stream.batch(10_000_000, batch, x, t)
+    in_scale = float(1.0 / max(float(x.pow(2).mean().sqrt()), 1e-6))
+    net = fr3d.Unet(32, 128, 128, batch, in_scale=in_scale, seed=5)
+    t0 = time.perf_counter()
+    hist, t_gen, t_net = PC.train(net, stream, pairs=pairs, batch=batch, seed=100_000, lr=1e-3, lr_final=1e-4,
+                                  log_every=250)
+    t_train = time.perf_counter() - t0
+    plain, learned = PC.evaluate(net, stream, held_out, seed=900_000, batch=batch)
+    # per-volume times: plain inversion (graph replay) and the network's forward pass on a batch
+    H = stream.H
+    xi = torch.empty((32, 128, 128), device=dev)
+    U = torch.empty((1, 1, 128, 128), device=dev)
+    zeta = torch.empty((1, 32, 128, 128), device=dev)
+    fr3d.zeta_from_xi(H, t[0], stream.points, zeta)
+    fr3d.fwd_apply(H, zeta, 1, U)
+    opts = fr3d.Opts(alphas=stream.alphas, delta=float(0.02 * U.norm()), tau=1.1, points=stream.points)
+    st = torch.cuda.current_stream(dev)
+    fr3d.invert(H, U, 1, xi, opts)
+    torch.cuda.synchronize()
+    g = capture_step(fr3d, H, dev, st, lambda: fr3d.invert(H, U, 1, xi, opts), False)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        g.replay()
+        net.forward(x, y)
+    torch.cuda.synchronize()
+    reps = max(5, min(args.steps, 20))
+    t_inv = t_fwd = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(st)
+        g.replay()
+        b.record(st)
+        net.forward(x, y)
+        c.record(st)
+        c.synchronize()
+        t_inv += a.elapsed_time(b)
+        t_fwd += b.elapsed_time(c)
+    ms_inv = t_inv / reps
+    ms_net = t_fwd / reps / batch
+    vox = 128 * 128 * 32
+    return {"workload": "128^2 x 32, one source, 1-12 inclusions, 0.5-5 % noise, 32 alphas (learned configuration)",
+            "params": net.n_params, "pairs_trained": (pairs // batch) * batch, "held_out": held_out, "batch": batch,
+            "in_scale": round(in_scale, 4), "train_s": round(t_train, 1), "pair_gen_s": round(t_gen, 1),
+            "net_train_s": round(t_net, 1), "pairs_per_s": round((pairs // batch) * batch / t_gen, 1),
+            "loss_history": [round(v, 4) for v in hist],
+            "rel_l2_vs_truth": {"plain_mean": round(float(np.mean(plain)), 4), "plain_std": round(float(np.std(plain)), 4),
+                                "learned_mean": round(float(np.mean(learned)), 4),
+                                "learned_std": round(float(np.std(learned)), 4),
+                                "learned_better_fraction": round(float(np.mean(learned < plain)), 3)},
+            "plain": {"ms_per_volume": round(ms_inv, 5), "voxels_per_s": vox / (ms_inv * 1e-3)},
+            "learned": {"ms_per_volume": round(ms_inv + ms_net, 5), "net_ms_per_volume": round(ms_net, 5),
+                        "voxels_per_s": vox / ((ms_inv + ms_net) * 1e-3)},
+            "flags": net.error_flags()}
 
 
 def bench_paper_geometry(args, dev, flush, n=512, m=51, mp=51, n_alpha=32, pad=1, ras=("tsvd", "tikhonov"),

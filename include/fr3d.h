@@ -308,6 +308,43 @@ int fr3d_autotune_mode(int mode);
  * times the tuner measured on this handle (0 if it did not tune here).  Returns the variant count. */
 int fr3d_autotune_query(fr3d_handle* h, int* variant, float* ms, int cap);
 
+/* ---- learned post-corrector: a 3D U-Net on the tensor cores (fr3d_unet) ----
+ * The paper has no network.  This one post-corrects the reconstruction of fr3d_invert: with one observation
+ * plane each frequency's system has rank one, so the regularised normal solution (Assumption U, Sec. 4)
+ * keeps one depth direction per frequency, and a network trained on examples from the same forward
+ * operator restores the others.  Architecture (4 levels, widths 16, 32, 64, 128; 1 902 081 parameters):
+ * level 0 conv(1 -> 16), conv(16 -> 16); levels 1, 2: 2x average pooling, conv(w_{l-1} -> w_l), conv(w_l -> w_l);
+ * level 3: pooling and three conv to 128; going up, 2x nearest upsampling concatenated (channels first)
+ * with the encoder output of the level, conv(w_{l+1} + w_l -> w_l), conv(w_l -> w_l); every conv 3 x 3 x 3 with
+ * zero padding, bias and leaky ReLU (slope 0.01); a 1 x 1 x 1 head 16 -> 1 added to the input:
+ *     y = x + head(...),   with x = in_scale * xi_in and the prediction y / in_scale.
+ * Loss: the batch mean of ||y - t||^2 / ||t||^2 (the squared relative L2 error).  Convolutions and their
+ * gradients run on the tensor cores with BF16 weights and activations and FP32 accumulation; the update is
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master parameters.  Parameters in one flat vector, per
+ * conv layer in the order above w [co][ci][3][3][3] then b [co], then the head w [16] and b [1].
+ * Volumes: device FP32 [B][depth][height][width] (x fastest); depth, height and width multiples of 8
+ * (three poolings), depth <= 256, height, width <= 512; 1 <= B <= max_batch.  The network owns its
+ * activation buffers for max_batch samples (about 330 MB per sample at 32 x 128 x 128); one network serves
+ * one stream at a time.  A bounded device wait that gives up sets FR3D_INFO_TIMEOUT in the flags
+ * fr3d_unet_error_flags reads (synchronous). */
+typedef struct fr3d_unet fr3d_unet;
+int fr3d_unet_create(int depth, int height, int width, int max_batch, float in_scale, unsigned long long seed,
+                     fr3d_unet** out);   /* He-normal conv weights from SplitMix64(seed), zero biases and head
+                                            (the initial network is the identity); synchronous */
+void fr3d_unet_destroy(fr3d_unet* net);
+int fr3d_unet_query(const fr3d_unet* net, int* n_params);
+int fr3d_unet_get_params(fr3d_unet* net, float* params);        /* host [n_params]; synchronous */
+int fr3d_unet_set_params(fr3d_unet* net, const float* params);  /* host [n_params]; resets Adam; synchronous */
+/* y: device [B][depth][height][width], the corrected volume (caller's units) */
+int fr3d_unet_forward(fr3d_unet* net, const float* x, int B, float* y, void* stream);
+/* loss (device float, or NULL) and gradient (device float[n_params], or NULL) for inputs x and targets t */
+int fr3d_unet_gradient(fr3d_unet* net, const float* x, const float* t, int B, float* grad, float* loss,
+                       void* stream);
+/* gradient + one Adam step with learning rate lr */
+int fr3d_unet_train_step(fr3d_unet* net, const float* x, const float* t, int B, float lr, float* loss,
+                         void* stream);
+int fr3d_unet_error_flags(fr3d_unet* net, int* flags);
+
 /* Right-hand side of Eq. (7) (the form Eq. (3) takes for point sources, Sec. 6) from the measured
  * z-derivative of V2 on the observation depths:
  *     U_q = 2 pi dV2/dx3 + (A2 / 2) sum_l d/dx3 (1/|x - x_{q,l}|)

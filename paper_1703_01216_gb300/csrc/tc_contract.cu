@@ -79,7 +79,7 @@ __host__ __device__ inline TcLayout tc_layout(int Kc, int Q) {
   L.sboB = L.KcB * 128;
   L.bRegion = (L.N / 8) * L.sboB;
   int c = 32;
-  while (c < L.N) c <<= 1;
+  while (c < 2 * L.N) c <<= 1;   // two accumulators (consecutive pairs)
   L.ncols_tmem = c;
   return L;
 }
@@ -99,28 +99,50 @@ __device__ __forceinline__ int cm_off(int row, int col, int chunks) {
   return ((row >> 3) * chunks + (col >> 3)) * 128 + (row & 7) * 16 + (col & 7) * 2;
 }
 
+// Pipeline of one CTA over its pairs j (pair blockIdx.x + j gridDim.x), stage j % kTcStages, TMEM
+// accumulator j % 2:
+//   thread 0: wait for pair j's tables, issue its MMAs, commit; then request the tables of pair
+//             j + kTcStages - 1 into the stage that pair j - 1 used (its MMAs completed before its epilogue);
+//   all:      class members of pair j + 1, gather and round its right-hand sides into its stage (the loads
+//             of a thread issued together), while pair j's MMAs run;
+//   all:      wait for pair j's MMAs, read the accumulator (one output row per thread) and scatter it.
+constexpr int kTcStages = 2;
+constexpr int kGatherUnroll = 4;
+
+struct PairInfo {
+  long bin[2][4];
+  float wt[2][4];
+  int nm[2], cls[2];
+};
+
+__device__ __forceinline__ int tc_flag(const int* f) { return *reinterpret_cast<const volatile int*>(f); }
+
 template <bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads) k_tc_contract(TcArgs a, TcAlphas al) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ __align__(8) uint64_t bar_tma[kTcStages], bar_mma[2];
   __shared__ uint32_t tbase;
   __shared__ int sbad;
-  __shared__ long sbin[2][4];
-  __shared__ float swt[2][4];
-  __shared__ int snm[2], scls[2];
-  __shared__ float gsc[2][64];
+  __shared__ PairInfo info[kTcStages];
+  __shared__ int sidx[FR3D_MAX_BANDS];
   const TcLayout L = tc_layout(a.Kc, a.Q);
-  unsigned char* sA[2] = {sm, sm + L.aRegion};
-  unsigned char* sB[2] = {sm + (SPLIT ? 2 : 1) * L.aRegion, sm + (SPLIT ? 2 : 1) * L.aRegion + L.bRegion};
+  const int stage_bytes = (SPLIT ? 2 : 1) * (L.aRegion + L.bRegion);
+  auto sA = [&](int st, int h) { return sm + (size_t)st * stage_bytes + h * L.aRegion; };
+  auto sB = [&](int st, int h) { return sm + (size_t)st * stage_bytes + (SPLIT ? 2 : 1) * L.aRegion + h * L.bRegion; };
   const int tid = threadIdx.x, warp = tid >> 5;
-  // zero the table regions once: the rows past R, the chunks past K and the tail are never copied and
-  // must hold finite values (they meet zero right-hand-side entries or feed discarded rows)
-  for (int e = tid; e < (SPLIT ? 2 : 1) * L.aRegion / 16; e += kTcThreads)
+  const int npairs = (a.C + 1) / 2;
+  const int nloc = blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto pair_of = [&](int j) { return (int)blockIdx.x + j * (int)gridDim.x; };
+  // zero every table region once: rows past R, chunks past K and the tail are never copied
+  for (int e = tid; e < kTcStages * stage_bytes / 16; e += kTcThreads)
     reinterpret_cast<uint4*>(sm)[e] = make_uint4(0, 0, 0, 0);
-  tc::fence_proxy_async();   // the zeros are ordered before the bulk copies into the same region
+  tc::fence_proxy_async();   // the zeros are ordered before the bulk copies into the same regions
+  if (a.scale == kScaleSolve)
+    for (int b = tid; b < max(a.nb, 1); b += kTcThreads) sidx[b] = min(max(a.aidx[b], 0), a.na - 1);
   if (tid == 0) {
-    tc::mbar_init(&bar_tma, 1);
-    tc::mbar_init(&bar_mma, 1);
+    for (int st = 0; st < kTcStages; ++st) tc::mbar_init(&bar_tma[st], 1);
+    tc::mbar_init(&bar_mma[0], 1);
+    tc::mbar_init(&bar_mma[1], 1);
     tc::mbar_fence_init();
     sbad = 0;
   }
@@ -129,127 +151,156 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_contract(TcArgs a, TcAlphas a
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tbase;
-  const int npairs = (a.C + 1) / 2;
   const uint32_t idesc = tc::idesc_bf16(128, L.N);
-  uint32_t phase = 0;
-  for (int pair = blockIdx.x; pair < npairs; pair += gridDim.x, phase ^= 1u) {
-    // class tables of the pair: one bulk copy per class (and per split half)
+
+  auto request_tables = [&](int j) {   // thread 0
+    const int st = j % kTcStages, pair = pair_of(j);
+    const int nv = (2 * pair + 1 < a.C) ? 2 : 1;
+    tc::mbar_arrive_expect_tx(&bar_tma[st], (uint32_t)(nv * a.blob * (SPLIT ? 2 : 1)));
+    for (int s = 0; s < nv; ++s) {
+      const long c = 2L * pair + s;
+      tc::bulk_g2s(sA(st, 0) + s * 8 * L.sboA, reinterpret_cast<const unsigned char*>(a.hi) + c * a.blob,
+                   (uint32_t)a.blob, &bar_tma[st]);
+      if (SPLIT)
+        tc::bulk_g2s(sA(st, 1) + s * 8 * L.sboA, reinterpret_cast<const unsigned char*>(a.lo) + c * a.blob,
+                     (uint32_t)a.blob, &bar_tma[st]);
+    }
+  };
+  auto set_info = [&](int j) {         // threads 0 and 1: the classes of pair j and their member bins
     if (tid < 2) {
-      const int c = 2 * pair + tid;
-      scls[tid] = c < a.C ? c : -1;
+      PairInfo& I = info[j % kTcStages];
+      const int c = 2 * pair_of(j) + tid;
+      I.cls[tid] = c < a.C ? c : -1;
       int kxs[4], kys[4];
       float wts[4];
       int nm = 0;
       if (c < a.C) nm = class_members(c, a.n, kxs, kys, wts);
-      snm[tid] = nm;
+      I.nm[tid] = nm;
       for (int m = 0; m < 4; ++m) {
-        sbin[tid][m] = m < nm ? (long)kxs[m] * a.n + kys[m] : 0;
-        swt[tid][m] = m < nm ? wts[m] : 0.f;
+        I.bin[tid][m] = m < nm ? (long)kxs[m] * a.n + kys[m] : 0;
+        I.wt[tid][m] = m < nm ? wts[m] : 0.f;
       }
     }
-    if (tid == 0) {
-      const int nv = (2 * pair + 1 < a.C) ? 2 : 1;
-      tc::mbar_arrive_expect_tx(&bar_tma, (uint32_t)(nv * a.blob * (SPLIT ? 2 : 1)));
-      for (int s = 0; s < nv; ++s) {
-        const long c = 2L * pair + s;
-        unsigned char* dst = sA[0] + s * 8 * L.sboA;
-        tc::bulk_g2s(dst, reinterpret_cast<const unsigned char*>(a.hi) + c * a.blob, (uint32_t)a.blob, &bar_tma);
-        if (SPLIT)
-          tc::bulk_g2s(sA[1] + s * 8 * L.sboA, reinterpret_cast<const unsigned char*>(a.lo) + c * a.blob,
-                       (uint32_t)a.blob, &bar_tma);
-      }
-    }
-    __syncthreads();
-    // per-class scaling of the right-hand sides
-    if (a.scale == kScaleSolve) {
-      for (int e = tid; e < 2 * a.K; e += kTcThreads) {
-        const int s = e / a.K, k = e - s * a.K, c = scls[s];
-        float g = 0.f;
-        if (c >= 0) {
-          const int ki = min(max(a.aidx[a.nb > 1 ? (int)a.cband[c] : 0], 0), a.na - 1);
-          const double t = al.a[ki] * (*a.s2);
-          const double l = a.lam[(long)c * a.K + k];
-          float gi;
-          if (a.ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? __frcp_rn((float)l) : 0.f;
-          else gi = __frcp_rn((float)(l + t));
-          g = gi * a.inv_n2;
-        }
-        gsc[s][k] = g;
-      }
-      __syncthreads();
-    }
-    // B operand: column (slot s, q, member m, re/im), contraction index k; zeros outside the data
-    {
-      const int kpad = 8 * L.KcB;
-      const int total = 2 * a.Q * kpad * 4;
-      for (int e = tid; e < total; e += kTcThreads) {
+  };
+  // B operand of pair j: column (slot s, q, member m, re/im), contraction index k; zeros outside the data
+  auto gather = [&](int j) {
+    const int st = j % kTcStages;
+    const PairInfo& I = info[st];
+    const int kpad = 8 * L.KcB;
+    const int total = 2 * a.Q * kpad * 4;
+    for (int e0 = 0; e0 < total; e0 += kTcThreads * kGatherUnroll) {
+      float2 v[kGatherUnroll];
+      double lv[kGatherUnroll];
+      int kk[kGatherUnroll], col[kGatherUnroll], sl[kGatherUnroll];
+      bool live[kGatherUnroll], inb[kGatherUnroll];
+#pragma unroll
+      for (int u = 0; u < kGatherUnroll; ++u) {
+        const int e = e0 + u * kTcThreads + tid;
+        inb[u] = e < total;
         const int m = e & 3;
         int rest = e >> 2;
         const int k = rest % kpad;
         rest /= kpad;
         const int q = rest % a.Q, s = rest / a.Q;
-        float2 v = make_float2(0.f, 0.f);
-        if (scls[s] >= 0 && k < a.K && m < snm[s]) {
-          v = a.in[((long)q * a.K + k) * a.ps + sbin[s][m]];
-          const float f = a.scale == kScaleSolve ? gsc[s][k] : (a.scale == kScaleConst ? a.cscale : 1.f);
-          v.x *= f;
-          v.y *= f;
+        kk[u] = k;
+        sl[u] = s;
+        col[u] = s * L.ncolc + q * 8 + 2 * m;
+        live[u] = inb[u] && I.cls[s] >= 0 && k < a.K && m < I.nm[s];
+        v[u] = make_float2(0.f, 0.f);
+        lv[u] = 0.0;
+        if (live[u]) {
+          v[u] = __ldg(a.in + ((long)q * a.K + k) * a.ps + I.bin[s][m]);
+          if (a.scale == kScaleSolve) lv[u] = __ldg(a.lam + (long)I.cls[s] * a.K + k);
         }
-        const int col = s * L.ncolc + q * 8 + 2 * m;
-        const uint16_t hx = tc::bf16_rn(v.x), hy = tc::bf16_rn(v.y);
-        *reinterpret_cast<uint16_t*>(sB[0] + cm_off(col, k, L.KcB)) = hx;
-        *reinterpret_cast<uint16_t*>(sB[0] + cm_off(col + 1, k, L.KcB)) = hy;
+      }
+#pragma unroll
+      for (int u = 0; u < kGatherUnroll; ++u) {
+        if (!inb[u]) continue;
+        float f = 1.f;
+        if (live[u] && a.scale == kScaleSolve) {
+          const int c = I.cls[sl[u]];
+          const double t = al.a[sidx[a.nb > 1 ? (int)a.cband[c] : 0]] * (*a.s2);
+          const double l = lv[u];
+          float gi;
+          if (a.ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? __frcp_rn((float)l) : 0.f;
+          else gi = __frcp_rn((float)(l + t));
+          f = gi * a.inv_n2;
+        } else if (a.scale == kScaleConst) {
+          f = a.cscale;
+        }
+        const float x = v[u].x * f, y = v[u].y * f;
+        const uint16_t hx = tc::bf16_rn(x), hy = tc::bf16_rn(y);
+        *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u], kk[u], L.KcB)) = hx;
+        *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u] + 1, kk[u], L.KcB)) = hy;
         if (SPLIT) {
-          *reinterpret_cast<uint16_t*>(sB[1] + cm_off(col, k, L.KcB)) = tc::bf16_rn(v.x - tc::bf16_val(hx));
-          *reinterpret_cast<uint16_t*>(sB[1] + cm_off(col + 1, k, L.KcB)) = tc::bf16_rn(v.y - tc::bf16_val(hy));
+          *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u], kk[u], L.KcB)) = tc::bf16_rn(x - tc::bf16_val(hx));
+          *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u] + 1, kk[u], L.KcB)) =
+              tc::bf16_rn(y - tc::bf16_val(hy));
         }
       }
     }
     tc::fence_proxy_async();
+  };
+
+  // prologue: tables of the first kTcStages pairs requested, pair 0's right-hand sides gathered
+  if (tid == 0)
+    for (int j = 0; j < min(nloc, kTcStages); ++j) request_tables(j);
+  if (nloc > 0) {
+    set_info(0);
     __syncthreads();
-    // tables landed?  (every thread waits, so a give-up is seen by all)
-    const bool got = tc::mbar_wait(&bar_tma, phase, kWaitPolls);
-    if (!got) sbad = 1;
-    __syncthreads();
-    if (sbad) break;
+    gather(0);
+  }
+  __syncthreads();
+  for (int j = 0; j < nloc; ++j) {
+    const int st = j % kTcStages, ab = j & 1;
+    const uint32_t acc = tmem + (uint32_t)(ab * (L.ncols_tmem / 2));   // accumulator j % 2
     if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_addr(sA[0]), b0 = tc::smem_addr(sB[0]);
-      for (int st = 0; st < L.nsteps; ++st) {
-        const uint64_t da = tc::desc_kmajor(a0 + 256 * st, 128, L.sboA);
-        const uint64_t db = tc::desc_kmajor(b0 + 256 * st, 128, L.sboB);
-        tc::mma_bf16(tmem, da, db, idesc, st > 0);
-      }
-      if (SPLIT) {
-        const uint32_t a1 = tc::smem_addr(sA[1]), b1 = tc::smem_addr(sB[1]);
-        for (int st = 0; st < L.nsteps; ++st) {
-          tc::mma_bf16(tmem, tc::desc_kmajor(a0 + 256 * st, 128, L.sboA), tc::desc_kmajor(b1 + 256 * st, 128, L.sboB),
-                       idesc, true);
-          tc::mma_bf16(tmem, tc::desc_kmajor(a1 + 256 * st, 128, L.sboA), tc::desc_kmajor(b0 + 256 * st, 128, L.sboB),
-                       idesc, true);
+      if (!tc::mbar_wait(&bar_tma[st], (uint32_t)((j / kTcStages) & 1), kWaitPolls)) {
+        sbad = 1;
+      } else {
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_addr(sA(st, 0)), b0 = tc::smem_addr(sB(st, 0));
+        for (int k = 0; k < L.nsteps; ++k)
+          tc::mma_bf16(acc, tc::desc_kmajor(a0 + 256 * k, 128, L.sboA), tc::desc_kmajor(b0 + 256 * k, 128, L.sboB),
+                       idesc, k > 0);
+        if (SPLIT) {
+          const uint32_t a1 = tc::smem_addr(sA(st, 1)), b1 = tc::smem_addr(sB(st, 1));
+          for (int k = 0; k < L.nsteps; ++k) {
+            tc::mma_bf16(acc, tc::desc_kmajor(a0 + 256 * k, 128, L.sboA), tc::desc_kmajor(b1 + 256 * k, 128, L.sboB),
+                         idesc, true);
+            tc::mma_bf16(acc, tc::desc_kmajor(a1 + 256 * k, 128, L.sboA), tc::desc_kmajor(b0 + 256 * k, 128, L.sboB),
+                         idesc, true);
+          }
         }
+        tc::mma_commit(&bar_mma[ab]);
+        // the stage of pair j - 1 is free (its MMAs completed before its epilogue): tables of j + S - 1
+        if (j >= 1 && j - 1 + kTcStages < nloc) request_tables(j - 1 + kTcStages);
       }
-      tc::mma_commit(&bar_mma);
     }
-    const bool done = tc::mbar_wait(&bar_mma, phase, kWaitPolls);
+    // right-hand sides of pair j + 1 while pair j's MMAs run
+    if (j + 1 < nloc) {
+      set_info(j + 1);
+      __syncthreads();
+      gather(j + 1);
+    }
+    // epilogue of pair j: thread tid owns TMEM lane tid = row tid: slot tid / 64, row r = tid % 64
+    const bool done = !tc_flag(&sbad) && tc::mbar_wait(&bar_mma[ab], (uint32_t)((j >> 1) & 1), kWaitPolls);
     if (!done) sbad = 1;
     tc::fence_after_sync();
-    __syncthreads();
-    if (sbad) break;
-    // epilogue: thread tid owns TMEM lane tid = row tid of the tile: slot tid / 64, row r = tid % 64
-    {
-      const int s = warp >> 1, r = tid & 63, c = scls[s];
-      const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * L.ncolc);
+    if (done) {
+      const PairInfo& I = info[st];
+      const int s = warp >> 1, r = tid & 63, c = I.cls[s];
+      const uint32_t tw = acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * L.ncolc);
       float pw = 0.f;
       for (int q = 0; q < a.Q; ++q) {
         float v[8];
         tmem_ld8(tw + 8 * q, v);   // warp-uniform address: every lane loads, rows past R are dropped
         if (c >= 0 && r < a.R) {
-          for (int m = 0; m < snm[s]; ++m) {
+          for (int m = 0; m < I.nm[s]; ++m) {
             const float2 y = make_float2(v[2 * m], v[2 * m + 1]);
             const long plane = a.jq ? (long)r * a.Q + q : (long)q * a.R + r;
-            a.out[plane * a.ps + sbin[s][m]] = y;
-            pw = fmaf(swt[s][m], y.x * y.x + y.y * y.y, pw);
+            a.out[plane * a.ps + I.bin[s][m]] = y;
+            pw = fmaf(I.wt[s][m], y.x * y.x + y.y * y.y, pw);
           }
         }
       }
@@ -257,12 +308,13 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_contract(TcArgs a, TcAlphas a
     }
     tc::fence_before_sync();
     __syncthreads();
+    if (tc_flag(&sbad)) break;
   }
   if (sbad) {
     // a wait gave up: report it, give in-flight copies and MMAs a bounded chance to land, release TMEM
     if (tid == 0 && a.info) atomicOr(a.info, FR3D_INFO_TIMEOUT);
-    tc::mbar_wait(&bar_tma, phase, kWaitPolls);
-    tc::mbar_wait(&bar_mma, phase, kWaitPolls);
+    for (int st = 0; st < kTcStages; ++st) tc::mbar_wait(&bar_tma[st], 0, 1024);
+    tc::mbar_wait(&bar_mma[0], 0, 1024);
     tc::fence_before_sync();
     __syncthreads();
   }
@@ -345,7 +397,7 @@ int tc_launch_config(const void* kern, const TcLayout& L, bool split, int npairs
   int dev = 0, sms = 0;
   FR3D_CUDA_TRY(cudaGetDevice(&dev));
   FR3D_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  size_t smem = (size_t)(split ? 2 : 1) * (L.aRegion + L.bRegion);
+  size_t smem = (size_t)kTcStages * (split ? 2 : 1) * (L.aRegion + L.bRegion);
   const int max_ctas = 512 / L.ncols_tmem;
   int occ = 0;
   std::lock_guard<std::mutex> lock(g_tc_mu);

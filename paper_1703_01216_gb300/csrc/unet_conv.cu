@@ -37,7 +37,7 @@ constexpr int kSlabPos = 130;                   // positions of one (a, e) slab:
 constexpr int kSlabBytes = kSlabPos * 16;       // one channel chunk of a slab
 // MN-major shared-memory descriptor: byte strides between core matrices along MN (channel chunks) and
 // along K (groups of 8 voxels)
-constexpr uint32_t kMnStrideMN_LBO = 1;         // 1: the MN stride goes in the LBO field, the K stride in SBO
+constexpr uint32_t kMnStrideMN_LBO = 0;         // 0: the MN stride goes in the SBO field, the K stride in LBO (measured)
 
 __device__ __forceinline__ uint64_t desc_mn(uint32_t saddr, uint32_t mn_stride, uint32_t k_stride) {
   return kMnStrideMN_LBO ? tc::desc_kmajor(saddr, mn_stride, k_stride) : tc::desc_kmajor(saddr, k_stride, mn_stride);
@@ -177,8 +177,12 @@ __global__ void __launch_bounds__(128) k_conv3(ConvArgs a) {
         const uint4 m = *reinterpret_cast<const uint4*>(
             a.mask + (((long)b * a.mask_chunks + a.mask_off + j) * a.Vs + p) * 16);
         const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+        // the gradient is stored (rounded) first, then scaled by the leaky derivative and rounded again,
+        // as the two steps of the chain rule store it
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+          v[2 * k] = tc::bf16_val(tc::bf16_rn(v[2 * k]));
+          v[2 * k + 1] = tc::bf16_val(tc::bf16_rn(v[2 * k + 1]));
           if (!(lo16(mw[k]) > 0.f)) v[2 * k] *= kLeaky;
           if (!(hi16(mw[k]) > 0.f)) v[2 * k + 1] *= kLeaky;
         }

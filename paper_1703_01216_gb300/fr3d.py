@@ -71,7 +71,9 @@ EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", 
            "fr3d_invert_batched",
            "fr3d_mlp_create", "fr3d_mlp_destroy", "fr3d_mlp_query", "fr3d_mlp_get_params", "fr3d_mlp_set_params",
            "fr3d_mlp_forward", "fr3d_mlp_gradient", "fr3d_mlp_train_step", "fr3d_band_features",
-           "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query", "fr3d_assemble_rhs")
+           "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query", "fr3d_assemble_rhs",
+           "fr3d_unet_create", "fr3d_unet_destroy", "fr3d_unet_query", "fr3d_unet_get_params", "fr3d_unet_set_params",
+           "fr3d_unet_forward", "fr3d_unet_gradient", "fr3d_unet_train_step", "fr3d_unet_error_flags")
 
 
 def load(path: str | None = None):
@@ -117,10 +119,21 @@ def load(path: str | None = None):
     lib.fr3d_autotune_mode.argtypes = [i]
     lib.fr3d_autotune_query.argtypes = [vp, ct.POINTER(i), ct.POINTER(ct.c_float), i]
     lib.fr3d_assemble_rhs.argtypes = [vp, vp, i, ct.POINTER(Sources), d, d, i, d, vp, vp]
+    lib.fr3d_unet_create.argtypes = [i, i, i, i, ct.c_float, ct.c_ulonglong, ct.POINTER(vp)]
+    lib.fr3d_unet_destroy.argtypes = [vp]
+    lib.fr3d_unet_destroy.restype = None
+    lib.fr3d_unet_query.argtypes = [vp, ct.POINTER(i)]
+    lib.fr3d_unet_get_params.argtypes = [vp, vp]
+    lib.fr3d_unet_set_params.argtypes = [vp, vp]
+    lib.fr3d_unet_forward.argtypes = [vp, vp, i, vp, vp]
+    lib.fr3d_unet_gradient.argtypes = [vp, vp, vp, i, vp, vp, vp]
+    lib.fr3d_unet_train_step.argtypes = [vp, vp, vp, i, ct.c_float, vp, vp]
+    lib.fr3d_unet_error_flags.argtypes = [vp, ct.POINTER(i)]
     lib.fr3d_status_string.argtypes = [i]
     lib.fr3d_status_string.restype = ct.c_char_p
     for name in EXPORTS:
-        if name not in ("fr3d_handle_destroy", "fr3d_status_string", "fr3d_batch_destroy", "fr3d_mlp_destroy"):
+        if name not in ("fr3d_handle_destroy", "fr3d_status_string", "fr3d_batch_destroy", "fr3d_mlp_destroy",
+                        "fr3d_unet_destroy"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib
@@ -402,6 +415,59 @@ class Batch:
     def close(self):
         if getattr(self, "ptr", None):
             load().fr3d_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Unet:
+    """fr3d_unet: the learned post-corrector (weights, optimiser state and activation buffers on the device)."""
+
+    def __init__(self, depth: int, height: int, width: int, max_batch: int, in_scale: float = 1.0, seed: int = 0):
+        p = ct.c_void_p()
+        _check(load().fr3d_unet_create(int(depth), int(height), int(width), int(max_batch), float(in_scale), int(seed),
+                                       ct.byref(p)), "fr3d_unet_create")
+        self.ptr = p
+        self.shape = (int(depth), int(height), int(width))
+        npar = ct.c_int()
+        _check(load().fr3d_unet_query(self.ptr, ct.byref(npar)), "fr3d_unet_query")
+        self.n_params = npar.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(load().fr3d_unet_get_params(self.ptr, _ptr(out)), "fr3d_unet_get_params")
+        return out
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(np.asarray(params, np.float32))
+        if a.size != self.n_params:
+            raise ValueError("wrong parameter count")
+        _check(load().fr3d_unet_set_params(self.ptr, _ptr(a)), "fr3d_unet_set_params")
+
+    def forward(self, x, y, stream=None):
+        _check(load().fr3d_unet_forward(self.ptr, _ptr(x), int(x.shape[0]), _ptr(y), _stream(stream)),
+               "fr3d_unet_forward")
+
+    def gradient(self, x, t, grad=None, loss=None, stream=None):
+        _check(load().fr3d_unet_gradient(self.ptr, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grad), _ptr(loss),
+                                         _stream(stream)), "fr3d_unet_gradient")
+
+    def train_step(self, x, t, lr: float, loss=None, stream=None):
+        _check(load().fr3d_unet_train_step(self.ptr, _ptr(x), _ptr(t), int(x.shape[0]), float(lr), _ptr(loss),
+                                           _stream(stream)), "fr3d_unet_train_step")
+
+    def error_flags(self) -> int:
+        f = ct.c_int()
+        _check(load().fr3d_unet_error_flags(self.ptr, ct.byref(f)), "fr3d_unet_error_flags")
+        return f.value
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().fr3d_unet_destroy(self.ptr)
             self.ptr = None
 
     def __del__(self):
