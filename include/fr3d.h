@@ -244,8 +244,15 @@ int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** out, void* 
 int fr3d_batch_run(fr3d_batch* b, void* stream);
 int fr3d_batch_launch_count(fr3d_batch* b);
 void fr3d_batch_destroy(fr3d_batch* b);
-/* create + run + synchronise + destroy in one call */
-int fr3d_invert_batched(const fr3d_instance* inst, int n, void* stream);
+/* One-shot form in caller-provided device memory: fr3d_invert_batched_workspace validates the instances,
+ * prepares every handle's tables (allocating them; synchronous) and writes the workspace bytes the run
+ * needs (the data spectra of all instances and the descriptor tables); fr3d_invert_batched then runs
+ * the batch in `workspace` (device, 256-byte aligned, at least that many bytes, else
+ * FR3D_ERR_INVALID_ARG), allocating nothing when called with the same instances and options.  It is
+ * asynchronous on `stream`; the workspace must stay untouched until the stream has synchronised.  The
+ * fused inverse uses the forced tile variant (autotuner mode 2 + v) or variant 3. */
+int fr3d_invert_batched_workspace(const fr3d_instance* inst, int n, size_t* bytes, void* stream);
+int fr3d_invert_batched(const fr3d_instance* inst, int n, void* workspace, size_t ws_bytes, void* stream);
 
 /* ---- learned per-band alpha (FR3D_ALPHA_LEARNED) ----
  * The paper chooses one alpha by the discrepancy principle (Sec. 4); it has no learned rule.  This

@@ -371,9 +371,11 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
 int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** Uh, const float** Dd,
                          const int** aidx, cudaStream_t st) {
   FR3D_TRY(check_invert_args(H, Q, o));
-  const InvertPlan p = plan_invert<float>(H, Q, false, o->output);
-  FR3D_TRY(ensure_ws(H, p.total));
-  *Uh = reinterpret_cast<float2*>((char*)H->ws + p.uh_off);
+  if (Uh) {   // data spectra in the handle's workspace (Uh = NULL: the caller provides them)
+    const InvertPlan p = plan_invert<float>(H, Q, false, o->output);
+    FR3D_TRY(ensure_ws(H, p.total));
+    *Uh = reinterpret_cast<float2*>((char*)H->ws + p.uh_off);
+  }
   if (o->output == FR3D_OUT_XI) FR3D_TRY(ensure_wtab(H, o->sources, st));
   const int nb = o->n_bands > 1 ? o->n_bands : 1;
   if (nb > 1) FR3D_TRY(ensure_bands(H, nb, nullptr));

@@ -109,33 +109,51 @@ struct fr3d_batch {
   fr3d::Batch b;
 };
 
-extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** out, void* stream) {
-  using namespace fr3d;
-  if (!inst || n < 1 || !out) return FR3D_ERR_INVALID_ARG;
-  *out = nullptr;
-  cudaStream_t st = (cudaStream_t)stream;
+namespace fr3d {
+namespace {
+
+size_t spectra_bytes(const fr3d_instance& I) {
+  const int n = I.handle->h.n;
+  return al(sizeof(float2) * (size_t)I.Q * (n / 2 + 1) * n);
+}
+
+// Validate the instances, prepare every handle's tables (cold; allocates) and group them by grid size.
+// With ext = true the data spectra are laid out from offset 0 of a caller workspace (uh[i] = offsets).
+int batch_prepare(const fr3d_instance* inst, int n, bool ext, std::vector<float2*>& uh, std::vector<const float*>& dd,
+                  std::vector<const int*>& ai, std::map<int, std::vector<int>>& by_n, size_t* spectra_total,
+                  cudaStream_t st) {
   const int output = inst[0].opts ? inst[0].opts->output : FR3D_OUT_XI;
-  // per-instance preparation (tables, workspaces), grouped by grid size
-  std::map<int, std::vector<int>> by_n;
-  std::vector<float2*> uh(n);
-  std::vector<const float*> dd(n);
-  std::vector<const int*> ai(n);
+  size_t off = 0;
   for (int i = 0; i < n; ++i) {
     const fr3d_instance& I = inst[i];
     if (!I.handle || !I.U || !I.out || !I.opts || I.Q < 1) return FR3D_ERR_INVALID_ARG;
     if (I.handle->padded) return FR3D_ERR_UNSUPPORTED_SIZE;   // periodic box only
     for (int k = 0; k < i; ++k)
-      if (inst[k].handle == I.handle) return FR3D_ERR_INVALID_ARG;   // one workspace per handle
+      if (inst[k].handle == I.handle) return FR3D_ERR_INVALID_ARG;   // one set of tables and scratch per handle
     if (I.opts->output != output || I.opts->precision != FR3D_PREC_FP32) return FR3D_ERR_INVALID_ARG;
     Handle* H = &I.handle->h;
     if (H->M != 1 || !fused_supported(H->n)) return FR3D_ERR_UNSUPPORTED_SIZE;
-    FR3D_TRY(prepare_instance_f32(H, I.Q, I.opts, &uh[i], &dd[i], &ai[i], st));
+    FR3D_TRY(prepare_instance_f32(H, I.Q, I.opts, ext ? nullptr : &uh[i], &dd[i], &ai[i], st));
+    if (ext) {
+      uh[i] = reinterpret_cast<float2*>(off);
+      off += spectra_bytes(I);
+    }
     by_n[H->n].push_back(i);
   }
-  // descriptor tables
-  Batch b;
-  b.output = output;
-  std::vector<unsigned char> host;
+  *spectra_total = off;
+  return FR3D_OK;
+}
+
+}  // namespace
+}  // namespace fr3d
+
+namespace fr3d {
+namespace {
+
+// Descriptor tables of the groups (host image; device offsets relative to the table's start).
+void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vector<int>>& by_n,
+                       const std::vector<float2*>& uh, const std::vector<const float*>& dd,
+                       const std::vector<const int*>& ai, std::vector<unsigned char>& host, std::vector<Group>& groups) {
   auto put = [&](const void* p, size_t bytes) {
     const size_t off = al(host.size());
     host.resize(off + bytes);
@@ -187,8 +205,34 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
     g.off_alpha = alph.empty() ? 0 : put(alph.data(), alph.size() * sizeof(AlphaInst));
     g.off_fused = put(fa.data(), fa.size() * sizeof(FusedArgs));
     g.off_map = put(map.data(), map.size() * sizeof(int2));
-    b.groups.push_back(g);
+    groups.push_back(g);
   }
+}
+
+int batch_launches(const std::vector<Group>& groups) {
+  int k = 0;
+  for (const auto& g : groups) k += 3 + (g.nalpha_inst > 0 ? 1 : 0);
+  return k;
+}
+
+}  // namespace
+}  // namespace fr3d
+
+extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** out, void* stream) {
+  using namespace fr3d;
+  if (!inst || n < 1 || !out) return FR3D_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::map<int, std::vector<int>> by_n;
+  std::vector<float2*> uh(n);
+  std::vector<const float*> dd(n);
+  std::vector<const int*> ai(n);
+  size_t spectra = 0;
+  FR3D_TRY(batch_prepare(inst, n, false, uh, dd, ai, by_n, &spectra, st));
+  Batch b;
+  b.output = inst[0].opts->output;
+  std::vector<unsigned char> host;
+  build_descriptors(inst, by_n, uh, dd, ai, host, b.groups);
   FR3D_CUDA_TRY(cudaMalloc(&b.dev, al(host.size())));
   {
     cudaError_t e = cudaMemcpyAsync(b.dev, host.data(), host.size(), cudaMemcpyHostToDevice, st);
@@ -198,8 +242,7 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
       return FR3D_ERR_CUDA;
     }
   }
-  b.launches = 0;
-  for (const auto& g : b.groups) b.launches += 3 + (g.nalpha_inst > 0 ? 1 : 0);
+  b.launches = batch_launches(b.groups);
   fr3d_batch* h = new (std::nothrow) fr3d_batch();
   if (!h) {
     cudaFree(b.dev);
@@ -245,11 +288,52 @@ extern "C" void fr3d_batch_destroy(fr3d_batch* h) {
   delete h;
 }
 
-extern "C" int fr3d_invert_batched(const fr3d_instance* inst, int n, void* stream) {
-  fr3d_batch* b = nullptr;
-  FR3D_TRY(fr3d_batch_create(inst, n, &b, stream));
-  const int rc = fr3d_batch_run(b, stream);
-  if (rc == FR3D_OK) cudaStreamSynchronize((cudaStream_t)stream);
-  fr3d_batch_destroy(b);
-  return rc;
+// One-shot batched inversion in caller-provided device memory.  The query prepares every handle's
+// tables (allocating them, synchronously) and returns the bytes the run needs: the data spectra of all
+// instances and the descriptor tables.  The run allocates nothing when the handles' tables are already
+// prepared for these options; it copies the descriptors into the workspace and launches the groups.
+extern "C" int fr3d_invert_batched_workspace(const fr3d_instance* inst, int n, size_t* bytes, void* stream) {
+  using namespace fr3d;
+  if (!inst || n < 1 || !bytes) return FR3D_ERR_INVALID_ARG;
+  std::map<int, std::vector<int>> by_n;
+  std::vector<float2*> uh(n);
+  std::vector<const float*> dd(n);
+  std::vector<const int*> ai(n);
+  size_t spectra = 0;
+  FR3D_TRY(batch_prepare(inst, n, true, uh, dd, ai, by_n, &spectra, (cudaStream_t)stream));
+  std::vector<unsigned char> host;
+  std::vector<Group> groups;
+  build_descriptors(inst, by_n, uh, dd, ai, host, groups);
+  *bytes = al(spectra) + al(host.size());
+  return FR3D_OK;
+}
+
+extern "C" int fr3d_invert_batched(const fr3d_instance* inst, int n, void* workspace, size_t ws_bytes, void* stream) {
+  using namespace fr3d;
+  if (!inst || n < 1 || !workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return FR3D_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::map<int, std::vector<int>> by_n;
+  std::vector<float2*> uh(n);
+  std::vector<const float*> dd(n);
+  std::vector<const int*> ai(n);
+  size_t spectra = 0;
+  FR3D_TRY(batch_prepare(inst, n, true, uh, dd, ai, by_n, &spectra, st));
+  unsigned char* base = static_cast<unsigned char*>(workspace);
+  for (int i = 0; i < n; ++i) uh[i] = reinterpret_cast<float2*>(base + reinterpret_cast<size_t>(uh[i]));
+  std::vector<unsigned char> host;
+  std::vector<Group> groups;
+  build_descriptors(inst, by_n, uh, dd, ai, host, groups);
+  const size_t need = al(spectra) + al(host.size());
+  if (ws_bytes < need) return FR3D_ERR_INVALID_ARG;
+  unsigned char* tables = base + al(spectra);
+  // pageable source: the copy has staged the descriptors when the call returns
+  FR3D_CUDA_TRY(cudaMemcpyAsync(tables, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+  const int mode = fused_tune_mode_get();
+  const int v = mode >= 2 ? mode - 2 : 3;   // the forced tile, else the register-accumulator tile
+  for (auto& g : groups) {
+    FR3D_TRY(run_group_pre(g, tables, st));
+    FR3D_TRY(inv_fused_batched_f32(g.n, fused_of(g, tables), map_of(g, tables), g.nclusters, inst[0].opts->output, v,
+                                   st));
+  }
+  return FR3D_OK;
 }

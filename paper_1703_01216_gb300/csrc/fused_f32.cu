@@ -65,12 +65,39 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
 
-int launch_variant(int v, int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st) {
+// variants 0-3: the fused cluster kernel's tiles; 4: the two-pass inverse (inv2p.cu), whose intermediate
+// lives in the handle's inv2 buffer (grown outside stream captures only)
+constexpr int kInvVariants = kFusedVariants + 1;
+
+int ensure_inv2(Handle* H, int Q, int nj, cudaStream_t st, bool* ok) {
+  const size_t need = inv2_scratch_bytes(H->n, Q, nj);
+  *ok = H->inv2_cap >= need;
+  if (*ok) return FR3D_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FR3D_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return FR3D_OK;   // no allocation inside a capture
+  FR3D_CUDA_TRY(cudaStreamSynchronize(st));
+  if (H->inv2_buf) cudaFree(H->inv2_buf);
+  H->inv2_buf = nullptr;
+  H->inv2_cap = 0;
+  FR3D_CUDA_TRY(cudaMalloc(&H->inv2_buf, need));
+  H->inv2_cap = need;
+  *ok = true;
+  return FR3D_OK;
+}
+
+int launch_variant(Handle* H, int v, int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st) {
   switch (v) {
     case 0: return fused_launch<0>(n, xi, a, nj, st);
     case 1: return fused_launch<1>(n, xi, a, nj, st);
     case 2: return fused_launch<2>(n, xi, a, nj, st);
     case 3: return fused_launch<3>(n, xi, a, nj, st);
+    case 4: {
+      bool ok = false;
+      FR3D_TRY(ensure_inv2(H, a.Q, nj, st, &ok));
+      if (!ok) return fused_launch<3>(n, xi, a, nj, st);   // inside a capture without the buffer
+      return inv2_launch(n, xi, a, nj, H->inv2_buf, st);
+    }
   }
   return FR3D_ERR_INVALID_ARG;
 }
@@ -80,7 +107,7 @@ int launch_variant(int v, int n, bool xi, const FusedArgs& a, int nj, cudaStream
 int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, bool once, cudaStream_t st, int* v_out) {
   const int mode = g_tune_mode.load();
   if (mode >= 2) {
-    *v_out = std::min(mode - 2, kFusedVariants - 1);
+    *v_out = std::min(mode - 2, kInvVariants - 1);
     return FR3D_OK;
   }
   *v_out = 0;
@@ -103,14 +130,14 @@ int choose_variant(Handle* H, const FusedArgs& a, int nj, bool xi, bool once, cu
   FR3D_CUDA_TRY(cudaEventCreate(&e1));
   int best = 0, st_ok = FR3D_OK;
   float best_ms = 3.4e38f;
-  for (int v = 0; v < kFusedVariants && st_ok == FR3D_OK; ++v) {
-    if (once && fused_rereads_output(v)) {
+  for (int v = 0; v < kInvVariants && st_ok == FR3D_OK; ++v) {
+    if (once && v < kFusedVariants && fused_rereads_output(v)) {
       H->fused_tune_ms[v] = 0.f;
       continue;
     }
-    st_ok = launch_variant(v, H->n, xi, a, nj, st);
+    st_ok = launch_variant(H, v, H->n, xi, a, nj, st);
     if (st_ok == FR3D_OK && cudaEventRecord(e0, st) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
-    for (int rep = 0; rep < 3 && st_ok == FR3D_OK; ++rep) st_ok = launch_variant(v, H->n, xi, a, nj, st);
+    for (int rep = 0; rep < 3 && st_ok == FR3D_OK; ++rep) st_ok = launch_variant(H, v, H->n, xi, a, nj, st);
     if (st_ok == FR3D_OK && cudaEventRecord(e1, st) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
     if (st_ok == FR3D_OK && cudaEventSynchronize(e1) != cudaSuccess) st_ok = FR3D_ERR_CUDA;
     float ms = 0.f;
@@ -164,7 +191,7 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   int v = 0;
   FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, nj, xi, out_host_mapped, st, &v));
   const_cast<Handle*>(H)->fused_var = v;
-  return launch_variant(v, H->n, xi, a, nj, st);
+  return launch_variant(const_cast<Handle*>(H), v, H->n, xi, a, nj, st);
 }
 
 namespace {
@@ -270,7 +297,7 @@ int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, dou
 }  // namespace fr3d
 
 extern "C" int fr3d_autotune_mode(int mode) {
-  if (mode < -1 || mode > 1 + fr3d::kFusedVariants) return FR3D_ERR_INVALID_ARG;
+  if (mode < -1 || mode > 1 + fr3d::kInvVariants) return FR3D_ERR_INVALID_ARG;
   if (mode == -1) return fr3d::g_tune_mode.load();
   return fr3d::g_tune_mode.exchange(mode);
 }
@@ -281,6 +308,6 @@ extern "C" int fr3d_autotune_query(fr3d_handle* h, int* variant, float* ms, int 
   const fr3d::Handle* H = &h->h;
   if (variant) *variant = H->fused_var;
   if (ms)
-    for (int v = 0; v < std::min(cap, fr3d::kFusedVariants); ++v) ms[v] = H->fused_tuned ? H->fused_tune_ms[v] : 0.f;
-  return fr3d::kFusedVariants;
+    for (int v = 0; v < std::min(cap, fr3d::kInvVariants); ++v) ms[v] = H->fused_tuned ? H->fused_tune_ms[v] : 0.f;
+  return fr3d::kInvVariants;
 }

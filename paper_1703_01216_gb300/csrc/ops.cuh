@@ -46,6 +46,11 @@ template <typename T> struct Ops {
 bool fused_supported(int n);
 int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
                   float* out, int Q, int j0, int nj, int output, cudaStream_t st, bool out_host_mapped = false);
+// the two-pass inverse (inv2p.cu): column pass with the solve, row pass with the combination; T holds
+// inv2_scratch_bytes(n, Q, nj)
+struct FusedArgs;
+size_t inv2_scratch_bytes(int n, int Q, int nj);
+int inv2_launch(int n, bool xi, const FusedArgs& f, int nj, float2* T, cudaStream_t st);
 // W_q = V0_q / sum_q' V0_q'^2 on the R grid for the handle's cached sources
 int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st);
 

@@ -68,7 +68,7 @@ EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", 
            "fr3d_zeta_from_xi", "fr3d_choose_alpha", "fr3d_invert", "fr3d_invert_host",
            "fr3d_last_launch_count", "fr3d_profile_enable", "fr3d_profile_read", "fr3d_status_string",
            "fr3d_batch_create", "fr3d_batch_run", "fr3d_batch_launch_count", "fr3d_batch_destroy",
-           "fr3d_invert_batched",
+           "fr3d_invert_batched", "fr3d_invert_batched_workspace",
            "fr3d_mlp_create", "fr3d_mlp_destroy", "fr3d_mlp_query", "fr3d_mlp_get_params", "fr3d_mlp_set_params",
            "fr3d_mlp_forward", "fr3d_mlp_gradient", "fr3d_mlp_train_step", "fr3d_band_features",
            "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query", "fr3d_assemble_rhs",
@@ -104,7 +104,8 @@ def load(path: str | None = None):
     lib.fr3d_batch_launch_count.argtypes = [vp]
     lib.fr3d_batch_destroy.argtypes = [vp]
     lib.fr3d_batch_destroy.restype = None
-    lib.fr3d_invert_batched.argtypes = [ct.POINTER(Instance), i, vp]
+    lib.fr3d_invert_batched.argtypes = [ct.POINTER(Instance), i, vp, ct.c_size_t, vp]
+    lib.fr3d_invert_batched_workspace.argtypes = [ct.POINTER(Instance), i, ct.POINTER(ct.c_size_t), vp]
     lib.fr3d_mlp_create.argtypes = [i, i, i, ct.c_ulonglong, ct.POINTER(vp)]
     lib.fr3d_mlp_destroy.argtypes = [vp]
     lib.fr3d_mlp_destroy.restype = None
@@ -161,6 +162,43 @@ def _stream(stream):
     if isinstance(stream, int):
         return ct.c_void_p(stream)
     return ct.c_void_p(stream.cuda_stream)
+
+
+def _need(t, what: str, *, device: bool = True, dtype=None, numel: int | None = None, optional: bool = False):
+    """Argument check before a call: a torch tensor (or numpy array for host buffers) must live where the
+    C ABI expects it (device or host), be contiguous, have the dtype of the call's precision and hold at
+    least the elements the call reads or writes.  A plain integer is a raw address the caller vouches for
+    and is passed through unchecked."""
+    if t is None:
+        if optional:
+            return
+        raise Fr3dError(-1, f"{what}: missing")
+    if isinstance(t, int):
+        return
+    if isinstance(t, np.ndarray):
+        if device:
+            raise Fr3dError(-1, f"{what}: a device (CUDA) buffer is required, got a numpy array")
+        ok_c, n_el, dt = t.flags["C_CONTIGUOUS"], t.size, t.dtype
+        want = None if dtype is None else np.dtype(str(dtype).replace("torch.", ""))
+    elif hasattr(t, "data_ptr"):
+        if device and not t.is_cuda:
+            raise Fr3dError(-1, f"{what}: a device (CUDA) tensor is required, got one on {t.device}")
+        if not device and t.is_cuda:
+            raise Fr3dError(-1, f"{what}: a host tensor is required, got one on {t.device}")
+        ok_c, n_el, dt, want = t.is_contiguous(), t.numel(), t.dtype, dtype
+    else:
+        raise Fr3dError(-1, f"{what}: unsupported argument type {type(t).__name__}")
+    if not ok_c:
+        raise Fr3dError(-1, f"{what}: must be contiguous")
+    if want is not None and dt != want:
+        raise Fr3dError(-1, f"{what}: dtype {dt} does not match the call (expected {want})")
+    if numel is not None and n_el < numel:
+        raise Fr3dError(-1, f"{what}: {n_el} elements, the call needs {numel}")
+
+
+def _real_dtype(precision: int):
+    import torch
+    return torch.float64 if precision == PREC_FP64 else torch.float32
 
 
 def _ptr(t):
@@ -221,25 +259,40 @@ def kernel_transform(n, x0, h, zr, zy, nu=None, stream=None, kind=K_DZ_INV_R, pa
 
 
 def fwd_apply(handle: Handle, zeta, Q: int, U, precision: int = PREC_FP32, stream=None):
+    n2, dt = handle.n * handle.n, _real_dtype(precision)
+    _need(zeta, "zeta", dtype=dt, numel=Q * handle.Mp * n2)
+    _need(U, "U", dtype=dt, numel=Q * handle.M * n2)
     _check(load().fr3d_fwd_apply(handle.ptr, _ptr(zeta), int(Q), _ptr(U), int(precision), _stream(stream)),
            "fr3d_fwd_apply")
 
 
 def fwd_apply_noalloc(handle: Handle, zeta, Q: int, U, stream=None):
     """fr3d_fwd_apply_noalloc: FP32 forward operator using the library's static scratch (no allocation)."""
+    import torch
+    n2 = handle.n * handle.n
+    _need(zeta, "zeta", dtype=torch.float32, numel=Q * handle.Mp * n2)
+    _need(U, "U", dtype=torch.float32, numel=Q * handle.M * n2)
     _check(load().fr3d_fwd_apply_noalloc(handle.ptr, _ptr(zeta), int(Q), _ptr(U), _stream(stream)),
            "fr3d_fwd_apply_noalloc")
 
 
 def zeta_from_xi(handle: Handle, xi, points, zeta, A0: float = 1.0, precision: int = PREC_FP32, stream=None):
     src, keep = make_sources(points, A0)
+    n2, dt = handle.n * handle.n, _real_dtype(precision)
+    _need(xi, "xi", dtype=dt, numel=handle.Mp * n2)
+    _need(zeta, "zeta", dtype=dt, numel=src.q * handle.Mp * n2)
     _check(load().fr3d_zeta_from_xi(handle.ptr, _ptr(xi), ct.byref(src), _ptr(zeta), int(precision),
                                     _stream(stream)), "fr3d_zeta_from_xi")
 
 
 def choose_alpha(handle: Handle, U, Q: int, alphas, delta: float, tau: float, alpha_idx, residuals=None, info=None,
                  precision: int = PREC_FP32, stream=None):
+    import torch
     a, ap = _f64(alphas)
+    _need(U, "U", dtype=_real_dtype(precision), numel=Q * handle.M * handle.n * handle.n)
+    _need(alpha_idx, "alpha_idx", dtype=torch.int32, numel=1)
+    _need(residuals, "residuals", dtype=torch.float64, numel=a.size, optional=True)
+    _need(info, "info", dtype=torch.int32, numel=1, optional=True)
     _check(load().fr3d_choose_alpha(handle.ptr, _ptr(U), int(Q), ap, a.size, float(delta), float(tau),
                                     int(precision), _ptr(alpha_idx), _ptr(residuals), _ptr(info), _stream(stream)),
            "fr3d_choose_alpha")
@@ -271,14 +324,31 @@ class Opts:
         o.residuals = _ptr(residuals)
         o.info = _ptr(info)
         self.c = o
+        self._aux = (alpha_idx, residuals, info)
+
+    def check(self, handle: "Handle", Q: int, U, out, device: bool = True):
+        """The buffers of one fr3d_invert / fr3d_invert_host call against the handle's sizes."""
+        import torch
+        o = self.c
+        n2, dt = handle.n * handle.n, _real_dtype(o.precision)
+        _need(U, "U", device=device, dtype=dt, numel=Q * handle.M * n2)
+        _need(out, "out", device=device, dtype=dt, numel=(1 if o.output == OUT_XI else Q) * handle.Mp * n2)
+        nb = max(1, o.n_bands)
+        na = 1 if o.alpha_mode == ALPHA_FIXED else o.n_alpha
+        idx, res, info = self._aux
+        _need(idx, "alpha_idx", dtype=torch.int32, numel=nb, optional=o.alpha_mode != ALPHA_GIVEN)
+        _need(res, "residuals", dtype=torch.float64, numel=nb * na, optional=True)
+        _need(info, "info", dtype=torch.int32, numel=1, optional=True)
 
 
 def invert(handle: Handle, U, Q: int, out, opts: Opts, stream=None):
+    opts.check(handle, Q, U, out)
     _check(load().fr3d_invert(handle.ptr, _ptr(U), int(Q), ct.byref(opts.c), _ptr(out), _stream(stream)),
            "fr3d_invert")
 
 
 def invert_host(handle: Handle, U_host, Q: int, out_host, opts: Opts, stream=None):
+    opts.check(handle, Q, U_host, out_host, device=False)
     _check(load().fr3d_invert_host(handle.ptr, _ptr(U_host), int(Q), ct.byref(opts.c), _ptr(out_host),
                                    _stream(stream)), "fr3d_invert_host")
 
@@ -305,7 +375,11 @@ def profile_read(handle: Handle, cap: int = 96):
 
 def assemble_rhs(handle: Handle, dV2dz, Q: int, points, A2: float, c0: float, n_pi: int, pi_half: float, U,
                  A0: float = 1.0, stream=None):
+    import torch
     src, keep = make_sources(points, A0)
+    n = Q * handle.M * handle.n * handle.n
+    _need(dV2dz, "dV2dz", dtype=torch.float32, numel=n)
+    _need(U, "U", dtype=torch.float32, numel=n)
     _check(load().fr3d_assemble_rhs(handle.ptr, _ptr(dV2dz), int(Q), ct.byref(src), float(A2), float(c0), int(n_pi),
                                     float(pi_half), _ptr(U), _stream(stream)), "fr3d_assemble_rhs")
 
@@ -376,13 +450,23 @@ class Mlp:
 
 
 def band_features(handle: Handle, U, Q: int, n_bands: int, delta: float, feat, stream=None):
+    import torch
+    _need(U, "U", dtype=torch.float32, numel=Q * handle.M * handle.n * handle.n)
+    _need(feat, "feat", dtype=torch.float32, numel=max(1, n_bands))
     _check(load().fr3d_band_features(handle.ptr, _ptr(U), int(Q), int(n_bands), float(delta), _ptr(feat),
                                      _stream(stream)), "fr3d_band_features")
 
 
 def band_alpha_targets(handle: Handle, U, zeta_true, Q: int, alphas, n_bands: int, idx, target=None, err=None,
                        stream=None):
+    import torch
     a, ap = _f64(alphas)
+    n2 = handle.n * handle.n
+    _need(U, "U", dtype=torch.float32, numel=Q * handle.M * n2)
+    _need(zeta_true, "zeta_true", dtype=torch.float32, numel=Q * handle.Mp * n2)
+    _need(idx, "idx", dtype=torch.int32, numel=max(1, n_bands))
+    _need(target, "target", dtype=torch.float32, numel=max(1, n_bands), optional=True)
+    _need(err, "err", dtype=torch.float64, numel=max(1, n_bands) * a.size, optional=True)
     _check(load().fr3d_band_alpha_targets(handle.ptr, _ptr(U), _ptr(zeta_true), int(Q), ap, a.size, int(n_bands),
                                           _ptr(idx), _ptr(target), _ptr(err), _stream(stream)),
            "fr3d_band_alpha_targets")
@@ -448,15 +532,32 @@ class Unet:
             raise ValueError("wrong parameter count")
         _check(load().fr3d_unet_set_params(self.ptr, _ptr(a)), "fr3d_unet_set_params")
 
+    def _vol(self, t, what, optional=False):
+        import torch
+        b = int(t.shape[0]) if hasattr(t, "shape") else 1
+        _need(t, what, dtype=torch.float32, numel=b * self.shape[0] * self.shape[1] * self.shape[2],
+              optional=optional)
+
     def forward(self, x, y, stream=None):
+        self._vol(x, "x")
+        self._vol(y, "y")
         _check(load().fr3d_unet_forward(self.ptr, _ptr(x), int(x.shape[0]), _ptr(y), _stream(stream)),
                "fr3d_unet_forward")
 
     def gradient(self, x, t, grad=None, loss=None, stream=None):
+        import torch
+        self._vol(x, "x")
+        self._vol(t, "t")
+        _need(grad, "grad", dtype=torch.float32, numel=self.n_params, optional=True)
+        _need(loss, "loss", dtype=torch.float32, numel=1, optional=True)
         _check(load().fr3d_unet_gradient(self.ptr, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grad), _ptr(loss),
                                          _stream(stream)), "fr3d_unet_gradient")
 
     def train_step(self, x, t, lr: float, loss=None, stream=None):
+        import torch
+        self._vol(x, "x")
+        self._vol(t, "t")
+        _need(loss, "loss", dtype=torch.float32, numel=1, optional=True)
         _check(load().fr3d_unet_train_step(self.ptr, _ptr(x), _ptr(t), int(x.shape[0]), float(lr), _ptr(loss),
                                            _stream(stream)), "fr3d_unet_train_step")
 
@@ -475,3 +576,28 @@ class Unet:
             self.close()
         except Exception:
             pass
+
+
+def _instances(items):
+    arr = (Instance * len(items))()
+    for k, (h, U, Q, opts, out) in enumerate(items):
+        arr[k] = Instance(h.ptr.value, U.data_ptr(), int(Q), ct.pointer(opts.c), out.data_ptr())
+    return arr
+
+
+def invert_batched_workspace(items, stream=None) -> int:
+    """Bytes of device workspace fr3d_invert_batched needs for these (handle, U, Q, opts, out) items."""
+    arr = _instances(items)
+    b = ct.c_size_t()
+    _check(load().fr3d_invert_batched_workspace(arr, len(items), ct.byref(b), _stream(stream)),
+           "fr3d_invert_batched_workspace")
+    return int(b.value)
+
+
+def invert_batched(items, workspace, stream=None):
+    """One-shot batched inversion in the caller's device workspace (a uint8 CUDA tensor)."""
+    _need(workspace, "workspace")
+    arr = _instances(items)
+    nbytes = workspace.numel() * workspace.element_size() if hasattr(workspace, "numel") else 0
+    _check(load().fr3d_invert_batched(arr, len(items), _ptr(workspace), nbytes, _stream(stream)),
+           "fr3d_invert_batched")

@@ -1,5 +1,6 @@
-"""Tile variants of the fused inverse and their autotuner: every variant gives the same bits (single
-calls and batched plans), the oracle agrees, and the tuner times every variant and keeps one."""
+"""Variants of the inverse (steps 2-4) and their autotuner: the four tiles of the fused cluster kernel
+and the two-pass inverse give the same bits (same butterflies in the same order; single calls and batched
+plans, which use the fused tiles), the oracle agrees, and the tuner times every variant and keeps one."""
 
 import numpy as np
 import pytest
@@ -9,7 +10,7 @@ from paper_1703_01216_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-NV = 4   # tile variants of the fused inverse (0: shared-memory xi, 1-2: xi in the output array, 3: in registers)
+NV = 5   # 0: shared-memory xi, 1-2: xi in the output array, 3: in registers (fused tiles); 4: two passes
 
 
 @pytest.fixture(scope="module")

@@ -99,3 +99,29 @@ def test_batch_rejects_shared_handles(F):
     dup = [items[0], (H, items[1][1], items[1][2], items[1][3], items[1][4])]
     with pytest.raises(F.Fr3dError):
         F.Batch(dup)
+
+
+def test_one_shot_batch_in_caller_workspace_matches_the_plan(F):
+    """fr3d_invert_batched in a workspace the caller allocates (size queried first) gives the plan's bits
+    and allocates nothing itself: the device's free memory is unchanged across the call."""
+    items, ws = _instances(F, SHAPES[:5], 950)
+    B = F.Batch(items)
+    B.run()
+    torch.cuda.synchronize()
+    ref = [it[4].clone() for it in items]
+    B.close()
+    need = F.invert_batched_workspace(items)
+    assert need > 0
+    work = torch.empty(need, dtype=torch.uint8, device="cuda")
+    for it in items:
+        it[4].fill_(float("nan"))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    F.invert_batched(items, work)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    for it, r in zip(items, ref):
+        assert torch.equal(it[4], r)
+    with pytest.raises(F.Fr3dError):
+        F.invert_batched(items, work[: need // 2])
