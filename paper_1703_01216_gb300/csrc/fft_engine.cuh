@@ -23,8 +23,18 @@ __device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, 
 __device__ __forceinline__ double2 cmk(double a, double b) { return make_double2(a, b); }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// Products and fused multiply-adds with their rounding pinned (the compiler may not contract them
+// differently in different kernels), so that every kernel built from these butterflies computes the
+// same bits for the same inputs.
+__device__ __forceinline__ float fmul_p(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fmul_p(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_p(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_p(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
-  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+  C r;
+  r.x = fma_p(a.x, b.x, -fmul_p(a.y, b.y));
+  r.y = fma_p(a.x, b.y, fmul_p(a.y, b.x));
+  return r;
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 // multiply by -i (forward) or +i (inverse)
@@ -33,7 +43,11 @@ template <bool INV, typename C> __device__ __forceinline__ C cmul_mi(C a) {
   if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
   return r;
 }
-template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { a.x *= s; a.y *= s; return a; }
+template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) {
+  a.x = fmul_p(a.x, s);
+  a.y = fmul_p(a.y, s);
+  return a;
+}
 
 // cos and sin of 2 pi n / 16, n = 0..15 (exact decimal expansions of the 16th roots of unity)
 #define FR3D_C1 0.92387953251128675613
@@ -57,8 +71,8 @@ __device__ __forceinline__ C twiddle_const(C a) {
     const T c = (T)cs[m];
     const T s = INV ? (T)sn[m] : (T)(-sn[m]);
     C r;
-    r.x = a.x * c - a.y * s;
-    r.y = a.x * s + a.y * c;
+    r.x = fma_p(a.x, c, -fmul_p(a.y, s));
+    r.y = fma_p(a.x, s, fmul_p(a.y, c));
     return r;
   }
 }

@@ -172,10 +172,11 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
           wd[i] = __ldg(drow + o);
         }
 #pragma unroll
-        for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = wa[i] * wd[i];
+        for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = __fmul_rn(wa[i], wd[i]);
       }
       if (r == 0)
-        for (int e = tid; e < N; e += NT) wsm[CPC * N + e] = __ldg(Aj + (long)L * N + e) * __ldg(drow + (long)L * N + e);
+        for (int e = tid; e < N; e += NT)
+          wsm[CPC * N + e] = __fmul_rn(__ldg(Aj + (long)L * N + e), __ldg(drow + (long)L * N + e));
     } else {
 #pragma unroll
       for (int b0 = 0; b0 < CLD; b0 += CB) {
@@ -190,12 +191,12 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
           wd[i] = __ldg(a.Dd + (long)s_aidx[bb[i]] * ps + o);
         }
 #pragma unroll
-        for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = wa[i] * wd[i];
+        for (int i = 0; i < CB; ++i) wsm[tid + (b0 + i) * NT] = __fmul_rn(wa[i], wd[i]);
       }
       if (r == 0)
         for (int e = tid; e < N; e += NT) {
           const long o = (long)L * N + e;
-          wsm[CPC * N + e] = __ldg(Aj + o) * __ldg(a.Dd + (long)s_aidx[__ldg(a.bbin + o)] * ps + o);
+          wsm[CPC * N + e] = __fmul_rn(__ldg(Aj + o), __ldg(a.Dd + (long)s_aidx[__ldg(a.bbin + o)] * ps + o));
         }
     }
   }
@@ -250,12 +251,12 @@ __device__ __forceinline__ void inv_fused_body(const FusedArgs& a, int jl) {
       }
       const float2 u = __ldg(Zq + (long)c0 * N + e);
       const float w = wsm[e];
-      float2 v = make_float2(u.x * w, u.y * w);
+      float2 v = make_float2(__fmul_rn(u.x, w), __fmul_rn(u.y, w));
       if (r == 0 && col == 0) {   // packed column 0: add i w(n/2, ky) U~(n/2, ky)
         const float2 un = __ldg(Zq + (long)L * N + ky);
         const float wl = wsm[CPC * N + ky];
-        v.x -= un.y * wl;
-        v.y += un.x * wl;
+        v.x = __fmaf_rn(-un.y, wl, v.x);
+        v.y = __fmaf_rn(un.x, wl, v.y);
       }
       return v;
     };

@@ -70,19 +70,19 @@ __global__ void __launch_bounds__(kColThreads) k_inv2_col(Inv2Args a) {
   const float* Aj = a.A + (long)j * ps;
   auto wt = [&](long o) -> float {
     const int row = a.nb > 1 ? s_aidx[__ldg(a.bbin + o)] : s_aidx[0];
-    return __ldg(Aj + o) * __ldg(a.Dd + (long)row * ps + o);
+    return __fmul_rn(__ldg(Aj + o), __ldg(a.Dd + (long)row * ps + o));
   };
   auto ldc = [&](int s, int ky) -> float2 {
     const long o = (long)(c0 + s) * N + ky;
     const float2 u = __ldg(Uq + o);
     const float w = wt(o);
-    float2 v = make_float2(u.x * w, u.y * w);
+    float2 v = make_float2(__fmul_rn(u.x, w), __fmul_rn(u.y, w));
     if (c0 + s == 0) {   // packed column 0: add i w(n/2, ky) U~(n/2, ky)
       const long oL = (long)L * N + ky;
       const float2 un = __ldg(Uq + oL);
       const float wl = wt(oL);
-      v.x -= un.y * wl;
-      v.y += un.x * wl;
+      v.x = __fmaf_rn(-un.y, wl, v.x);
+      v.y = __fmaf_rn(un.x, wl, v.y);
     }
     return v;
   };
@@ -123,10 +123,23 @@ __global__ void __launch_bounds__(kRowThreads) k_inv2_row(Inv2Args a) {
   for (int k = 0; k < KR; ++k)
 #pragma unroll
     for (int rr = 0; rr < LP::R; ++rr) acc[k][rr] = make_float2(0.f, 0.f);
-  for (int q = 0; q < a.Q; ++q) {
+  // loads of source parameter q: the split pairs X(k), X(L - k) of every row (column 0 packed) and the
+  // combination weights in the layout of the last pass; those of q + 1 are in flight while q is
+  // transformed
+  float2 xa[SIT], xb[SIT], wv[KR][LP::R];
+  auto load_q = [&](int q, float2 (&ya)[SIT], float2 (&yb)[SIT], float2 (&yw)[KR][LP::R]) {
     const float2* Tq = a.T + ((long)(q * a.nj + jl) * N + y0) * L;
-    // combination weights of this q in the layout of the last pass, requested before the passes
-    float2 wv[KR][LP::R];
+#pragma unroll
+    for (int i = 0; i < SIT; ++i) {
+      const int e = tid + i * kRowThreads;
+      if (NSPL % kRowThreads == 0 || e < NSPL) {
+        const int row = e / NK, k = e - row * NK;   // consecutive threads: consecutive k of one row
+        const float2 u = __ldg(Tq + (long)row * L + k);
+        const float2 v = __ldg(Tq + (long)row * L + (k == 0 ? 0 : L - k));
+        ya[i] = k == 0 ? make_float2(u.x, 0.f) : u;                     // X(0): real part of column 0
+        yb[i] = k == 0 ? make_float2(v.y, 0.f) : v;                     // X(L): its imaginary part
+      }
+    }
     if constexpr (MODE == 1) {
       const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + j) * N + y0) * N);
 #pragma unroll
@@ -135,28 +148,15 @@ __global__ void __launch_bounds__(kRowThreads) k_inv2_row(Inv2Args a) {
         if (NBF % kRowThreads == 0 || b < NBF) {
           const int sr = b / LP::BPS, jq = b % LP::BPS;
 #pragma unroll
-          for (int rr = 0; rr < LP::R; ++rr) wv[k][rr] = __ldg(wq + sr * L + jq + rr * LP::NS);
+          for (int rr = 0; rr < LP::R; ++rr) yw[k][rr] = __ldg(wq + sr * L + jq + rr * LP::NS);
         }
       }
     }
-    // X(kx, y) for kx in [0, n/2] from T (column 0 packed)
-    auto xat = [&](int row, int kx) -> float2 {
-      const float2 v = __ldg(Tq + (long)row * L + (kx == L ? 0 : kx));
-      if (kx == 0) return make_float2(v.x, 0.f);
-      if (kx == L) return make_float2(v.y, 0.f);
-      return v;
-    };
-    float2 xa[SIT], xb[SIT];
-#pragma unroll
-    for (int i = 0; i < SIT; ++i) {
-      const int e = tid + i * kRowThreads;
-      if (NSPL % kRowThreads == 0 || e < NSPL) {
-        const int row = e / NK, k = e - row * NK;   // consecutive threads: consecutive k of one row
-        xa[i] = xat(row, k);
-        xb[i] = xat(row, L - k);
-      }
-    }
+  };
+  load_q(0, xa, xb, wv);
+  for (int q = 0; q < a.Q; ++q) {
     __syncthreads();   // the previous q's last pass has read rowbuf
+    // Hermitian split Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), pairs (k, L - k)
 #pragma unroll
     for (int i = 0; i < SIT; ++i) {
       const int e = tid + i * kRowThreads;
@@ -173,11 +173,17 @@ __global__ void __launch_bounds__(kRowThreads) k_inv2_row(Inv2Args a) {
         }
       }
     }
+    float2 wq_cur[KR][LP::R];
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+#pragma unroll
+      for (int rr = 0; rr < LP::R; ++rr) wq_cur[k][rr] = wv[k][rr];
+    if (q + 1 < a.Q) load_q(q + 1, xa, xb, wv);
     __syncthreads();
     fft_passes<L, true, kRB, kRowThreads, 0, Plan<L>::np - 1>(rowbuf, SSR, ptr, tid);
     if constexpr (MODE == 1) {
       auto emit = [&](int, int, float2 v, int k, int rr) {
-        acc[k][rr] = make_float2(fmaf(wv[k][rr].x, v.x, acc[k][rr].x), fmaf(wv[k][rr].y, v.y, acc[k][rr].y));
+        acc[k][rr] = make_float2(fmaf(wq_cur[k][rr].x, v.x, acc[k][rr].x), fmaf(wq_cur[k][rr].y, v.y, acc[k][rr].y));
       };
       last_pass_to<L, true, kRB, kRowThreads>(rowbuf, SSR, ptr, emit, tid);
     } else {

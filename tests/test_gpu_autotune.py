@@ -1,6 +1,7 @@
-"""Variants of the inverse (steps 2-4) and their autotuner: the four tiles of the fused cluster kernel
-and the two-pass inverse give the same bits (same butterflies in the same order; single calls and batched
-plans, which use the fused tiles), the oracle agrees, and the tuner times every variant and keeps one."""
+"""Variants of the inverse (steps 2-4) and their autotuner: the four tiles of the fused cluster kernel and
+the two-pass inverse give the same bits (the same butterflies, with every product and fused multiply-add
+pinned so that no kernel contracts them differently; single calls and batched plans), the oracle agrees,
+and the tuner times every variant and keeps one."""
 
 import numpy as np
 import pytest
