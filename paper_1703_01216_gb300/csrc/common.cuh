@@ -152,6 +152,8 @@ int ensure_ws(Handle* H, size_t bytes);
 // dynamic shared memory share) once per (kernel, device); later calls are a lookup, so launches
 // inside a stream capture make no attribute call.  Returns an error if bytes exceed the device limit.
 int smem_optin(const void* kernel, size_t bytes);
+// CTAs of `kernel` that fit on one SM by registers, threads and the device's per-SM shared memory
+int resident_ctas(const void* kernel, int threads, size_t dyn_smem);
 
 // stage kinds reported by fr3d_profile_read
 enum StageKind { kStRowR2C = 0, kStColFwd = 1, kStAlpha = 2, kStColSolve = 3, kStRowC2R = 4, kStTable = 5,

@@ -25,7 +25,7 @@ constexpr int kRB = 8;   // rows per block of pass 2
 
 template <int N> struct Inv2Geom {
   static constexpr int L = N / 2;
-  static constexpr int CA = L <= 32 ? L : (L % 32 == 0 ? 32 : 24);   // columns per block of pass 1
+  static constexpr int CA = L <= 16 ? L : (L % 16 == 0 ? 16 : 12);   // columns per block of pass 1
   static constexpr int SSC = PaddedLen<N, float2>::v + 1;            // odd: transposed reads free of conflicts
   static constexpr int SSR = PaddedLen<L, float2>::v;
   static constexpr int PTC = passtw_size<N>() > 0 ? passtw_size<N>() : 1;
@@ -123,11 +123,25 @@ __global__ void __launch_bounds__(kRowThreads) k_inv2_row(Inv2Args a) {
   for (int k = 0; k < KR; ++k)
 #pragma unroll
     for (int rr = 0; rr < LP::R; ++rr) acc[k][rr] = make_float2(0.f, 0.f);
-  // loads of source parameter q: the split pairs X(k), X(L - k) of every row (column 0 packed) and the
-  // combination weights in the layout of the last pass; those of q + 1 are in flight while q is
-  // transformed
+  // loads of source parameter q: the split pairs X(k), X(L - k) of every row (column 0 packed), those of
+  // q + 1 in flight while q is transformed, and the combination weights in the layout of the last pass,
+  // requested before the split
   float2 xa[SIT], xb[SIT], wv[KR][LP::R];
-  auto load_q = [&](int q, float2 (&ya)[SIT], float2 (&yb)[SIT], float2 (&yw)[KR][LP::R]) {
+  auto load_w = [&](int q) {
+    if constexpr (MODE == 1) {
+      const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + j) * N + y0) * N);
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const int b = tid + k * kRowThreads;
+        if (NBF % kRowThreads == 0 || b < NBF) {
+          const int sr = b / LP::BPS, jq = b % LP::BPS;
+#pragma unroll
+          for (int rr = 0; rr < LP::R; ++rr) wv[k][rr] = __ldg(wq + sr * L + jq + rr * LP::NS);
+        }
+      }
+    }
+  };
+  auto load_q = [&](int q, float2 (&ya)[SIT], float2 (&yb)[SIT]) {
     const float2* Tq = a.T + ((long)(q * a.nj + jl) * N + y0) * L;
 #pragma unroll
     for (int i = 0; i < SIT; ++i) {
@@ -140,21 +154,10 @@ __global__ void __launch_bounds__(kRowThreads) k_inv2_row(Inv2Args a) {
         yb[i] = k == 0 ? make_float2(v.y, 0.f) : v;                     // X(L): its imaginary part
       }
     }
-    if constexpr (MODE == 1) {
-      const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + j) * N + y0) * N);
-#pragma unroll
-      for (int k = 0; k < KR; ++k) {
-        const int b = tid + k * kRowThreads;
-        if (NBF % kRowThreads == 0 || b < NBF) {
-          const int sr = b / LP::BPS, jq = b % LP::BPS;
-#pragma unroll
-          for (int rr = 0; rr < LP::R; ++rr) yw[k][rr] = __ldg(wq + sr * L + jq + rr * LP::NS);
-        }
-      }
-    }
   };
-  load_q(0, xa, xb, wv);
+  load_q(0, xa, xb);
   for (int q = 0; q < a.Q; ++q) {
+    load_w(q);         // in flight during the split and the passes
     __syncthreads();   // the previous q's last pass has read rowbuf
     // Hermitian split Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), pairs (k, L - k)
 #pragma unroll
@@ -173,17 +176,12 @@ __global__ void __launch_bounds__(kRowThreads) k_inv2_row(Inv2Args a) {
         }
       }
     }
-    float2 wq_cur[KR][LP::R];
-#pragma unroll
-    for (int k = 0; k < KR; ++k)
-#pragma unroll
-      for (int rr = 0; rr < LP::R; ++rr) wq_cur[k][rr] = wv[k][rr];
-    if (q + 1 < a.Q) load_q(q + 1, xa, xb, wv);
+    if (q + 1 < a.Q) load_q(q + 1, xa, xb);
     __syncthreads();
     fft_passes<L, true, kRB, kRowThreads, 0, Plan<L>::np - 1>(rowbuf, SSR, ptr, tid);
     if constexpr (MODE == 1) {
       auto emit = [&](int, int, float2 v, int k, int rr) {
-        acc[k][rr] = make_float2(fmaf(wq_cur[k][rr].x, v.x, acc[k][rr].x), fmaf(wq_cur[k][rr].y, v.y, acc[k][rr].y));
+        acc[k][rr] = make_float2(fmaf(wv[k][rr].x, v.x, acc[k][rr].x), fmaf(wv[k][rr].y, v.y, acc[k][rr].y));
       };
       last_pass_to<L, true, kRB, kRowThreads>(rowbuf, SSR, ptr, emit, tid);
     } else {

@@ -29,7 +29,6 @@ namespace fr3d {
 
 namespace {
 
-constexpr int kTcThreads = 128;
 constexpr long kWaitPolls = 1L << 22;   // bounded mbarrier waits (a poll suspends for a short slice)
 
 struct TcAlphas {
@@ -99,15 +98,25 @@ __device__ __forceinline__ int cm_off(int row, int col, int chunks) {
   return ((row >> 3) * chunks + (col >> 3)) * 128 + (row & 7) * 16 + (col & 7) * 2;
 }
 
-// Pipeline of one CTA over its pairs j (pair blockIdx.x + j gridDim.x), stage j % kTcStages, TMEM
-// accumulator j % 2:
-//   thread 0: wait for pair j's tables, issue its MMAs, commit; then request the tables of pair
-//             j + kTcStages - 1 into the stage that pair j - 1 used (its MMAs completed before its epilogue);
-//   all:      class members of pair j + 1, gather and round its right-hand sides into its stage (the loads
-//             of a thread issued together), while pair j's MMAs run;
-//   all:      wait for pair j's MMAs, read the accumulator (one output row per thread) and scatter it.
-constexpr int kTcStages = 2;
+// One CTA = 8 warps over its pairs j (pair blockIdx.x + j gridDim.x), stage j % kTcStages, TMEM
+// accumulator j % 2, warp-specialised:
+//   producer warps 4-7: for every pair, once its stage is free (the MMAs of the pair kTcStages earlier
+//     have completed), request its class tables (one bulk copy per class, thread 128), gather and round
+//     its right-hand sides into the stage (loads of a thread issued together) and arrive on the stage's
+//     "operands ready" barrier; they run up to kTcStages pairs ahead of the MMAs;
+//   consumer warps 0-3: thread 0 waits for the stage's tables and right-hand sides, issues the pair's
+//     MMAs into accumulator j % 2 and commits twice (accumulator ready; stage free); then all 128
+//     consumer threads read the accumulator (one output row each) and scatter it, and meet on a named
+//     barrier before the accumulator is written again.
+constexpr int kTcStages = 3;
+constexpr int kTcCtaThreads = 256;
 constexpr int kGatherUnroll = 4;
+
+__device__ __forceinline__ int tc_flag(const int* f) { return *reinterpret_cast<const volatile int*>(f); }
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
 
 struct PairInfo {
   long bin[2][4];
@@ -115,15 +124,30 @@ struct PairInfo {
   int nm[2], cls[2];
 };
 
-__device__ __forceinline__ int tc_flag(const int* f) { return *reinterpret_cast<const volatile int*>(f); }
+__device__ __forceinline__ void pair_info(int pair, int C, int n, PairInfo& I) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int c = 2 * pair + s;
+    I.cls[s] = c < C ? c : -1;
+    int kxs[4], kys[4];
+    float wts[4];
+    int nm = 0;
+    if (c < C) nm = class_members(c, n, kxs, kys, wts);
+    I.nm[s] = nm;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      I.bin[s][m] = m < nm ? (long)kxs[m] * n + kys[m] : 0;
+      I.wt[s][m] = m < nm ? wts[m] : 0.f;
+    }
+  }
+}
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(kTcThreads) k_tc_contract(TcArgs a, TcAlphas al) {
+__global__ void __launch_bounds__(kTcCtaThreads) k_tc_contract(TcArgs a, TcAlphas al) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar_tma[kTcStages], bar_mma[2];
+  __shared__ __align__(8) uint64_t full_tma[kTcStages], full_b[kTcStages], empty[kTcStages], acc_ready[2];
   __shared__ uint32_t tbase;
-  __shared__ int sbad;
-  __shared__ PairInfo info[kTcStages];
+  __shared__ int sbad, cstop;
   __shared__ int sidx[FR3D_MAX_BANDS];
   const TcLayout L = tc_layout(a.Kc, a.Q);
   const int stage_bytes = (SPLIT ? 2 : 1) * (L.aRegion + L.bRegion);
@@ -134,17 +158,22 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_contract(TcArgs a, TcAlphas a
   const int nloc = blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   auto pair_of = [&](int j) { return (int)blockIdx.x + j * (int)gridDim.x; };
   // zero every table region once: rows past R, chunks past K and the tail are never copied
-  for (int e = tid; e < kTcStages * stage_bytes / 16; e += kTcThreads)
+  for (int e = tid; e < kTcStages * stage_bytes / 16; e += kTcCtaThreads)
     reinterpret_cast<uint4*>(sm)[e] = make_uint4(0, 0, 0, 0);
   tc::fence_proxy_async();   // the zeros are ordered before the bulk copies into the same regions
   if (a.scale == kScaleSolve)
-    for (int b = tid; b < max(a.nb, 1); b += kTcThreads) sidx[b] = min(max(a.aidx[b], 0), a.na - 1);
+    for (int b = tid; b < max(a.nb, 1); b += kTcCtaThreads) sidx[b] = min(max(a.aidx[b], 0), a.na - 1);
   if (tid == 0) {
-    for (int st = 0; st < kTcStages; ++st) tc::mbar_init(&bar_tma[st], 1);
-    tc::mbar_init(&bar_mma[0], 1);
-    tc::mbar_init(&bar_mma[1], 1);
+    for (int st = 0; st < kTcStages; ++st) {
+      tc::mbar_init(&full_tma[st], 1);
+      tc::mbar_init(&full_b[st], 128);
+      tc::mbar_init(&empty[st], 1);
+    }
+    tc::mbar_init(&acc_ready[0], 1);
+    tc::mbar_init(&acc_ready[1], 1);
     tc::mbar_fence_init();
     sbad = 0;
+    cstop = 0;
   }
   if (warp == 0) tc::tmem_alloc(&tbase, L.ncols_tmem);
   tc::fence_before_sync();
@@ -153,169 +182,158 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_contract(TcArgs a, TcAlphas a
   const uint32_t tmem = tbase;
   const uint32_t idesc = tc::idesc_bf16(128, L.N);
 
-  auto request_tables = [&](int j) {   // thread 0
-    const int st = j % kTcStages, pair = pair_of(j);
-    const int nv = (2 * pair + 1 < a.C) ? 2 : 1;
-    tc::mbar_arrive_expect_tx(&bar_tma[st], (uint32_t)(nv * a.blob * (SPLIT ? 2 : 1)));
-    for (int s = 0; s < nv; ++s) {
-      const long c = 2L * pair + s;
-      tc::bulk_g2s(sA(st, 0) + s * 8 * L.sboA, reinterpret_cast<const unsigned char*>(a.hi) + c * a.blob,
-                   (uint32_t)a.blob, &bar_tma[st]);
-      if (SPLIT)
-        tc::bulk_g2s(sA(st, 1) + s * 8 * L.sboA, reinterpret_cast<const unsigned char*>(a.lo) + c * a.blob,
-                     (uint32_t)a.blob, &bar_tma[st]);
-    }
-  };
-  auto set_info = [&](int j) {         // threads 0 and 1: the classes of pair j and their member bins
-    if (tid < 2) {
-      PairInfo& I = info[j % kTcStages];
-      const int c = 2 * pair_of(j) + tid;
-      I.cls[tid] = c < a.C ? c : -1;
-      int kxs[4], kys[4];
-      float wts[4];
-      int nm = 0;
-      if (c < a.C) nm = class_members(c, a.n, kxs, kys, wts);
-      I.nm[tid] = nm;
-      for (int m = 0; m < 4; ++m) {
-        I.bin[tid][m] = m < nm ? (long)kxs[m] * a.n + kys[m] : 0;
-        I.wt[tid][m] = m < nm ? wts[m] : 0.f;
-      }
-    }
-  };
-  // B operand of pair j: column (slot s, q, member m, re/im), contraction index k; zeros outside the data
-  auto gather = [&](int j) {
-    const int st = j % kTcStages;
-    const PairInfo& I = info[st];
+  if (warp >= 4) {
+    // ------------------------------------------------------------------ producers
+    const int ptid = tid - 128;
     const int kpad = 8 * L.KcB;
     const int total = 2 * a.Q * kpad * 4;
-    for (int e0 = 0; e0 < total; e0 += kTcThreads * kGatherUnroll) {
-      float2 v[kGatherUnroll];
-      double lv[kGatherUnroll];
-      int kk[kGatherUnroll], col[kGatherUnroll], sl[kGatherUnroll];
-      bool live[kGatherUnroll], inb[kGatherUnroll];
-#pragma unroll
-      for (int u = 0; u < kGatherUnroll; ++u) {
-        const int e = e0 + u * kTcThreads + tid;
-        inb[u] = e < total;
-        const int m = e & 3;
-        int rest = e >> 2;
-        const int k = rest % kpad;
-        rest /= kpad;
-        const int q = rest % a.Q, s = rest / a.Q;
-        kk[u] = k;
-        sl[u] = s;
-        col[u] = s * L.ncolc + q * 8 + 2 * m;
-        live[u] = inb[u] && I.cls[s] >= 0 && k < a.K && m < I.nm[s];
-        v[u] = make_float2(0.f, 0.f);
-        lv[u] = 0.0;
-        if (live[u]) {
-          v[u] = __ldg(a.in + ((long)q * a.K + k) * a.ps + I.bin[s][m]);
-          if (a.scale == kScaleSolve) lv[u] = __ldg(a.lam + (long)I.cls[s] * a.K + k);
+    for (int j = 0; j < nloc && !tc_flag(&sbad); ++j) {
+      const int st = j % kTcStages, use = j / kTcStages;
+      if (use > 0 && !tc::mbar_wait(&empty[st], (uint32_t)((use - 1) & 1), kWaitPolls)) {
+        sbad = 1;
+        break;
+      }
+      const int pair = pair_of(j);
+      if (ptid == 0) {
+        const int nv = (2 * pair + 1 < a.C) ? 2 : 1;
+        tc::mbar_arrive_expect_tx(&full_tma[st], (uint32_t)(nv * a.blob * (SPLIT ? 2 : 1)));
+        for (int s = 0; s < nv; ++s) {
+          const long c = 2L * pair + s;
+          tc::bulk_g2s(sA(st, 0) + s * 8 * L.sboA, reinterpret_cast<const unsigned char*>(a.hi) + c * a.blob,
+                       (uint32_t)a.blob, &full_tma[st]);
+          if (SPLIT)
+            tc::bulk_g2s(sA(st, 1) + s * 8 * L.sboA, reinterpret_cast<const unsigned char*>(a.lo) + c * a.blob,
+                         (uint32_t)a.blob, &full_tma[st]);
         }
       }
+      PairInfo I;
+      pair_info(pair, a.C, a.n, I);
+      for (int e0 = 0; e0 < total; e0 += 128 * kGatherUnroll) {
+        float2 v[kGatherUnroll];
+        double lv[kGatherUnroll];
+        int kk[kGatherUnroll], col[kGatherUnroll], sl[kGatherUnroll];
+        bool live[kGatherUnroll], inb[kGatherUnroll];
 #pragma unroll
-      for (int u = 0; u < kGatherUnroll; ++u) {
-        if (!inb[u]) continue;
-        float f = 1.f;
-        if (live[u] && a.scale == kScaleSolve) {
-          const int c = I.cls[sl[u]];
-          const double t = al.a[sidx[a.nb > 1 ? (int)a.cband[c] : 0]] * (*a.s2);
-          const double l = lv[u];
-          float gi;
-          if (a.ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? __frcp_rn((float)l) : 0.f;
-          else gi = __frcp_rn((float)(l + t));
-          f = gi * a.inv_n2;
-        } else if (a.scale == kScaleConst) {
-          f = a.cscale;
+        for (int u = 0; u < kGatherUnroll; ++u) {
+          const int e = e0 + u * 128 + ptid;
+          inb[u] = e < total;
+          const int m = e & 3;
+          int rest = e >> 2;
+          const int k = rest % kpad;
+          rest /= kpad;
+          const int q = rest % a.Q, s = rest / a.Q;
+          kk[u] = k;
+          sl[u] = s;
+          col[u] = s * L.ncolc + q * 8 + 2 * m;
+          live[u] = inb[u] && I.cls[s] >= 0 && k < a.K && m < I.nm[s];
+          v[u] = make_float2(0.f, 0.f);
+          lv[u] = 0.0;
+          if (live[u]) {
+            v[u] = __ldg(a.in + ((long)q * a.K + k) * a.ps + I.bin[s][m]);
+            if (a.scale == kScaleSolve) lv[u] = __ldg(a.lam + (long)I.cls[s] * a.K + k);
+          }
         }
-        const float x = v[u].x * f, y = v[u].y * f;
-        const uint16_t hx = tc::bf16_rn(x), hy = tc::bf16_rn(y);
-        *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u], kk[u], L.KcB)) = hx;
-        *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u] + 1, kk[u], L.KcB)) = hy;
-        if (SPLIT) {
-          *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u], kk[u], L.KcB)) = tc::bf16_rn(x - tc::bf16_val(hx));
-          *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u] + 1, kk[u], L.KcB)) =
-              tc::bf16_rn(y - tc::bf16_val(hy));
+#pragma unroll
+        for (int u = 0; u < kGatherUnroll; ++u) {
+          if (!inb[u]) continue;
+          float f = 1.f;
+          if (live[u] && a.scale == kScaleSolve) {
+            const int c = I.cls[sl[u]];
+            const double t = al.a[sidx[a.nb > 1 ? (int)a.cband[c] : 0]] * (*a.s2);
+            const double l = lv[u];
+            float gi;
+            if (a.ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? __frcp_rn((float)l) : 0.f;
+            else gi = __frcp_rn((float)(l + t));
+            f = gi * a.inv_n2;
+          } else if (a.scale == kScaleConst) {
+            f = a.cscale;
+          }
+          const float x = v[u].x * f, y = v[u].y * f;
+          const uint16_t hx = tc::bf16_rn(x), hy = tc::bf16_rn(y);
+          *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u], kk[u], L.KcB)) = hx;
+          *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u] + 1, kk[u], L.KcB)) = hy;
+          if (SPLIT) {
+            *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u], kk[u], L.KcB)) = tc::bf16_rn(x - tc::bf16_val(hx));
+            *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u] + 1, kk[u], L.KcB)) =
+                tc::bf16_rn(y - tc::bf16_val(hy));
+          }
         }
       }
+      tc::fence_proxy_async();   // this thread's operand writes before the MMAs read them
+      mbar_arrive(&full_b[st]);
     }
-    tc::fence_proxy_async();
-  };
-
-  // prologue: tables of the first kTcStages pairs requested, pair 0's right-hand sides gathered
-  if (tid == 0)
-    for (int j = 0; j < min(nloc, kTcStages); ++j) request_tables(j);
-  if (nloc > 0) {
-    set_info(0);
-    __syncthreads();
-    gather(0);
+  } else {
+    // ------------------------------------------------------------------ consumers
+    // thread 0 issues the MMAs of pair j + 1 before the epilogue of pair j (accumulators alternate), so
+    // each pair's MMAs run while the previous pair is written out
+    auto issue = [&](int j) {   // thread 0 only; false if a wait gave up
+      const int st = j % kTcStages, use = j / kTcStages;
+      const uint32_t acc = tmem + (uint32_t)((j & 1) * (L.ncols_tmem / 2));
+      if (tc_flag(&sbad) || !tc::mbar_wait(&full_tma[st], (uint32_t)(use & 1), kWaitPolls) ||
+          !tc::mbar_wait(&full_b[st], (uint32_t)(use & 1), kWaitPolls))
+        return false;
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_addr(sA(st, 0)), b0 = tc::smem_addr(sB(st, 0));
+      for (int k = 0; k < L.nsteps; ++k)
+        tc::mma_bf16(acc, tc::desc_kmajor(a0 + 256 * k, 128, L.sboA), tc::desc_kmajor(b0 + 256 * k, 128, L.sboB),
+                     idesc, k > 0);
+      if (SPLIT) {
+        const uint32_t a1 = tc::smem_addr(sA(st, 1)), b1 = tc::smem_addr(sB(st, 1));
+        for (int k = 0; k < L.nsteps; ++k) {
+          tc::mma_bf16(acc, tc::desc_kmajor(a0 + 256 * k, 128, L.sboA), tc::desc_kmajor(b1 + 256 * k, 128, L.sboB),
+                       idesc, true);
+          tc::mma_bf16(acc, tc::desc_kmajor(a1 + 256 * k, 128, L.sboA), tc::desc_kmajor(b0 + 256 * k, 128, L.sboB),
+                       idesc, true);
+        }
+      }
+      tc::mma_commit(&acc_ready[j & 1]);
+      tc::mma_commit(&empty[st]);
+      return true;
+    };
+    if (tid == 0 && nloc > 0 && !issue(0)) sbad = 1;
+    for (int j = 0; j < nloc; ++j) {
+      const int ab = j & 1;
+      const uint32_t acc = tmem + (uint32_t)(ab * (L.ncols_tmem / 2));
+      // accumulator (j + 1) % 2 was read by the epilogue of pair j - 1, which ended at the last barrier
+      if (tid == 0 && j + 1 < nloc && !issue(j + 1)) sbad = 1;
+      __syncwarp();
+      bool done = !tc_flag(&sbad) && tc::mbar_wait(&acc_ready[ab], (uint32_t)((j >> 1) & 1), kWaitPolls);
+      done = __all_sync(0xffffffffu, done);   // the TMEM loads below are warp-collective
+      if (!done) sbad = 1;
+      tc::fence_after_sync();
+      if (done) {
+        // epilogue of pair j: thread tid owns TMEM lane tid = row tid: slot tid / 64, row r = tid % 64
+        PairInfo I;
+        pair_info(pair_of(j), a.C, a.n, I);
+        const int s = warp >> 1, r = tid & 63, c = I.cls[s];
+        const uint32_t tw = acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * L.ncolc);
+        float pw = 0.f;
+        for (int q = 0; q < a.Q; ++q) {
+          float v[8];
+          tmem_ld8(tw + 8 * q, v);   // warp-uniform address: every lane loads, rows past R are dropped
+          if (c >= 0 && r < a.R) {
+            for (int m = 0; m < I.nm[s]; ++m) {
+              const float2 y = make_float2(v[2 * m], v[2 * m + 1]);
+              const long plane = a.jq ? (long)r * a.Q + q : (long)q * a.R + r;
+              a.out[plane * a.ps + I.bin[s][m]] = y;
+              pw = fmaf(I.wt[s][m], y.x * y.x + y.y * y.y, pw);
+            }
+          }
+        }
+        if (a.Pc && c >= 0 && r < a.R) a.Pc[(long)c * a.R + r] = (double)pw;
+      }
+      tc::fence_before_sync();
+      if (tid == 0) cstop = tc_flag(&sbad);
+      consumer_sync();   // every row of accumulator j % 2 is read before the MMAs of pair j + 2 reuse it
+      if (cstop) break;  // the same decision for every consumer thread (written before the barrier)
+    }
   }
   __syncthreads();
-  for (int j = 0; j < nloc; ++j) {
-    const int st = j % kTcStages, ab = j & 1;
-    const uint32_t acc = tmem + (uint32_t)(ab * (L.ncols_tmem / 2));   // accumulator j % 2
-    if (tid == 0) {
-      if (!tc::mbar_wait(&bar_tma[st], (uint32_t)((j / kTcStages) & 1), kWaitPolls)) {
-        sbad = 1;
-      } else {
-        tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_addr(sA(st, 0)), b0 = tc::smem_addr(sB(st, 0));
-        for (int k = 0; k < L.nsteps; ++k)
-          tc::mma_bf16(acc, tc::desc_kmajor(a0 + 256 * k, 128, L.sboA), tc::desc_kmajor(b0 + 256 * k, 128, L.sboB),
-                       idesc, k > 0);
-        if (SPLIT) {
-          const uint32_t a1 = tc::smem_addr(sA(st, 1)), b1 = tc::smem_addr(sB(st, 1));
-          for (int k = 0; k < L.nsteps; ++k) {
-            tc::mma_bf16(acc, tc::desc_kmajor(a0 + 256 * k, 128, L.sboA), tc::desc_kmajor(b1 + 256 * k, 128, L.sboB),
-                         idesc, true);
-            tc::mma_bf16(acc, tc::desc_kmajor(a1 + 256 * k, 128, L.sboA), tc::desc_kmajor(b0 + 256 * k, 128, L.sboB),
-                         idesc, true);
-          }
-        }
-        tc::mma_commit(&bar_mma[ab]);
-        // the stage of pair j - 1 is free (its MMAs completed before its epilogue): tables of j + S - 1
-        if (j >= 1 && j - 1 + kTcStages < nloc) request_tables(j - 1 + kTcStages);
-      }
-    }
-    // right-hand sides of pair j + 1 while pair j's MMAs run
-    if (j + 1 < nloc) {
-      set_info(j + 1);
-      __syncthreads();
-      gather(j + 1);
-    }
-    // epilogue of pair j: thread tid owns TMEM lane tid = row tid: slot tid / 64, row r = tid % 64
-    const bool done = !tc_flag(&sbad) && tc::mbar_wait(&bar_mma[ab], (uint32_t)((j >> 1) & 1), kWaitPolls);
-    if (!done) sbad = 1;
-    tc::fence_after_sync();
-    if (done) {
-      const PairInfo& I = info[st];
-      const int s = warp >> 1, r = tid & 63, c = I.cls[s];
-      const uint32_t tw = acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * L.ncolc);
-      float pw = 0.f;
-      for (int q = 0; q < a.Q; ++q) {
-        float v[8];
-        tmem_ld8(tw + 8 * q, v);   // warp-uniform address: every lane loads, rows past R are dropped
-        if (c >= 0 && r < a.R) {
-          for (int m = 0; m < I.nm[s]; ++m) {
-            const float2 y = make_float2(v[2 * m], v[2 * m + 1]);
-            const long plane = a.jq ? (long)r * a.Q + q : (long)q * a.R + r;
-            a.out[plane * a.ps + I.bin[s][m]] = y;
-            pw = fmaf(I.wt[s][m], y.x * y.x + y.y * y.y, pw);
-          }
-        }
-      }
-      if (a.Pc && c >= 0 && r < a.R) a.Pc[(long)c * a.R + r] = (double)pw;
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tc_flag(&sbad)) break;
-  }
   if (sbad) {
-    // a wait gave up: report it, give in-flight copies and MMAs a bounded chance to land, release TMEM
+    // a wait gave up: report it and give in-flight copies and MMAs a bounded chance to land
     if (tid == 0 && a.info) atomicOr(a.info, FR3D_INFO_TIMEOUT);
-    for (int st = 0; st < kTcStages; ++st) tc::mbar_wait(&bar_tma[st], 0, 1024);
-    tc::mbar_wait(&bar_mma[0], 0, 1024);
-    tc::fence_before_sync();
+    tc::mbar_wait(&acc_ready[0], 0, 1024);
+    tc::mbar_wait(&acc_ready[1], 0, 1024);
     __syncthreads();
   }
   tc::fence_after_sync();
@@ -403,12 +421,12 @@ int tc_launch_config(const void* kern, const TcLayout& L, bool split, int npairs
   std::lock_guard<std::mutex> lock(g_tc_mu);
   for (;;) {
     FR3D_TRY(smem_optin(kern, smem));
-    FR3D_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcThreads, smem));
+    occ = resident_ctas(kern, kTcCtaThreads, smem);
     if (occ <= max_ctas) break;
     smem += 4096;
   }
   if (occ < 1) return FR3D_ERR_UNSUPPORTED_SIZE;
-  out->smem = smem;
+  out->smem = smem;   // (occupancy computed for kTcCtaThreads threads)
   out->grid = std::max(1, std::min(npairs, occ * sms));
   return FR3D_OK;
 }
@@ -420,8 +438,8 @@ int tc_run(const TcArgs& a, const TcAlphas& al, bool split, cudaStream_t st) {
                            : reinterpret_cast<const void*>(k_tc_contract<false>);
   TcLaunch lc;
   FR3D_TRY(tc_launch_config(kern, L, split, npairs, &lc));
-  if (split) k_tc_contract<true><<<lc.grid, kTcThreads, lc.smem, st>>>(a, al);
-  else k_tc_contract<false><<<lc.grid, kTcThreads, lc.smem, st>>>(a, al);
+  if (split) k_tc_contract<true><<<lc.grid, kTcCtaThreads, lc.smem, st>>>(a, al);
+  else k_tc_contract<false><<<lc.grid, kTcCtaThreads, lc.smem, st>>>(a, al);
   FR3D_CUDA_TRY(cudaGetLastError());
   return FR3D_OK;
 }

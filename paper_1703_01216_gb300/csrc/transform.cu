@@ -131,6 +131,29 @@ int twiddle_offset(const Handle* H, int L) {
   return -1;
 }
 
+// CTAs of `kernel` that fit on one SM by its registers, threads and shared memory (the device's full
+// per-SM shared memory; the occupancy calculator's answer depends on the carveout it assumes).
+int resident_ctas(const void* kernel, int threads, size_t dyn_smem) {
+  cudaFuncAttributes fa;
+  int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0, reserved = 0;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;   // allocation unit of 256 registers
+  int n = std::min(blk_sm, thr_sm / std::max(threads, 1));
+  if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
+  const size_t per = dyn_smem + fa.sharedSizeBytes + (size_t)reserved;
+  if (per > 0) n = std::min<int>(n, (int)(smem_sm / per));
+  return std::max(n, 1);
+}
+
 int smem_optin(const void* kernel, size_t bytes) {
   // static shared memory counts against the same 48 KB default, so opt in whenever dynamic memory
   // is used (at most once per kernel and device)

@@ -331,13 +331,13 @@ int launch_cfg(const void* kern, size_t smem, int ncols, int* occ_out) {
   std::lock_guard<std::mutex> lock(g_conv_mu);
   FR3D_TRY(smem_optin(kern, smem));
   int occ = 0;
-  FR3D_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem));
+  occ = resident_ctas(kern, 128, smem);
   // the resident CTAs of an SM must not ask for more than its 512 TMEM columns together
   const int cap = 512 / ncols;
   while (occ > cap) {
     smem += 8192;
     FR3D_TRY(smem_optin(kern, smem));
-    FR3D_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem));
+    occ = resident_ctas(kern, 128, smem);
   }
   if (occ < 1) return FR3D_ERR_UNSUPPORTED_SIZE;
   *occ_out = occ;
