@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(128) k_conv3(ConvArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------ k_wgrad3
-constexpr int kWgStages = 4;
-constexpr int kWgVox = 32;                      // voxels (K) per stage: two MMAs of K = 16
+constexpr int kWgStages = 3;
+constexpr int kWgVox = 64;                      // voxels (K) per stage: four MMAs of K = 16 (a multiple of 16 dividing the range)
 constexpr int kWgPlane = kWgVox * 16;           // bytes of one channel chunk of a stage
 
 __global__ void __launch_bounds__(128) k_wgrad3(WgradArgs a) {
