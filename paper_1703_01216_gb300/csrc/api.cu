@@ -335,7 +335,8 @@ int invert_impl(Handle* H, const T* U, int Q, const fr3d_invert_opts* o, T* out,
         prof_mark(H, kStTable, st);
       }
       const float* Dd = o->alpha_mode == FR3D_ALPHA_FIXED ? H->Ddfix32 : H->Dd32;
-      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, nb, H->wtab, out, Q, 0, H->Mp, o->output, st, out_host_mapped));
+      FR3D_TRY(inv_fused_f32(H, Uh, Dd, aidx, nb, H->wtab, out, Q, 0, H->Mp, o->output, st, out_host_mapped,
+                             o->info));
       prof_mark(H, kStFused, st);
       H->last_launches = launches + 1;
       return FR3D_OK;

@@ -117,10 +117,13 @@ struct Handle {
   // fused-inverse tile variant of the last call, and the autotuner's timings (ms) if it ran
   int fused_var = 0;
   int fused_tuned = 0;
-  float fused_tune_ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  // intermediate of the two-pass inverse (inv2p.cu): [Q][M'][n][n/2] complex, grown outside captures
+  float fused_tune_ms[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // intermediate of the two-pass and the tile-queue inverses (inv2p.cu, inv_queue.cu): Q M' n n/2 complex,
+  // grown outside captures; the tile queue's counters (zeroed at allocation, left zeroed by every launch)
   float2* inv2_buf = nullptr;
   size_t inv2_cap = 0;
+  int* qctl = nullptr;
+  size_t qctl_n = 0;
   // stage profiling: events recorded between consecutive launches of one call
   static constexpr int kMaxEv = 96;
   bool prof_on = false;

@@ -36,6 +36,15 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   r.y = fma_p(a.x, b.y, fmul_p(a.y, b.x));
   return r;
 }
+// float2: the two lanes in one packed FP32x2 operation (one instruction, each lane rounded to nearest
+// like the scalar form, so the results are the same bits)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+      "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&r);
+}
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 // multiply by -i (forward) or +i (inverse)
 template <bool INV, typename C> __device__ __forceinline__ C cmul_mi(C a) {

@@ -116,6 +116,8 @@ struct FusedArgs {
   int Q, j0, Mp;
   const float2* Zs;    // NULL, or solved spectra [Q][M'][n/2+1][n] (1/n^2 folded in): then A, Dd, aidx
                        // are not read and the column phase transforms Zs directly (M > 1 path)
+  int* info = nullptr; // NULL or the caller's info word: a variant whose bounded waits give up ORs
+                       // FR3D_INFO_TIMEOUT into it
 };
 
 // PRE: the column phase transforms the solved spectra a.Zs (M > 1 path) instead of weighting U~.

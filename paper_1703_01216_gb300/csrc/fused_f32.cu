@@ -66,8 +66,9 @@ std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
 
 // variants 0-3: the fused cluster kernel's tiles; 4: the two-pass inverse (inv2p.cu), whose intermediate
-// lives in the handle's inv2 buffer (grown outside stream captures only)
-constexpr int kInvVariants = kFusedVariants + 1;
+// lives in the handle's inv2 buffer (grown outside stream captures only); 5: the persistent tile queue
+// (inv_queue.cu: n = 256, xi output), through the same intermediate and the handle's queue counters
+constexpr int kInvVariants = kFusedVariants + 2;
 
 int ensure_inv2(Handle* H, int Q, int nj, cudaStream_t st, bool* ok) {
   const size_t need = inv2_scratch_bytes(H->n, Q, nj);
@@ -86,6 +87,25 @@ int ensure_inv2(Handle* H, int Q, int nj, cudaStream_t st, bool* ok) {
   return FR3D_OK;
 }
 
+// the queue counters of variant 5 (zeroed once here; every launch leaves them zeroed)
+int ensure_qctl(Handle* H, int nj, int Q, cudaStream_t st, bool* ok) {
+  const size_t need = inv_queue_ctl_ints(nj, Q);
+  *ok = H->qctl_n >= need;
+  if (*ok) return FR3D_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FR3D_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return FR3D_OK;
+  FR3D_CUDA_TRY(cudaStreamSynchronize(st));
+  if (H->qctl) cudaFree(H->qctl);
+  H->qctl = nullptr;
+  H->qctl_n = 0;
+  FR3D_CUDA_TRY(cudaMalloc(&H->qctl, need * sizeof(int)));
+  FR3D_CUDA_TRY(cudaMemset(H->qctl, 0, need * sizeof(int)));
+  H->qctl_n = need;
+  *ok = true;
+  return FR3D_OK;
+}
+
 int launch_variant(Handle* H, int v, int n, bool xi, const FusedArgs& a, int nj, cudaStream_t st) {
   switch (v) {
     case 0: return fused_launch<0>(n, xi, a, nj, st);
@@ -97,6 +117,15 @@ int launch_variant(Handle* H, int v, int n, bool xi, const FusedArgs& a, int nj,
       FR3D_TRY(ensure_inv2(H, a.Q, nj, st, &ok));
       if (!ok) return fused_launch<3>(n, xi, a, nj, st);   // inside a capture without the buffer
       return inv2_launch(n, xi, a, nj, H->inv2_buf, st);
+    }
+    case 5: {
+      // other sizes and outputs, and a first call inside a capture: the register-accumulator tile
+      if (!inv_queue_supported(n, xi) || a.Zs) return fused_launch<3>(n, xi, a, nj, st);
+      bool ok = false, okc = false;
+      FR3D_TRY(ensure_inv2(H, a.Q, nj, st, &ok));
+      FR3D_TRY(ensure_qctl(H, nj, a.Q, st, &okc));
+      if (!ok || !okc) return fused_launch<3>(n, xi, a, nj, st);
+      return inv_queue_launch(n, a, nj, H->inv2_buf, H->qctl, st);
     }
   }
   return FR3D_ERR_INVALID_ARG;
@@ -171,7 +200,7 @@ bool fused_supported(int n) {
 }
 
 int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
-                  float* out, int Q, int j0, int nj, int output, cudaStream_t st, bool out_host_mapped) {
+                  float* out, int Q, int j0, int nj, int output, cudaStream_t st, bool out_host_mapped, int* info) {
   FusedArgs a;
   a.Uh = Uh;
   a.A = H->A32;
@@ -187,6 +216,7 @@ int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int*
   a.j0 = j0;
   a.Mp = H->Mp;
   a.Zs = nullptr;
+  a.info = info;
   const bool xi = output == FR3D_OUT_XI;
   int v = 0;
   FR3D_TRY(choose_variant(const_cast<Handle*>(H), a, nj, xi, out_host_mapped, st, &v));

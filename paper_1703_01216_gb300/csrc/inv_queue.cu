@@ -1,0 +1,431 @@
+// Steps 2-4 of Algorithm 1 at M = 1 (FP32) as one persistent launch over a queue of tiles: the sixth
+// variant of the inverse that the autotuner weighs against the fused cluster kernel (fused.cuh) and the
+// two-pass form (inv2p.cu).  n = 256.
+//
+// The work of a call is a list of tiles, taken in ticket order from one atomic counter:
+//   column tile (j, t)  depth j, packed columns [8t, 8t + 8) (column 0 carries kx = 0 in its real part and
+//                       kx = n/2 in its imaginary part: both columns are Hermitian in ky, so one complex
+//                       DFT gives both): for every source parameter q the solve U~_q w_j and the inverse
+//                       DFT along ky, written to the intermediate T[j][q][y / 16][kx][y % 16];
+//   row tile (j, b)     depth j, rows [16b, 16b + 16): for every q those rows of T, the Hermitian split,
+//                       the inverse row DFT and xi += W_q zeta_q in registers; xi written once.
+// Ordering: the column tiles of depth j come `lag` depths before its row tiles in the ticket order (about
+// as many tiles as the GPU runs at once, so a row tile rarely finds its depth unfinished).  A column tile
+// counts itself on its depth's counter once its stores are done (a release), and a row tile starts once
+// all column tiles of its depth have counted (an acquire, bounded).  Every waiting tile was ticketed
+// after the tiles it waits for, which are running or finished and wait for nothing, so the queue cannot
+// deadlock.  The intermediate of a depth is read about one tile duration after it is written, from L2;
+// a row tile drops each line from L2 once it holds it in shared memory (no line is read twice, so none
+// is written back to HBM), and the combination weights W, read once, are loaded evict-first: only W
+// streams from HBM.
+// Staging: the inputs of every q (a column tile's 8 columns of U~_q, 16 KB, plus column n/2 in tile 0; a
+// row tile's 16 rows of T, 16 KB) arrive by bulk copies two q ahead in double-buffered stages tracked by
+// mbarriers; a row tile's combination weights are loaded into registers one q ahead.  Every wait (on a
+// stage or a counter) is bounded: on expiry the kernel ORs FR3D_INFO_TIMEOUT into the caller's info word
+// and lets every other tile skip its waits, so the launch always ends.
+// The arithmetic of every output is the fused kernel's (solve weights, radix passes and twiddles, the
+// split, the order of the accumulation over q), so all variants return the same bits.
+#include "fused.cuh"
+#include "ops.cuh"
+#include "tc.cuh"
+
+namespace fr3d {
+
+namespace {
+
+constexpr int kQThreads = 128;
+constexpr int kQMinBlocks = 4;        // resident CTAs per SM the registers and shared memory are sized for
+constexpr long kSpinLimit = 1L << 20;  // polls before a wait gives up (a counter poll sleeps at least 128 ns)
+
+template <int N> struct QGeom {
+  static constexpr int L = N / 2;
+  static constexpr int CT = 8;                     // packed columns per column tile
+  static constexpr int NCT = L / CT;               // column tiles per depth
+  static constexpr int RB = 16;                    // rows per row tile
+  static constexpr int NRT = N / RB;               // row tiles per depth
+  static constexpr int SSC = PaddedLen<N, float2>::v;        // column stride (complex) of the column buffer
+  static constexpr int SSR = PaddedLen<L, float2>::v + 1;    // row stride of the row buffer (odd)
+  static constexpr int STG = CT * N;               // complex elements of one stage
+  static constexpr int PTC = passtw_size<N>(), PTR = passtw_size<L>();
+  static constexpr int BUF = CT * SSC > RB * SSR ? CT * SSC : RB * SSR;
+  // per-tile tables: column tile = two stages of column n/2 + pass tables of length n; row tile = split
+  // twiddles (k <= n/2) + pass tables of length n/2
+  static constexpr int TABC = 2 * N + PTC, TABR = L + 1 + PTR;
+  static constexpr int TAB = TABC > TABR ? TABC : TABR;
+  static constexpr size_t head = 32;               // two mbarriers, the broadcast ticket
+  static constexpr size_t smem = head + sizeof(float2) * (2 * (size_t)STG + BUF + TAB);
+  static_assert(STG == RB * L, "a stage holds a column tile's columns or a row tile's rows");
+  static_assert(CT * 16 == kQThreads, "one radix-16 butterfly per thread in the column passes");
+  static_assert(RB * (L / Plan<L>::radix(0)) == kQThreads, "one butterfly per thread in the first row pass");
+};
+
+struct QArgs {
+  FusedArgs f;
+  float2* T;    // [nj][Q][n/16][n/2][16] intermediate
+  int* ctl;     // [0] ticket, [1] CTAs finished, [2] a wait gave up, [4 + j] column tiles of depth j done
+  int nj, lag;
+};
+
+// Tile of ticket k (depth j counted from the call's first depth j0): kind 0 = column tile, 1 = row tile.  Groups s = 0 .. nj - 1 + lag: the column tiles
+// of depth s (s < nj), then the row tiles of depth s - lag (s >= lag).
+template <int N>
+__device__ __forceinline__ void decode_ticket(int k, int nj, int lag, int& kind, int& j, int& t) {
+  using G = QGeom<N>;
+  constexpr int NCT = G::NCT, NRT = G::NRT, NG = NCT + NRT;
+  if (k < lag * NCT) {
+    kind = 0;
+    j = k / NCT;
+    t = k - j * NCT;
+    return;
+  }
+  k -= lag * NCT;
+  if (k < (nj - lag) * NG) {
+    const int s = lag + k / NG, w = k % NG;
+    if (w < NCT) {
+      kind = 0;
+      j = s;
+      t = w;
+    } else {
+      kind = 1;
+      j = s - lag;
+      t = w - NCT;
+    }
+    return;
+  }
+  k -= (nj - lag) * NG;
+  kind = 1;
+  j = nj - lag + k / NRT;
+  t = k % NRT;
+}
+
+__device__ __forceinline__ void report_timeout(const QArgs& qa) {
+  atomicExch(qa.ctl + 2, 1);
+  if (qa.f.info) atomicOr(qa.f.info, FR3D_INFO_TIMEOUT);
+}
+
+// Wait until *c >= target (acquire), or a wait elsewhere has given up; false if this one gave up.
+__device__ __forceinline__ bool wait_count(const QArgs& qa, const int* c, int target) {
+  const volatile int* gave_up = qa.ctl + 2;
+  for (long it = 0; it < kSpinLimit; ++it) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v >= target) return true;
+    if (*gave_up) return true;   // the results are flagged already; do not wait again
+    __nanosleep(128);
+  }
+  report_timeout(qa);
+  return false;
+}
+
+__device__ __forceinline__ void stage_wait(const QArgs& qa, uint64_t* bar, uint32_t& parity) {
+  if (!tc::mbar_wait(bar, parity, kSpinLimit)) report_timeout(qa);
+  parity ^= 1u;
+}
+
+// order this thread's earlier shared-memory accesses (and, through a preceding barrier, the CTA's) before
+// its next bulk copies into shared memory, which run in the async proxy
+__device__ __forceinline__ void fence_proxy_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// the same for global memory: the intermediate, written by other CTAs' generic stores, read by bulk copies
+__device__ __forceinline__ void fence_proxy_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float2 ld_evict_first(const float2* a, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+// drop a 128-byte line of L2 without writing it back (its contents are not needed again)
+__device__ __forceinline__ void l2_discard(const void* a) { asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory"); }
+
+template <int N>
+__device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float2* stage, float2* colbuf,
+                                            float2* tab, uint64_t* bar, uint32_t* par, const int* s_aidx, int tid) {
+  using G = QGeom<N>;
+  constexpr int L = G::L, CT = G::CT, SSC = G::SSC, STG = G::STG;
+  const FusedArgs& a = qa.f;
+  const long ps = (long)(L + 1) * N;
+  float2* stL = tab;              // [2][n] column n/2 of U~_q (tile 0)
+  float2* ptc = tab + 2 * N;      // pass tables of length n
+  const int s = tid >> 4, jj = tid & 15;   // column within the tile, butterfly of the first pass
+  const int kx = CT * t + s;
+  const bool pk = t == 0 && s == 0;        // packed column 0: also carries kx = n/2
+  auto issue = [&](int q, int sl) {
+    const float2* src = a.Uh + (long)q * ps;
+    tc::mbar_arrive_expect_tx(&bar[sl], (uint32_t)(sizeof(float2) * (STG + (t == 0 ? N : 0))));
+    tc::bulk_g2s(stage + sl * STG, src + (long)CT * t * N, (uint32_t)(sizeof(float2) * STG), &bar[sl]);
+    if (t == 0) tc::bulk_g2s(stL + sl * N, src + (long)L * N, (uint32_t)(sizeof(float2) * N), &bar[sl]);
+  };
+  if (tid == 0) {
+    fence_proxy_smem();
+    issue(0, 0);
+    if (a.Q > 1) issue(1, 1);
+  }
+  build_passtw<N, 1, kQThreads>(ptc, a.tw_n, tid);
+  // q-invariant solve weights w_j of this thread's 16 bins (and of column n/2 at the same ky), as the
+  // fused kernel stages them: A_j times the chosen row of the solve table
+  float w[16], wl[16];
+  {
+    const float* Aj = a.A + (long)(a.j0 + j) * ps;
+    int row[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const long o = (long)kx * N + jj + 16 * r;
+      row[r] = a.nb > 1 ? s_aidx[__ldg(a.bbin + o)] : s_aidx[0];
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const long o = (long)kx * N + jj + 16 * r;
+      w[r] = __fmul_rn(__ldg(Aj + o), __ldg(a.Dd + (long)row[r] * ps + o));
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) wl[r] = 0.f;
+    if (pk) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const long o = (long)L * N + jj + 16 * r;
+        const int rw = a.nb > 1 ? s_aidx[__ldg(a.bbin + o)] : s_aidx[0];
+        wl[r] = __fmul_rn(__ldg(Aj + o), __ldg(a.Dd + (long)rw * ps + o));
+      }
+    }
+  }
+  float2* Tj = qa.T + (long)j * a.Q * N * L;
+  for (int q = 0; q < a.Q; ++q) {
+    const int sl = q & 1;
+    stage_wait(qa, &bar[sl], par[sl]);
+    // first pass of the inverse column DFTs from the stage (butterfly jj of column s: bins jj + 16 r)
+    const float2* sg = stage + sl * STG + s * N;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const float2 u = sg[jj + 16 * r];
+      float2 x = make_float2(__fmul_rn(u.x, w[r]), __fmul_rn(u.y, w[r]));
+      if (pk) {   // add i w(n/2, ky) U~(n/2, ky)
+        const float2 un = stL[sl * N + jj + 16 * r];
+        x.x = __fmaf_rn(-un.y, wl[r], x.x);
+        x.y = __fmaf_rn(un.x, wl[r], x.y);
+      }
+      v[r] = x;
+    }
+    Dft<16, true>::run(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) colbuf[s * SSC + pidx<float2>(jj * 16 + r)] = v[r];
+    __syncthreads();   // the column buffer is complete and the stage consumed
+    if (tid == 0 && q + 2 < a.Q) {
+      fence_proxy_smem();
+      issue(q + 2, sl);
+    }
+    // last pass, straight to the intermediate: output y of column s goes to T[j][q][y / 16][kx][y % 16]
+    float2* Tq = Tj + (long)q * N * L;
+    auto emit = [&](int sc, int y, float2 val, int, int) {
+      Tq[((long)(y >> 4) * L + CT * t + sc) * 16 + (y & 15)] = val;
+    };
+    last_pass_to<N, true, CT, kQThreads>(colbuf, SSC, ptc, emit, tid);
+    __syncthreads();   // every store of q is issued and the column buffer is free again
+  }
+  if (tid == 0) {
+    __threadfence();
+    atomicAdd(qa.ctl + 4 + j, 1);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* stage, float2* rowbuf,
+                                         float2* tab, uint64_t* bar, uint32_t* par, uint64_t pol, int tid) {
+  using G = QGeom<N>;
+  constexpr int L = G::L, RB = G::RB, SSR = G::SSR, STG = G::STG, NCT = G::NCT;
+  using LP = LastPass<L>;
+  constexpr int NBF = RB * LP::BPS;
+  constexpr int KR = (NBF + kQThreads - 1) / kQThreads;
+  constexpr int NK = L / 2 + 1;               // Hermitian-split pairs (k, L - k), k <= L/2
+  constexpr int NSPL = RB * NK;
+  constexpr int SIT = (NSPL + kQThreads - 1) / kQThreads;
+  const FusedArgs& a = qa.f;
+  float2* tws = tab;                          // exp(-2 pi i k / n), k <= n/2
+  float2* ptr = tab + (L + 1);                // pass tables of length n/2
+  const float2* Tj = qa.T + (long)j * a.Q * N * L;
+  auto issue = [&](int q, int sl) {
+    tc::mbar_arrive_expect_tx(&bar[sl], (uint32_t)(sizeof(float2) * STG));
+    tc::bulk_g2s(stage + sl * STG, Tj + ((long)q * (N / 16) + b) * L * 16, (uint32_t)(sizeof(float2) * STG), &bar[sl]);
+  };
+  if (tid == 0) {   // once every column tile of depth j has finished
+    wait_count(qa, qa.ctl + 4 + j, NCT);
+    fence_proxy_global();
+    fence_proxy_smem();
+    issue(0, 0);
+    if (a.Q > 1) issue(1, 1);
+  }
+  for (int e = tid; e <= L; e += kQThreads) tws[e] = __ldg(a.tw_n + e);
+  build_passtw<L, 2, kQThreads>(ptr, a.tw_n, tid);
+  float2 acc[KR][LP::R], wv[KR][LP::R];
+#pragma unroll
+  for (int k = 0; k < KR; ++k)
+#pragma unroll
+    for (int rr = 0; rr < LP::R; ++rr) acc[k][rr] = make_float2(0.f, 0.f);
+  // combination weights of q in the layout of the last pass (butterfly (row, jq) owns outputs jq + rr NS)
+  auto load_w = [&](int q) {
+    const float2* wq = reinterpret_cast<const float2*>(a.W + (((long)q * a.Mp + a.j0 + j) * N + b * RB) * N);
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const int bb = tid + k * kQThreads;
+      if (NBF % kQThreads == 0 || bb < NBF) {
+        const int sr = bb / LP::BPS, jq = bb % LP::BPS;
+#pragma unroll
+        for (int rr = 0; rr < LP::R; ++rr) wv[k][rr] = ld_evict_first(wq + sr * L + jq + rr * LP::NS, pol);
+      }
+    }
+  };
+  load_w(0);
+  __syncthreads();   // tables
+  for (int q = 0; q < a.Q; ++q) {
+    const int sl = q & 1;
+    stage_wait(qa, &bar[sl], par[sl]);
+    // the rows of T are in shared memory now: drop their lines from L2 (one 128-byte line per thread)
+    static_assert(STG * sizeof(float2) == 128 * kQThreads, "one line per thread");
+    l2_discard(Tj + ((long)q * (N / 16) + b) * L * 16 + tid * 16);
+    const float2* sg = stage + sl * STG;      // [kx][row]
+    // Hermitian split Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), pairs (k, L - k)
+    float2 xa[SIT], xb[SIT];
+#pragma unroll
+    for (int i = 0; i < SIT; ++i) {
+      const int e = tid + i * kQThreads;
+      if (NSPL % kQThreads == 0 || e < NSPL) {
+        const int row = e % RB, k = e / RB;
+        const float2 u = sg[k * RB + row];
+        const float2 v = sg[(k == 0 ? 0 : L - k) * RB + row];
+        xa[i] = k == 0 ? make_float2(u.x, 0.f) : u;   // X(0): real part of column 0
+        xb[i] = k == 0 ? make_float2(v.y, 0.f) : v;   // X(n/2): its imaginary part
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < SIT; ++i) {
+      const int e = tid + i * kQThreads;
+      if (NSPL % kQThreads == 0 || e < NSPL) {
+        const int row = e % RB, k = e / RB;
+        float2* rw = rowbuf + row * SSR;
+        {
+          const float2 sum = cadd(xa[i], cconj(xb[i])), dif = csub(xa[i], cconj(xb[i]));
+          rw[pidx<float2>(k)] = cadd(sum, cmul_mi<true>(cmul(cconj(tws[k]), dif)));
+        }
+        if (k != 0 && 2 * k != L) {
+          const float2 sum = cadd(xb[i], cconj(xa[i])), dif = csub(xb[i], cconj(xa[i]));
+          rw[pidx<float2>(L - k)] = cadd(sum, cmul_mi<true>(cmul(cconj(tws[L - k]), dif)));
+        }
+      }
+    }
+    __syncthreads();   // the row buffer is complete and the stage consumed
+    if (tid == 0 && q + 2 < a.Q) {
+      fence_proxy_smem();
+      issue(q + 2, sl);
+    }
+    fft_passes<L, true, RB, kQThreads, 0, Plan<L>::np - 1>(rowbuf, SSR, ptr, tid);
+    // fmaf(w, v, 0) for q = 0, as in the accumulators of the other variants
+    auto emit = [&](int, int, float2 v, int k, int rr) {
+      acc[k][rr] = make_float2(fmaf(wv[k][rr].x, v.x, acc[k][rr].x), fmaf(wv[k][rr].y, v.y, acc[k][rr].y));
+    };
+    last_pass_to<L, true, RB, kQThreads>(rowbuf, SSR, ptr, emit, tid);
+    if (q + 1 < a.Q) load_w(q + 1);   // in flight during the next q's split and passes
+    __syncthreads();   // the last pass has read the row buffer
+  }
+  float2* ov = reinterpret_cast<float2*>(a.out + ((long)(a.j0 + j) * N + b * RB) * N);
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const int bb = tid + k * kQThreads;
+    if (NBF % kQThreads == 0 || bb < NBF) {
+      const int sr = bb / LP::BPS, jq = bb % LP::BPS;
+#pragma unroll
+      for (int rr = 0; rr < LP::R; ++rr) ov[sr * L + jq + rr * LP::NS] = acc[k][rr];
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kQThreads, kQMinBlocks) k_inv_queue(QArgs qa) {
+  using G = QGeom<N>;
+  const FusedArgs& a = qa.f;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  int* s_tick = reinterpret_cast<int*>(smem_raw + 16);
+  float2* stage = reinterpret_cast<float2*>(smem_raw + G::head);
+  float2* buf = stage + 2 * G::STG;
+  float2* tab = buf + G::BUF;
+  __shared__ int s_aidx[FR3D_MAX_BANDS];
+  const int tid = threadIdx.x;
+  const int total = qa.nj * (G::NCT + G::NRT);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::mbar_fence_init();
+  }
+  uint32_t par[2] = {0u, 0u};   // parity of each stage barrier's next completion
+  const uint64_t pol = evict_first_policy();
+  pdl_wait();   // the data spectra, the chosen alpha index and the queue counters of the previous call
+  if (tid < a.nb) s_aidx[tid] = min(max(a.aidx[tid], 0), a.na - 1);
+  for (;;) {
+    if (tid == 0) *s_tick = atomicAdd(qa.ctl, 1);
+    __syncthreads();   // the ticket; also orders the previous tile's last reads before this tile's writes
+    const int tick = *s_tick;
+    if (tick >= total) break;
+    int kind, j, t;
+    decode_ticket<N>(tick, qa.nj, qa.lag, kind, j, t);
+    if (kind == 0) column_tile<N>(qa, j, t, stage, buf, tab, bar, par, s_aidx, tid);
+    else row_tile<N>(qa, j, t, stage, buf, tab, bar, par, pol, tid);
+    __syncthreads();   // before thread 0 overwrites the ticket
+  }
+  // the last CTA to finish resets the queue for the next call
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(qa.ctl + 1, 1) == (int)gridDim.x - 1) {
+      __threadfence();
+      qa.ctl[0] = 0;
+      qa.ctl[2] = 0;
+      for (int e = 0; e < qa.nj; ++e) qa.ctl[4 + e] = 0;
+      __threadfence();
+      qa.ctl[1] = 0;
+    }
+  }
+}
+
+}  // namespace
+
+bool inv_queue_supported(int n, bool xi) { return n == 256 && xi; }
+
+size_t inv_queue_ctl_ints(int nj, int) { return 4 + (size_t)nj; }
+
+// T: the intermediate ([nj][Q][n][n/2] complex, inv2_scratch_bytes); ctl: inv_queue_ctl_ints(nj, Q) zeroed
+// ints (the kernel leaves them zeroed).
+int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cudaStream_t st) {
+  if (!inv_queue_supported(n, true) || f.Zs) return FR3D_ERR_UNSUPPORTED_SIZE;
+  using G = QGeom<256>;
+  const void* kern = reinterpret_cast<const void*>(k_inv_queue<256>);
+  FR3D_TRY(smem_optin(kern, G::smem));
+  static int grid_per_sm = 0;
+  if (grid_per_sm == 0) grid_per_sm = std::max(1, resident_ctas(kern, kQThreads, G::smem));
+  int dev = 0, sms = 0;
+  FR3D_CUDA_TRY(cudaGetDevice(&dev));
+  FR3D_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  QArgs qa;
+  qa.f = f;
+  qa.T = T;
+  qa.ctl = ctl;
+  qa.nj = nj;
+  qa.lag = std::min(20, nj);
+  const int total = nj * (G::NCT + G::NRT);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(std::min(total, grid_per_sm * sms));
+  cfg.blockDim = dim3(kQThreads);
+  cfg.dynamicSmemBytes = G::smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FR3D_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_inv_queue<256>, qa));
+  return FR3D_OK;
+}
+
+}  // namespace fr3d

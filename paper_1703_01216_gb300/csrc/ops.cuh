@@ -45,12 +45,19 @@ template <typename T> struct Ops {
 // the variants that write every output once)
 bool fused_supported(int n);
 int inv_fused_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
-                  float* out, int Q, int j0, int nj, int output, cudaStream_t st, bool out_host_mapped = false);
+                  float* out, int Q, int j0, int nj, int output, cudaStream_t st, bool out_host_mapped = false,
+                  int* info = nullptr);
 // the two-pass inverse (inv2p.cu): column pass with the solve, row pass with the combination; T holds
 // inv2_scratch_bytes(n, Q, nj)
 struct FusedArgs;
 size_t inv2_scratch_bytes(int n, int Q, int nj);
 int inv2_launch(int n, bool xi, const FusedArgs& f, int nj, float2* T, cudaStream_t st);
+// The persistent tile-queue inverse (inv_queue.cu): n = 256, xi output, U~ input (no solved spectra).
+// T: the two-pass intermediate (inv2_scratch_bytes); ctl: inv_queue_ctl_ints(nj, Q) ints, zeroed once at
+// allocation (every launch leaves them zeroed).
+bool inv_queue_supported(int n, bool xi);
+size_t inv_queue_ctl_ints(int nj, int Q);
+int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cudaStream_t st);
 // W_q = V0_q / sum_q' V0_q'^2 on the R grid for the handle's cached sources
 int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st);
 

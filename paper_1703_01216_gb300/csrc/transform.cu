@@ -320,7 +320,7 @@ void handle_free(Handle* H) {
   void* ptrs[] = {H->A64, H->nrm, H->s2, H->A32, H->A64d, H->tw32, H->tw64, H->Ft, H->D32, H->D64,
                   H->Dfix32, H->Dfix64, H->zr64, H->zr32, H->wtab, H->Dd32, H->Ddfix32, H->pts32, H->pts64, H->counter, H->idx_scratch, H->zero_idx,
                   H->info_scratch, H->partials, H->cband, H->bbin, H->mlam, H->mUt, H->mW, H->rhs_buf, H->ws,
-                  H->inv2_buf};
+                  H->inv2_buf, H->qctl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 3; ++k) {

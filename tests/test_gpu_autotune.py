@@ -1,5 +1,5 @@
-"""Variants of the inverse (steps 2-4) and their autotuner: the four tiles of the fused cluster kernel and
-the two-pass inverse give the same bits (the same butterflies, with every product and fused multiply-add
+"""Variants of the inverse (steps 2-4) and their autotuner: the four tiles of the fused cluster kernel, the
+two-pass inverse and the persistent tile queue give the same bits (the same butterflies, with every product and fused multiply-add
 pinned so that no kernel contracts them differently; single calls and batched plans), the oracle agrees,
 and the tuner times every variant and keeps one."""
 
@@ -11,7 +11,8 @@ from paper_1703_01216_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-NV = 5   # 0: shared-memory xi, 1-2: xi in the output array, 3: in registers (fused tiles); 4: two passes
+NV = 6   # 0: shared-memory xi, 1-2: xi in the output array, 3: in registers (fused tiles); 4: two passes;
+         # 5: tile queue (n = 256 with xi output; the register tile elsewhere)
 
 
 @pytest.fixture(scope="module")

@@ -96,7 +96,7 @@ def test_tuner_keeps_write_once_variants_for_mapped_output(F):
     oh = torch.empty((7, 96, 96), dtype=torch.float32).pin_memory()
     F.invert_host(H, uh, 3, oh, opts)
     v, ms = F.autotune_query(H)
-    assert v in (0, 3, 4)                    # the variants that write every output once
+    assert v in (0, 3, 4, 5)                 # the variants that write every output once
     assert ms[1] == 0 and ms[2] == 0 and ms[0] > 0 and ms[3] > 0 and ms[4] > 0
     od = torch.empty((7, 96, 96), device="cuda")
     F.invert(H, torch.as_tensor(U, dtype=torch.float32, device="cuda"), 3, od, opts)
