@@ -48,15 +48,16 @@ template <int N> struct QGeom {
   static constexpr int STG = CT * N;               // complex elements of one stage
   static constexpr int PTC = passtw_size<N>(), PTR = passtw_size<L>();
   static constexpr int BUF = CT * SSC > RB * SSR ? CT * SSC : RB * SSR;
-  // per-tile tables: column tile = two stages of column n/2 + pass tables of length n; row tile = split
-  // twiddles (k <= n/2) + pass tables of length n/2
-  static constexpr int TABC = 2 * N + PTC, TABR = L + 1 + PTR;
+  // per-tile tables: column tile = two stages of column n/2 + pass tables of length n; row tile = pass
+  // tables of length n/2
+  static constexpr int TABC = 2 * N + PTC, TABR = PTR;
   static constexpr int TAB = TABC > TABR ? TABC : TABR;
   static constexpr size_t head = 32;               // two mbarriers, the broadcast ticket
   static constexpr size_t smem = head + sizeof(float2) * (2 * (size_t)STG + BUF + TAB);
   static_assert(STG == RB * L, "a stage holds a column tile's columns or a row tile's rows");
   static_assert(CT * 16 == kQThreads, "one radix-16 butterfly per thread in the column passes");
-  static_assert(RB * (L / Plan<L>::radix(0)) == kQThreads, "one butterfly per thread in the first row pass");
+  static_assert(Plan<L>::np == 2 && Plan<L>::radix(0) == 16, "the row DFT: a radix-16 first pass, then the last pass");
+  static_assert(Plan<N>::np == 2 && Plan<N>::radix(0) == 16, "the column DFT: a radix-16 first pass, then the last pass");
 };
 
 struct QArgs {
@@ -141,22 +142,36 @@ __device__ __forceinline__ float2 ld_evict_first(const float2* a, uint64_t pol) 
 // drop a 128-byte line of L2 without writing it back (its contents are not needed again)
 __device__ __forceinline__ void l2_discard(const void* a) { asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory"); }
 
+// Column of stage slot c of column tile t: warp w handles the pair p = 4t + w of columns whose
+// Hermitian-split partners they are, p and n/2 - p (p >= 1), or column 0 (packed: also kx = n/2) and
+// column n/4, which are their own partners (p = 0); slot 2w + s holds the pair's column s.
+template <int N> __device__ __forceinline__ int pair_column(int t, int c) {
+  constexpr int L = N / 2;
+  const int p = (kQThreads / 32) * t + (c >> 1), s = c & 1;
+  return p == 0 ? (s == 0 ? 0 : L / 2) : (s == 0 ? p : L - p);
+}
+
 template <int N>
 __device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float2* stage, float2* colbuf,
                                             float2* tab, uint64_t* bar, uint32_t* par, const int* s_aidx, int tid) {
   using G = QGeom<N>;
   constexpr int L = G::L, CT = G::CT, SSC = G::SSC, STG = G::STG;
+  static_assert(CT == 2 * (kQThreads / 32), "two columns per warp");
   const FusedArgs& a = qa.f;
   const long ps = (long)(L + 1) * N;
   float2* stL = tab;              // [2][n] column n/2 of U~_q (tile 0)
   float2* ptc = tab + 2 * N;      // pass tables of length n
-  const int s = tid >> 4, jj = tid & 15;   // column within the tile, butterfly of the first pass
-  const int kx = CT * t + s;
-  const bool pk = t == 0 && s == 0;        // packed column 0: also carries kx = n/2
+  const int c = tid >> 4, jj = tid & 15;   // stage slot (column) and butterfly of the first pass
+  const int kx = pair_column<N>(t, c);
+  const bool pk = kx == 0;                 // packed column 0: also carries kx = n/2
+  const bool self = t == 0 && (c >> 1) == 0;   // columns 0 and n/4 are their own split partners
   auto issue = [&](int q, int sl) {
     const float2* src = a.Uh + (long)q * ps;
     tc::mbar_arrive_expect_tx(&bar[sl], (uint32_t)(sizeof(float2) * (STG + (t == 0 ? N : 0))));
-    tc::bulk_g2s(stage + sl * STG, src + (long)CT * t * N, (uint32_t)(sizeof(float2) * STG), &bar[sl]);
+#pragma unroll
+    for (int cc = 0; cc < CT; ++cc)
+      tc::bulk_g2s(stage + sl * STG + cc * N, src + (long)pair_column<N>(t, cc) * N, (uint32_t)(sizeof(float2) * N),
+                   &bar[sl]);
     if (t == 0) tc::bulk_g2s(stL + sl * N, src + (long)L * N, (uint32_t)(sizeof(float2) * N), &bar[sl]);
   };
   if (tid == 0) {
@@ -166,8 +181,9 @@ __device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float
   }
   build_passtw<N, 1, kQThreads>(ptc, a.tw_n, tid);
   // q-invariant solve weights w_j of this thread's 16 bins (and of column n/2 at the same ky), as the
-  // fused kernel stages them: A_j times the chosen row of the solve table
+  // fused kernel stages them: A_j times the chosen row of the solve table; the split twiddle w^kx
   float w[16], wl[16];
+  const float2 twk = __ldg(a.tw_n + kx);
   {
     const float* Aj = a.A + (long)(a.j0 + j) * ps;
     int row[16];
@@ -196,8 +212,8 @@ __device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float
   for (int q = 0; q < a.Q; ++q) {
     const int sl = q & 1;
     stage_wait(qa, &bar[sl], par[sl]);
-    // first pass of the inverse column DFTs from the stage (butterfly jj of column s: bins jj + 16 r)
-    const float2* sg = stage + sl * STG + s * N;
+    // first pass of the inverse column DFTs from the stage (butterfly jj of column c: bins jj + 16 r)
+    const float2* sg = stage + sl * STG + c * N;
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -212,19 +228,34 @@ __device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float
     }
     Dft<16, true>::run(v);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) colbuf[s * SSC + pidx<float2>(jj * 16 + r)] = v[r];
+    for (int r = 0; r < 16; ++r) colbuf[c * SSC + pidx<float2>(jj * 16 + r)] = v[r];
     __syncthreads();   // the column buffer is complete and the stage consumed
     if (tid == 0 && q + 2 < a.Q) {
       fence_proxy_smem();
       issue(q + 2, sl);
     }
-    // last pass, straight to the intermediate: output y of column s goes to T[j][q][y / 16][kx][y % 16]
-    float2* Tq = Tj + (long)q * N * L;
-    auto emit = [&](int sc, int y, float2 val, int, int) {
-      Tq[((long)(y >> 4) * L + CT * t + sc) * 16 + (y & 15)] = val;
-    };
+    // last pass: X(kx, y) for y = jj + 16 r
+    auto emit = [&](int, int, float2 val, int, int r) { v[r] = val; };
     last_pass_to<N, true, CT, kQThreads>(colbuf, SSC, ptc, emit, tid);
-    __syncthreads();   // every store of q is issued and the column buffer is free again
+    // Hermitian split of the row sequences, Z'(kx, y) = (X[kx] + conj X[L-kx]) + i w^-kx (X[kx] - conj X[L-kx])
+    // with X[L-kx] from the partner column (the lane 16 apart), stored to T[j][q][y / 16][kx][y % 16]
+    float2* Tq = Tj + (long)q * N * L;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const float2 own = v[r];
+      float2 oth;
+      oth.x = __shfl_xor_sync(0xffffffffu, own.x, 16);
+      oth.y = __shfl_xor_sync(0xffffffffu, own.y, 16);
+      float2 xa = own, xb = self ? own : oth;
+      if (pk) {   // X(0) and X(n/2): the real and imaginary parts of column 0
+        xa = make_float2(own.x, 0.f);
+        xb = make_float2(own.y, 0.f);
+      }
+      const float2 sum = cadd(xa, cconj(xb)), dif = csub(xa, cconj(xb));
+      const int y = jj + 16 * r;
+      Tq[((long)(y >> 4) * L + kx) * 16 + (y & 15)] = cadd(sum, cmul_mi<true>(cmul(cconj(twk), dif)));
+    }
+    __syncthreads();   // the column buffer is free again
   }
   if (tid == 0) {
     __threadfence();
@@ -240,12 +271,8 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
   using LP = LastPass<L>;
   constexpr int NBF = RB * LP::BPS;
   constexpr int KR = (NBF + kQThreads - 1) / kQThreads;
-  constexpr int NK = L / 2 + 1;               // Hermitian-split pairs (k, L - k), k <= L/2
-  constexpr int NSPL = RB * NK;
-  constexpr int SIT = (NSPL + kQThreads - 1) / kQThreads;
   const FusedArgs& a = qa.f;
-  float2* tws = tab;                          // exp(-2 pi i k / n), k <= n/2
-  float2* ptr = tab + (L + 1);                // pass tables of length n/2
+  float2* ptr = tab;                          // pass tables of length n/2
   const float2* Tj = qa.T + (long)j * a.Q * N * L;
   auto issue = [&](int q, int sl) {
     tc::mbar_arrive_expect_tx(&bar[sl], (uint32_t)(sizeof(float2) * STG));
@@ -258,7 +285,6 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
     issue(0, 0);
     if (a.Q > 1) issue(1, 1);
   }
-  for (int e = tid; e <= L; e += kQThreads) tws[e] = __ldg(a.tw_n + e);
   build_passtw<L, 2, kQThreads>(ptr, a.tw_n, tid);
   float2 acc[KR][LP::R], wv[KR][LP::R];
 #pragma unroll
@@ -278,6 +304,13 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
       }
     }
   };
+  auto prefetch_w = [&](int q) {   // the tile's rows of W_q into L2, so that the register loads hit there
+    const float* src = a.W + (((long)q * a.Mp + a.j0 + j) * N + b * RB) * N;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((uint32_t)(RB * N * sizeof(float)))
+                 : "memory");
+  };
+  if (tid == 0)
+    for (int q = 0; q < 3 && q < a.Q; ++q) prefetch_w(q);
   load_w(0);
   __syncthreads();   // tables
   for (int q = 0; q < a.Q; ++q) {
@@ -286,49 +319,33 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
     // the rows of T are in shared memory now: drop their lines from L2 (one 128-byte line per thread)
     static_assert(STG * sizeof(float2) == 128 * kQThreads, "one line per thread");
     l2_discard(Tj + ((long)q * (N / 16) + b) * L * 16 + tid * 16);
-    const float2* sg = stage + sl * STG;      // [kx][row]
-    // Hermitian split Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), pairs (k, L - k)
-    float2 xa[SIT], xb[SIT];
+    float2* sg = stage + sl * STG;            // Z'[k][row], split by the column tiles
+    // first pass (radix 16, no twiddles) from the stage into the row buffer, the threads running over the
+    // rows first: butterfly jb of a row reads jb + (n/32) r and writes 16 jb + r
+    {
+      constexpr int BPS0 = L / 16;
+      static_assert(RB * BPS0 == kQThreads, "one first-pass butterfly per thread");
+      const int row = tid % RB, jb = tid / RB;
+      float2 v[16];
 #pragma unroll
-    for (int i = 0; i < SIT; ++i) {
-      const int e = tid + i * kQThreads;
-      if (NSPL % kQThreads == 0 || e < NSPL) {
-        const int row = e % RB, k = e / RB;
-        const float2 u = sg[k * RB + row];
-        const float2 v = sg[(k == 0 ? 0 : L - k) * RB + row];
-        xa[i] = k == 0 ? make_float2(u.x, 0.f) : u;   // X(0): real part of column 0
-        xb[i] = k == 0 ? make_float2(v.y, 0.f) : v;   // X(n/2): its imaginary part
-      }
-    }
+      for (int r = 0; r < 16; ++r) v[r] = sg[(jb + BPS0 * r) * RB + row];
+      Dft<16, true>::run(v);
+      float2* rw = rowbuf + row * SSR;
 #pragma unroll
-    for (int i = 0; i < SIT; ++i) {
-      const int e = tid + i * kQThreads;
-      if (NSPL % kQThreads == 0 || e < NSPL) {
-        const int row = e % RB, k = e / RB;
-        float2* rw = rowbuf + row * SSR;
-        {
-          const float2 sum = cadd(xa[i], cconj(xb[i])), dif = csub(xa[i], cconj(xb[i]));
-          rw[pidx<float2>(k)] = cadd(sum, cmul_mi<true>(cmul(cconj(tws[k]), dif)));
-        }
-        if (k != 0 && 2 * k != L) {
-          const float2 sum = cadd(xb[i], cconj(xa[i])), dif = csub(xb[i], cconj(xa[i]));
-          rw[pidx<float2>(L - k)] = cadd(sum, cmul_mi<true>(cmul(cconj(tws[L - k]), dif)));
-        }
-      }
+      for (int r = 0; r < 16; ++r) rw[pidx<float2>(16 * jb + r)] = v[r];
     }
     __syncthreads();   // the row buffer is complete and the stage consumed
     if (tid == 0 && q + 2 < a.Q) {
       fence_proxy_smem();
       issue(q + 2, sl);
     }
-    fft_passes<L, true, RB, kQThreads, 0, Plan<L>::np - 1>(rowbuf, SSR, ptr, tid);
     // fmaf(w, v, 0) for q = 0, as in the accumulators of the other variants
     auto emit = [&](int, int, float2 v, int k, int rr) {
       acc[k][rr] = make_float2(fmaf(wv[k][rr].x, v.x, acc[k][rr].x), fmaf(wv[k][rr].y, v.y, acc[k][rr].y));
     };
     last_pass_to<L, true, RB, kQThreads>(rowbuf, SSR, ptr, emit, tid);
+    if (tid == 0 && q + 3 < a.Q) prefetch_w(q + 3);
     if (q + 1 < a.Q) load_w(q + 1);   // in flight during the next q's split and passes
-    __syncthreads();   // the last pass has read the row buffer
   }
   float2* ov = reinterpret_cast<float2*>(a.out + ((long)(a.j0 + j) * N + b * RB) * N);
 #pragma unroll
@@ -412,7 +429,7 @@ int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cud
   qa.T = T;
   qa.ctl = ctl;
   qa.nj = nj;
-  qa.lag = std::min(20, nj);
+  qa.lag = std::min(36, nj);
   const int total = nj * (G::NCT + G::NRT);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::min(total, grid_per_sm * sms));
