@@ -297,12 +297,15 @@ int fr3d_band_alpha_targets(fr3d_handle* h, const float* U, const float* zeta_tr
                             const double* alphas, int n_alpha, int n_bands, int* idx, float* target,
                             double* err, void* stream);
 
-/* ---- autotuner of the fused inverse (steps 2-4 in one kernel, FP32, M = 1) ----
- * The fused inverse has tile variants that compute the same bits (variant 0: the built-in table of
- * cluster size, threads and row-batch height per n with xi accumulated in shared memory; 1: xi
- * accumulated in the output array with taller row batches where they fit; 2: xi in the output
- * array, table batches; 3: one row batch of all a CTA's rows, xi accumulated in registers and
- * written once).  Modes: 0 = always variant 0; 1 (default) = on the first fr3d_invert of a
+/* ---- autotuner of the inverse (steps 2-4, FP32, M = 1) ----
+ * The inverse has variants that compute the same bits: the fused cluster kernel's tiles (variant 0: the
+ * built-in table of cluster size, threads and row-batch height per n with xi accumulated in shared
+ * memory; 1: xi accumulated in the output array with taller row batches where they fit; 2: xi in the
+ * output array, table batches; 3: one row batch of all a CTA's rows, xi accumulated in registers and
+ * written once); 4: two streaming passes through an intermediate in a handle-owned buffer; 5: one
+ * persistent launch over a queue of column and row tiles through the same intermediate, served from L2
+ * (n = 256 with xi output; other shapes run variant 3).  Variants 4 and 5 allocate their buffer on the
+ * first call outside a stream capture (inside a capture before that, they run variant 3).  Modes: 0 = always variant 0; 1 (default) = on the first fr3d_invert of a
  * shape (device, n, M', Q, output) made outside a stream capture, time every variant on that
  * call's own arguments (1 warm-up + 3 timed launches each, synchronising the stream once) and use
  * the fastest from then on, process-wide; 2 + v = always variant v.  A batched plan (mode 1) times
@@ -314,6 +317,11 @@ int fr3d_autotune_mode(int mode);
 /* The variant that the handle's last fused inverse used, and (ms, up to cap entries) the per-launch
  * times the tuner measured on this handle (0 if it did not tune here).  Returns the variant count. */
 int fr3d_autotune_query(fr3d_handle* h, int* variant, float* ms, int cap);
+/* Test hook of variant 5's bounded waits: while on != 0, its column tiles withhold the counts that release
+ * the intermediate to the row tiles, so the row tiles' waits run out (after about a second): the call
+ * still returns, with FR3D_INFO_TIMEOUT set in the info word, and its xi is not valid.  No fault and no
+ * hang is involved; the next call with the hook off is exact again.  Returns the previous setting. */
+int fr3d_test_withhold_queue_counts(int on);
 
 /* ---- learned post-corrector: a 3D U-Net on the tensor cores (fr3d_unet) ----
  * The paper has no network.  This one post-corrects the reconstruction of fr3d_invert: with one observation

@@ -3,28 +3,35 @@
 // two-pass form (inv2p.cu).  n = 256.
 //
 // The work of a call is a list of tiles, taken in ticket order from one atomic counter:
-//   column tile (j, t)  depth j, packed columns [8t, 8t + 8) (column 0 carries kx = 0 in its real part and
-//                       kx = n/2 in its imaginary part: both columns are Hermitian in ky, so one complex
-//                       DFT gives both): for every source parameter q the solve U~_q w_j and the inverse
-//                       DFT along ky, written to the intermediate T[j][q][y / 16][kx][y % 16];
-//   row tile (j, b)     depth j, rows [16b, 16b + 16): for every q those rows of T, the Hermitian split,
-//                       the inverse row DFT and xi += W_q zeta_q in registers; xi written once.
-// Ordering: the column tiles of depth j come `lag` depths before its row tiles in the ticket order (about
-// as many tiles as the GPU runs at once, so a row tile rarely finds its depth unfinished).  A column tile
-// counts itself on its depth's counter once its stores are done (a release), and a row tile starts once
-// all column tiles of its depth have counted (an acquire, bounded).  Every waiting tile was ticketed
-// after the tiles it waits for, which are running or finished and wait for nothing, so the queue cannot
-// deadlock.  The intermediate of a depth is read about one tile duration after it is written, from L2;
-// a row tile drops each line from L2 once it holds it in shared memory (no line is read twice, so none
-// is written back to HBM), and the combination weights W, read once, are loaded evict-first: only W
-// streams from HBM.
+//   column tile (j, t)  depth j, four pairs of packed columns (kx, n/2 - kx), which are each other's
+//                       partners in the Hermitian split of the rows (the pair (0, n/4) is its own: column
+//                       0 carries kx = 0 in its real part and kx = n/2 in its imaginary part, both
+//                       Hermitian in ky, so one complex DFT gives both); for every source parameter q the
+//                       solve U~_q w_j, the inverse DFT along ky, and the split
+//                       Z'(kx, y) = (X[kx] + conj X[n/2-kx]) + i w^-kx (X[kx] - conj X[n/2-kx]) with the
+//                       partner's value from the lane 16 apart, written to the intermediate
+//                       T[j][q][y / 16][kx][y % 16];
+//   row tile (j, b)     depth j, rows [16b, 16b + 16): for every q those rows of T, the n/2-point inverse
+//                       row DFT and xi += W_q zeta_q in registers; xi written once.
+// Ordering: the column tiles of depth j come `lag` depths before its row tiles in the ticket order.  A
+// column tile counts itself on its depth's first counter once it has stored the first half of the q
+// (a release), and on the second once it has stored all; a row tile requests the rows of the first half
+// once all column tiles of its depth have counted on the first, and those of the second half once they
+// have counted on the second (acquires, bounded).  Every waiting tile was ticketed after the tiles it
+// waits for, which are running or finished and wait for nothing, so the queue cannot deadlock.  The
+// intermediate of a depth is read about one tile duration after it is written, from L2; a row tile drops
+// each line from L2 once it holds it in shared memory (no line is read twice, so none needs writing back
+// to HBM), and the combination weights W, read once, are prefetched into L2 by bulk prefetches three q
+// ahead and loaded into registers one q ahead with an evict-first policy.
 // Staging: the inputs of every q (a column tile's 8 columns of U~_q, 16 KB, plus column n/2 in tile 0; a
 // row tile's 16 rows of T, 16 KB) arrive by bulk copies two q ahead in double-buffered stages tracked by
-// mbarriers; a row tile's combination weights are loaded into registers one q ahead.  Every wait (on a
-// stage or a counter) is bounded: on expiry the kernel ORs FR3D_INFO_TIMEOUT into the caller's info word
-// and lets every other tile skip its waits, so the launch always ends.
-// The arithmetic of every output is the fused kernel's (solve weights, radix passes and twiddles, the
-// split, the order of the accumulation over q), so all variants return the same bits.
+// mbarriers.  Every wait (on a stage or a counter) is bounded: on expiry the kernel ORs
+// FR3D_INFO_TIMEOUT into the caller's info word and lets every other wait end at once, so the launch
+// always ends.
+// The arithmetic of every output (the solve weights, the radix passes and their twiddles, the split, the
+// order of the accumulation over q) is the fused kernel's, so all variants return the same bits.
+#include <atomic>
+
 #include "fused.cuh"
 #include "ops.cuh"
 #include "tc.cuh"
@@ -63,8 +70,10 @@ template <int N> struct QGeom {
 struct QArgs {
   FusedArgs f;
   float2* T;    // [nj][Q][n/16][n/2][16] intermediate
-  int* ctl;     // [0] ticket, [1] CTAs finished, [2] a wait gave up, [4 + j] column tiles of depth j done
+  int* ctl;     // [0] ticket, [1] CTAs finished, [2] a wait gave up, [4 + 2j + h] column tiles of depth j done
+                // with the first (h = 0) or with every (h = 1) half of the source parameters
   int nj, lag;
+  int withhold;   // test hook: column tiles do not count themselves (the row tiles' waits run out)
 };
 
 // Tile of ticket k (depth j counted from the call's first depth j0): kind 0 = column tile, 1 = row tile.  Groups s = 0 .. nj - 1 + lag: the column tiles
@@ -98,6 +107,9 @@ __device__ __forceinline__ void decode_ticket(int k, int nj, int lag, int& kind,
   j = nj - lag + k / NRT;
   t = k % NRT;
 }
+
+// source parameters of the first half (the first dependency step of a row tile)
+__device__ __forceinline__ int half_q(int Q) { return Q > 1 ? Q / 2 : 1; }
 
 __device__ __forceinline__ void report_timeout(const QArgs& qa) {
   atomicExch(qa.ctl + 2, 1);
@@ -255,11 +267,15 @@ __device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float
       const int y = jj + 16 * r;
       Tq[((long)(y >> 4) * L + kx) * 16 + (y & 15)] = cadd(sum, cmul_mi<true>(cmul(cconj(twk), dif)));
     }
+    // release of a half of the q: every thread makes its own stores visible GPU-wide (a fence orders only
+    // the issuing thread's writes; the barrier below only orders their issue), then one thread counts
+    const bool release = q == half_q(a.Q) - 1 || q == a.Q - 1;
+    if (release) __threadfence();
     __syncthreads();   // the column buffer is free again
-  }
-  if (tid == 0) {
-    __threadfence();
-    atomicAdd(qa.ctl + 4 + j, 1);
+    if (tid == 0 && release && !qa.withhold) {
+      if (q == half_q(a.Q) - 1) atomicAdd(qa.ctl + 4 + 2 * j, 1);
+      if (q == a.Q - 1) atomicAdd(qa.ctl + 4 + 2 * j + 1, 1);
+    }
   }
 }
 
@@ -274,14 +290,17 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
   const FusedArgs& a = qa.f;
   float2* ptr = tab;                          // pass tables of length n/2
   const float2* Tj = qa.T + (long)j * a.Q * N * L;
+  // q's rows once every column tile of depth j has finished the half of the source parameters q is in
   auto issue = [&](int q, int sl) {
+    if (q == 0 || q == half_q(a.Q)) {
+      wait_count(qa, qa.ctl + 4 + 2 * j + (q == 0 ? 0 : 1), NCT);
+      fence_proxy_global();
+    }
+    fence_proxy_smem();
     tc::mbar_arrive_expect_tx(&bar[sl], (uint32_t)(sizeof(float2) * STG));
     tc::bulk_g2s(stage + sl * STG, Tj + ((long)q * (N / 16) + b) * L * 16, (uint32_t)(sizeof(float2) * STG), &bar[sl]);
   };
-  if (tid == 0) {   // once every column tile of depth j has finished
-    wait_count(qa, qa.ctl + 4 + j, NCT);
-    fence_proxy_global();
-    fence_proxy_smem();
+  if (tid == 0) {
     issue(0, 0);
     if (a.Q > 1) issue(1, 1);
   }
@@ -330,15 +349,13 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[r] = sg[(jb + BPS0 * r) * RB + row];
       Dft<16, true>::run(v);
+      __syncthreads();   // every thread has finished the previous q's last pass, which read the row buffer
       float2* rw = rowbuf + row * SSR;
 #pragma unroll
       for (int r = 0; r < 16; ++r) rw[pidx<float2>(16 * jb + r)] = v[r];
     }
     __syncthreads();   // the row buffer is complete and the stage consumed
-    if (tid == 0 && q + 2 < a.Q) {
-      fence_proxy_smem();
-      issue(q + 2, sl);
-    }
+    if (tid == 0 && q + 2 < a.Q) issue(q + 2, sl);
     // fmaf(w, v, 0) for q = 0, as in the accumulators of the other variants
     auto emit = [&](int, int, float2 v, int k, int rr) {
       acc[k][rr] = make_float2(fmaf(wv[k][rr].x, v.x, acc[k][rr].x), fmaf(wv[k][rr].y, v.y, acc[k][rr].y));
@@ -399,7 +416,7 @@ __global__ void __launch_bounds__(kQThreads, kQMinBlocks) k_inv_queue(QArgs qa) 
       __threadfence();
       qa.ctl[0] = 0;
       qa.ctl[2] = 0;
-      for (int e = 0; e < qa.nj; ++e) qa.ctl[4 + e] = 0;
+      for (int e = 0; e < 2 * qa.nj; ++e) qa.ctl[4 + e] = 0;
       __threadfence();
       qa.ctl[1] = 0;
     }
@@ -408,9 +425,11 @@ __global__ void __launch_bounds__(kQThreads, kQMinBlocks) k_inv_queue(QArgs qa) 
 
 }  // namespace
 
+std::atomic<int> g_withhold{0};
+
 bool inv_queue_supported(int n, bool xi) { return n == 256 && xi; }
 
-size_t inv_queue_ctl_ints(int nj, int) { return 4 + (size_t)nj; }
+size_t inv_queue_ctl_ints(int nj, int) { return 4 + 2 * (size_t)nj; }
 
 // T: the intermediate ([nj][Q][n][n/2] complex, inv2_scratch_bytes); ctl: inv_queue_ctl_ints(nj, Q) zeroed
 // ints (the kernel leaves them zeroed).
@@ -430,6 +449,7 @@ int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cud
   qa.ctl = ctl;
   qa.nj = nj;
   qa.lag = std::min(36, nj);
+  qa.withhold = g_withhold.load();
   const int total = nj * (G::NCT + G::NRT);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::min(total, grid_per_sm * sms));
@@ -446,3 +466,5 @@ int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cud
 }
 
 }  // namespace fr3d
+
+extern "C" int fr3d_test_withhold_queue_counts(int on) { return fr3d::g_withhold.exchange(on ? 1 : 0); }

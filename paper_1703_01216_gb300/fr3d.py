@@ -71,7 +71,8 @@ EXPORTS = ("fr3d_kernel_transform", "fr3d_handle_destroy", "fr3d_handle_query", 
            "fr3d_invert_batched", "fr3d_invert_batched_workspace",
            "fr3d_mlp_create", "fr3d_mlp_destroy", "fr3d_mlp_query", "fr3d_mlp_get_params", "fr3d_mlp_set_params",
            "fr3d_mlp_forward", "fr3d_mlp_gradient", "fr3d_mlp_train_step", "fr3d_band_features",
-           "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query", "fr3d_assemble_rhs",
+           "fr3d_band_alpha_targets", "fr3d_autotune_mode", "fr3d_autotune_query",
+           "fr3d_test_withhold_queue_counts", "fr3d_assemble_rhs",
            "fr3d_unet_create", "fr3d_unet_destroy", "fr3d_unet_query", "fr3d_unet_get_params", "fr3d_unet_set_params",
            "fr3d_unet_forward", "fr3d_unet_gradient", "fr3d_unet_train_step", "fr3d_unet_error_flags")
 
@@ -119,6 +120,7 @@ def load(path: str | None = None):
     lib.fr3d_band_alpha_targets.argtypes = [vp, vp, vp, i, _dp, i, i, vp, vp, vp, vp]
     lib.fr3d_autotune_mode.argtypes = [i]
     lib.fr3d_autotune_query.argtypes = [vp, ct.POINTER(i), ct.POINTER(ct.c_float), i]
+    lib.fr3d_test_withhold_queue_counts.argtypes = [i]
     lib.fr3d_assemble_rhs.argtypes = [vp, vp, i, ct.POINTER(Sources), d, d, i, d, vp, vp]
     lib.fr3d_unet_create.argtypes = [i, i, i, i, ct.c_float, ct.c_ulonglong, ct.POINTER(vp)]
     lib.fr3d_unet_destroy.argtypes = [vp]
@@ -399,6 +401,12 @@ def autotune_query(handle: Handle):
     n = load().fr3d_autotune_query(handle.ptr, ct.byref(v), ms, 8)
     _check(n, "fr3d_autotune_query")
     return v.value, [float(ms[k]) for k in range(n)]
+
+
+def test_withhold_queue_counts(on: bool) -> bool:
+    """Test hook of the tile-queue variant's bounded waits (fr3d_test_withhold_queue_counts): while on, its
+    row tiles' waits run out and the call reports FR3D_INFO_TIMEOUT.  Returns the previous setting."""
+    return bool(load().fr3d_test_withhold_queue_counts(1 if on else 0))
 
 
 class Mlp:
