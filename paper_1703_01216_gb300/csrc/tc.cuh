@@ -57,6 +57,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   }
   return false;
 }
+// The same with a suspend-time hint: a poll that finds the phase incomplete parks the thread until the
+// phase completes or hint_ns nanoseconds pass, instead of returning at once, so waiting threads do not
+// take issue slots from working ones.  Gives up after `limit` polls (at most limit * hint_ns).
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, long limit, uint32_t hint_ns) {
+  const uint32_t a = smem_addr(bar);
+  for (long it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "r"(hint_ns)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
 // ---- bulk copy global -> shared (bytes a multiple of 16, both addresses 16-byte aligned); completes
 // `bytes` transactions on bar

@@ -30,6 +30,7 @@ namespace fr3d {
 namespace {
 
 constexpr long kWaitPolls = 1L << 22;   // bounded mbarrier waits (a poll suspends for a short slice)
+constexpr uint32_t kSleepNs = 200;      // suspend-time hint of the pipeline waits (at most about 0.8 s in all)
 
 struct TcAlphas {
   double a[FR3D_MAX_ALPHAS];
@@ -110,7 +111,6 @@ __device__ __forceinline__ int cm_off(int row, int col, int chunks) {
 //     barrier before the accumulator is written again.
 constexpr int kTcStages = 3;
 constexpr int kTcCtaThreads = 256;
-constexpr int kGatherUnroll = 4;
 
 __device__ __forceinline__ int tc_flag(const int* f) { return *reinterpret_cast<const volatile int*>(f); }
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
@@ -185,11 +185,10 @@ __global__ void __launch_bounds__(kTcCtaThreads) k_tc_contract(TcArgs a, TcAlpha
   if (warp >= 4) {
     // ------------------------------------------------------------------ producers
     const int ptid = tid - 128;
-    const int kpad = 8 * L.KcB;
-    const int total = 2 * a.Q * kpad * 4;
+    const int njobs = 2 * a.Q * 4 * L.KcB;   // (class, source parameter, member, 8-index chunk)
     for (int j = 0; j < nloc && !tc_flag(&sbad); ++j) {
       const int st = j % kTcStages, use = j / kTcStages;
-      if (use > 0 && !tc::mbar_wait(&empty[st], (uint32_t)((use - 1) & 1), kWaitPolls)) {
+      if (use > 0 && !tc::mbar_wait_sleep(&empty[st], (uint32_t)((use - 1) & 1), kWaitPolls, kSleepNs)) {
         sbad = 1;
         break;
       }
@@ -208,55 +207,63 @@ __global__ void __launch_bounds__(kTcCtaThreads) k_tc_contract(TcArgs a, TcAlpha
       }
       PairInfo I;
       pair_info(pair, a.C, a.n, I);
-      for (int e0 = 0; e0 < total; e0 += 128 * kGatherUnroll) {
-        float2 v[kGatherUnroll];
-        double lv[kGatherUnroll];
-        int kk[kGatherUnroll], col[kGatherUnroll], sl[kGatherUnroll];
-        bool live[kGatherUnroll], inb[kGatherUnroll];
+      // right-hand sides: job (s, q, m, kc) gathers the contraction indices k = 8 kc .. 8 kc + 7 of member m
+      // of class s and source parameter q (8 loads in flight), scales and rounds them to BF16 and writes
+      // one 16-byte core-matrix row each for the real and the imaginary column
+      for (int jb = ptid; jb < njobs; jb += 128) {
+        const int kc = jb % L.KcB;
+        int r = jb / L.KcB;
+        const int m = r & 3;
+        r >>= 2;
+        const int q = r % a.Q, s = r / a.Q;
+        const int c = I.cls[s];
+        const bool live = c >= 0 && m < I.nm[s];
+        const long bin = I.bin[s][m];
+        float2 v[8];
+        double lv[8];
 #pragma unroll
-        for (int u = 0; u < kGatherUnroll; ++u) {
-          const int e = e0 + u * 128 + ptid;
-          inb[u] = e < total;
-          const int m = e & 3;
-          int rest = e >> 2;
-          const int k = rest % kpad;
-          rest /= kpad;
-          const int q = rest % a.Q, s = rest / a.Q;
-          kk[u] = k;
-          sl[u] = s;
-          col[u] = s * L.ncolc + q * 8 + 2 * m;
-          live[u] = inb[u] && I.cls[s] >= 0 && k < a.K && m < I.nm[s];
-          v[u] = make_float2(0.f, 0.f);
-          lv[u] = 0.0;
-          if (live[u]) {
-            v[u] = __ldg(a.in + ((long)q * a.K + k) * a.ps + I.bin[s][m]);
-            if (a.scale == kScaleSolve) lv[u] = __ldg(a.lam + (long)I.cls[s] * a.K + k);
-          }
+        for (int u = 0; u < 8; ++u) {
+          const int k = 8 * kc + u;
+          const bool ok = live && k < a.K;
+          v[u] = ok ? __ldg(a.in + ((long)q * a.K + k) * a.ps + bin) : make_float2(0.f, 0.f);
+          lv[u] = (ok && a.scale == kScaleSolve) ? __ldg(a.lam + (long)c * a.K + k) : 0.0;
         }
+        double t = 0.0;
+        if (live && a.scale == kScaleSolve) t = al.a[sidx[a.nb > 1 ? (int)a.cband[c] : 0]] * (*a.s2);
+        uint32_t hx[4], hy[4], lx[4], ly[4];
 #pragma unroll
-        for (int u = 0; u < kGatherUnroll; ++u) {
-          if (!inb[u]) continue;
-          float f = 1.f;
-          if (live[u] && a.scale == kScaleSolve) {
-            const int c = I.cls[sl[u]];
-            const double t = al.a[sidx[a.nb > 1 ? (int)a.cband[c] : 0]] * (*a.s2);
-            const double l = lv[u];
-            float gi;
-            if (a.ra == FR3D_RA_TSVD) gi = (l >= t && l > 0.0) ? __frcp_rn((float)l) : 0.f;
-            else gi = __frcp_rn((float)(l + t));
-            f = gi * a.inv_n2;
-          } else if (a.scale == kScaleConst) {
-            f = a.cscale;
+        for (int u = 0; u < 8; u += 2) {
+          uint16_t h[2][2], l[2][2];
+#pragma unroll
+          for (int w = 0; w < 2; ++w) {
+            float f = 1.f;
+            if (live && 8 * kc + u + w < a.K && a.scale == kScaleSolve) {
+              const double lam = lv[u + w];
+              float gi;
+              if (a.ra == FR3D_RA_TSVD) gi = (lam >= t && lam > 0.0) ? __frcp_rn((float)lam) : 0.f;
+              else gi = __frcp_rn((float)(lam + t));
+              f = gi * a.inv_n2;
+            } else if (a.scale == kScaleConst) {
+              f = a.cscale;
+            }
+            const float x = v[u + w].x * f, y = v[u + w].y * f;
+            h[0][w] = tc::bf16_rn(x);
+            h[1][w] = tc::bf16_rn(y);
+            l[0][w] = SPLIT ? tc::bf16_rn(x - tc::bf16_val(h[0][w])) : (uint16_t)0;
+            l[1][w] = SPLIT ? tc::bf16_rn(y - tc::bf16_val(h[1][w])) : (uint16_t)0;
           }
-          const float x = v[u].x * f, y = v[u].y * f;
-          const uint16_t hx = tc::bf16_rn(x), hy = tc::bf16_rn(y);
-          *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u], kk[u], L.KcB)) = hx;
-          *reinterpret_cast<uint16_t*>(sB(st, 0) + cm_off(col[u] + 1, kk[u], L.KcB)) = hy;
-          if (SPLIT) {
-            *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u], kk[u], L.KcB)) = tc::bf16_rn(x - tc::bf16_val(hx));
-            *reinterpret_cast<uint16_t*>(sB(st, 1) + cm_off(col[u] + 1, kk[u], L.KcB)) =
-                tc::bf16_rn(y - tc::bf16_val(hy));
-          }
+          hx[u / 2] = (uint32_t)h[0][0] | ((uint32_t)h[0][1] << 16);
+          hy[u / 2] = (uint32_t)h[1][0] | ((uint32_t)h[1][1] << 16);
+          lx[u / 2] = (uint32_t)l[0][0] | ((uint32_t)l[0][1] << 16);
+          ly[u / 2] = (uint32_t)l[1][0] | ((uint32_t)l[1][1] << 16);
+        }
+        const int col = s * L.ncolc + q * 8 + 2 * m;
+        *reinterpret_cast<uint4*>(sB(st, 0) + cm_off(col, 8 * kc, L.KcB)) = make_uint4(hx[0], hx[1], hx[2], hx[3]);
+        *reinterpret_cast<uint4*>(sB(st, 0) + cm_off(col + 1, 8 * kc, L.KcB)) = make_uint4(hy[0], hy[1], hy[2], hy[3]);
+        if (SPLIT) {
+          *reinterpret_cast<uint4*>(sB(st, 1) + cm_off(col, 8 * kc, L.KcB)) = make_uint4(lx[0], lx[1], lx[2], lx[3]);
+          *reinterpret_cast<uint4*>(sB(st, 1) + cm_off(col + 1, 8 * kc, L.KcB)) =
+              make_uint4(ly[0], ly[1], ly[2], ly[3]);
         }
       }
       tc::fence_proxy_async();   // this thread's operand writes before the MMAs read them
@@ -269,8 +276,8 @@ __global__ void __launch_bounds__(kTcCtaThreads) k_tc_contract(TcArgs a, TcAlpha
     auto issue = [&](int j) {   // thread 0 only; false if a wait gave up
       const int st = j % kTcStages, use = j / kTcStages;
       const uint32_t acc = tmem + (uint32_t)((j & 1) * (L.ncols_tmem / 2));
-      if (tc_flag(&sbad) || !tc::mbar_wait(&full_tma[st], (uint32_t)(use & 1), kWaitPolls) ||
-          !tc::mbar_wait(&full_b[st], (uint32_t)(use & 1), kWaitPolls))
+      if (tc_flag(&sbad) || !tc::mbar_wait_sleep(&full_tma[st], (uint32_t)(use & 1), kWaitPolls, kSleepNs) ||
+          !tc::mbar_wait_sleep(&full_b[st], (uint32_t)(use & 1), kWaitPolls, kSleepNs))
         return false;
       tc::fence_after_sync();
       const uint32_t a0 = tc::smem_addr(sA(st, 0)), b0 = tc::smem_addr(sB(st, 0));
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(kTcCtaThreads) k_tc_contract(TcArgs a, TcAlpha
       // accumulator (j + 1) % 2 was read by the epilogue of pair j - 1, which ended at the last barrier
       if (tid == 0 && j + 1 < nloc && !issue(j + 1)) sbad = 1;
       __syncwarp();
-      bool done = !tc_flag(&sbad) && tc::mbar_wait(&acc_ready[ab], (uint32_t)((j >> 1) & 1), kWaitPolls);
+      bool done = !tc_flag(&sbad) && tc::mbar_wait_sleep(&acc_ready[ab], (uint32_t)((j >> 1) & 1), kWaitPolls, kSleepNs);
       done = __all_sync(0xffffffffu, done);   // the TMEM loads below are warp-collective
       if (!done) sbad = 1;
       tc::fence_after_sync();
