@@ -133,7 +133,7 @@ def whole_job_rate(units_per_rank: float, world: int, steps: int, seconds: float
 # while these files are unchanged
 STAGE_SOURCES = {
     "inv_fused": ("common.cuh", "fft_engine.cuh", "fft2d.cuh", "fused.cuh", "fused_f32.cu", "fused_v0.cu", "ops.cuh",
-                  "fused_v1.cu", "fused_v2.cu", "fused_v3.cu"),
+                  "fused_v1.cu", "fused_v2.cu", "fused_v3.cu", "inv2p.cu", "inv_queue.cu", "tc.cuh"),
     "alpha": ("common.cuh", "fft_engine.cuh", "fft2d.cuh", "ops.cuh", "ops_impl.cuh", "ops_f32.cu"),
 }
 
