@@ -37,7 +37,10 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   return r;
 }
 // float2: the two lanes in one packed FP32x2 operation (one instruction, each lane rounded to nearest
-// like the scalar form, so the results are the same bits)
+// like the scalar form, so the results are the same bits).  A translation unit that defines
+// FR3D_SCALAR_COMPLEX_ADDS before including this header keeps the scalar form (its kernels then use
+// fewer registers; the device code of every unit is self-contained, so units may differ).
+#ifndef FR3D_SCALAR_COMPLEX_ADDS
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) {
   unsigned long long r;
@@ -45,6 +48,7 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
       "l"(*reinterpret_cast<const unsigned long long*>(&b)));
   return *reinterpret_cast<const float2*>(&r);
 }
+#endif
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 // multiply by -i (forward) or +i (inverse)
 template <bool INV, typename C> __device__ __forceinline__ C cmul_mi(C a) {
