@@ -32,6 +32,7 @@ namespace fr3d {
 namespace {
 
 constexpr long kPolls = 1L << 22;
+constexpr uint32_t kSleepNs = 1000;   // suspend-time hint of the waits: a waiting thread parks (bound: kPolls * 1 us)
 constexpr int kConvStages = 4;
 constexpr int kSlabPos = 130;                   // positions of one (a, e) slab: 128 + the two f neighbours
 constexpr int kSlabBytes = kSlabPos * 16;       // one channel chunk of a slab
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(128) k_conv3(ConvArgs a) {
         const long gi = g + it;
         const int s = (int)(gi % kConvStages);
         const long use = gi / kConvStages;
-        if (use > 0 && !tc::mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), kPolls)) {
+        if (use > 0 && !tc::mbar_wait_sleep(&empty[s], (uint32_t)((use - 1) & 1), kPolls, kSleepNs)) {
           sabort = 1;
           break;
         }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(128) k_conv3(ConvArgs a) {
       for (int it = 0; it < niter && !flag(&sabort); ++it) {
         const long gi = g + it;
         const int s = (int)(gi % kConvStages);
-        if (!tc::mbar_wait(&full[s], (uint32_t)((gi / kConvStages) & 1), kPolls)) {
+        if (!tc::mbar_wait_sleep(&full[s], (uint32_t)((gi / kConvStages) & 1), kPolls, kSleepNs)) {
           sabort = 1;
           break;
         }
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(128) k_conv3(ConvArgs a) {
     }
     g += niter;
     __syncwarp();
-    const bool ok = tc::mbar_wait(&done, tcount & 1u, kPolls);
+    const bool ok = tc::mbar_wait_sleep(&done, tcount & 1u, kPolls, kSleepNs);
     if (!ok) sabort = 1;
     tc::fence_after_sync();
     __syncthreads();
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(128) k_wgrad3(WgradArgs a) {
     for (int it = 0; it < nst && !flag(&sabort); ++it) {
       const int s = it % kWgStages;
       const int use = it / kWgStages;
-      if (use > 0 && !tc::mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), kPolls)) {
+      if (use > 0 && !tc::mbar_wait_sleep(&empty[s], (uint32_t)((use - 1) & 1), kPolls, kSleepNs)) {
         sabort = 1;
         break;
       }
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(128) k_wgrad3(WgradArgs a) {
   } else if (tid == 32) {
     for (int it = 0; it < nst && !flag(&sabort); ++it) {
       const int s = it % kWgStages;
-      if (!tc::mbar_wait(&full[s], (uint32_t)((it / kWgStages) & 1), kPolls)) {
+      if (!tc::mbar_wait_sleep(&full[s], (uint32_t)((it / kWgStages) & 1), kPolls, kSleepNs)) {
         sabort = 1;
         break;
       }
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(128) k_wgrad3(WgradArgs a) {
     tc::mma_commit(&done);
   }
   __syncwarp();
-  const bool ok = nst == 0 || tc::mbar_wait(&done, 0u, kPolls);
+  const bool ok = nst == 0 || tc::mbar_wait_sleep(&done, 0u, kPolls, kSleepNs);
   if (!ok) sabort = 1;
   tc::fence_after_sync();
   __syncthreads();
