@@ -43,7 +43,7 @@ int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int ncl
                           cudaStream_t st);
 int fused_tune_mode_get();
 int fused_tune_batched(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st,
-                       int* best);
+                       int* best, float* best_ms);
 void fused_args_f32(const Handle* H, const float2* Uh, const float* Dd, const int* aidx, int nb, const float* W,
                     float* out, int Q, FusedArgs* a);
 int prepare_instance_f32(Handle* H, int Q, const fr3d_invert_opts* o, float2** Uh, const float** Dd, const int** aidx,
@@ -55,9 +55,19 @@ struct Group {
   int n = 0;
   const Handle* H0 = nullptr;
   int nplanes = 0, nalpha_inst = 0, nalpha_blk = 0, nclusters = 0, max_na = 0;
-  int var = -1;   // fused-inverse tile variant (-1: not chosen yet)
+  int var = -1;   // inverse variant (-1: not chosen yet; 5: the tile queue)
   size_t off_planes = 0, off_alpha = 0, off_fused = 0, off_map = 0;
+  // the tile queue over the group's instances (n = 256, xi output, plan form): its descriptor table in
+  // the plan's tables, its counters and intermediates in the plan's queue buffer
+  int qn = 0, qtotal = 0, qncnt = 0;
+  size_t off_queue = 0;
+  int* qctl = nullptr;
+  int* qcnt = nullptr;
 };
+
+// Bytes of the queue buffer for the instances of a group (4 launch counters, the depth counters, the
+// intermediates), laid out by queue_layout.
+bool queue_group(int n, int output) { return output == FR3D_OUT_XI && inv_queue_supported(n, true); }
 
 // the launches of a group before the fused inverse: data row and column passes, alpha rule
 template <int N>
@@ -99,6 +109,7 @@ size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 struct Batch {
   std::vector<Group> groups;
   unsigned char* dev = nullptr;
+  unsigned char* qbuf = nullptr;   // the tile queue's counters and intermediates (zeroed once)
   int output = FR3D_OUT_XI;
   int launches = 0;
 };
@@ -151,9 +162,11 @@ namespace fr3d {
 namespace {
 
 // Descriptor tables of the groups (host image; device offsets relative to the table's start).
+// qbuf: the plan's queue buffer (device), or null (no tile queue: the one-shot workspace form).
 void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vector<int>>& by_n,
                        const std::vector<float2*>& uh, const std::vector<const float*>& dd,
-                       const std::vector<const int*>& ai, std::vector<unsigned char>& host, std::vector<Group>& groups) {
+                       const std::vector<const int*>& ai, std::vector<unsigned char>& host, std::vector<Group>& groups,
+                       unsigned char* qbuf = nullptr) {
   auto put = [&](const void* p, size_t bytes) {
     const size_t off = al(host.size());
     host.resize(off + bytes);
@@ -201,12 +214,55 @@ void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vecto
     g.nplanes = (int)planes.size();
     g.nalpha_inst = (int)alph.size();
     g.nclusters = (int)map.size();
+    if (qbuf && queue_group(g.n, inst[kv.second[0]].opts->output)) {
+      // [4 launch counters][2 M' depth counters per instance][intermediates, 256-byte aligned]
+      int ncnt = 0;
+      for (int idx : kv.second) ncnt += 2 * inst[idx].handle->h.Mp;
+      g.qctl = reinterpret_cast<int*>(qbuf);
+      g.qcnt = g.qctl + 4;
+      unsigned char* tp = qbuf + al(sizeof(int) * (4 + (size_t)ncnt));
+      std::vector<unsigned char> qt(inv_queue_inst_bytes() * kv.second.size());
+      int tick = 0, c = 0, k = 0;
+      for (int idx : kv.second) {
+        const fr3d_instance& I = inst[idx];
+        const int mp = I.handle->h.Mp;
+        tick += inv_queue_make_inst(qt.data() + k * inv_queue_inst_bytes(), fa[k], reinterpret_cast<float2*>(tp),
+                                    g.qcnt + c, mp, tick);
+        tp += al(inv2_scratch_bytes(g.n, I.Q, mp));
+        c += 2 * mp;
+        ++k;
+      }
+      g.qn = k;
+      g.qtotal = tick;
+      g.qncnt = ncnt;
+      g.off_queue = put(qt.data(), qt.size());
+    }
     g.off_planes = put(planes.data(), planes.size() * sizeof(PlanePtr));
     g.off_alpha = alph.empty() ? 0 : put(alph.data(), alph.size() * sizeof(AlphaInst));
     g.off_fused = put(fa.data(), fa.size() * sizeof(FusedArgs));
     g.off_map = put(map.data(), map.size() * sizeof(int2));
     groups.push_back(g);
   }
+}
+
+// bytes of the plan's queue buffer (the tile queue of its n = 256 group, xi output), 0 if none
+size_t queue_bytes(const fr3d_instance* inst, const std::map<int, std::vector<int>>& by_n) {
+  size_t b = 0;
+  for (auto& kv : by_n) {
+    if (!queue_group(kv.first, inst[kv.second[0]].opts->output)) continue;
+    size_t ncnt = 0;
+    for (int idx : kv.second) ncnt += 2 * (size_t)inst[idx].handle->h.Mp;
+    b += al(sizeof(int) * (4 + ncnt));
+    for (int idx : kv.second) b += al(inv2_scratch_bytes(kv.first, inst[idx].Q, inst[idx].handle->h.Mp));
+  }
+  return b;
+}
+
+// the inverse of a group: the tile queue (variant 5, where the plan has one) or a fused tile variant
+int run_inverse(const Group& g, const unsigned char* dev, int output, int v, cudaStream_t st) {
+  if (v == 5 && g.qn > 0)
+    return inv_queue_launch_table(dev + g.off_queue, g.qn, g.qctl, g.qcnt, g.qncnt, g.qtotal, st);
+  return inv_fused_batched_f32(g.n, fused_of(g, dev), map_of(g, dev), g.nclusters, output, std::min(v, 3), st);
 }
 
 int batch_launches(const std::vector<Group>& groups) {
@@ -231,14 +287,28 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
   FR3D_TRY(batch_prepare(inst, n, false, uh, dd, ai, by_n, &spectra, st));
   Batch b;
   b.output = inst[0].opts->output;
+  const size_t qb = queue_bytes(inst, by_n);
+  if (qb > 0) {
+    FR3D_CUDA_TRY(cudaMalloc(&b.qbuf, qb));
+    cudaError_t e = cudaMemsetAsync(b.qbuf, 0, qb, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaFree(b.qbuf);
+      return FR3D_ERR_CUDA;
+    }
+  }
   std::vector<unsigned char> host;
-  build_descriptors(inst, by_n, uh, dd, ai, host, b.groups);
-  FR3D_CUDA_TRY(cudaMalloc(&b.dev, al(host.size())));
+  build_descriptors(inst, by_n, uh, dd, ai, host, b.groups, b.qbuf);
+  if (cudaMalloc(&b.dev, al(host.size())) != cudaSuccess) {
+    cudaFree(b.qbuf);
+    return FR3D_ERR_OOM;
+  }
   {
     cudaError_t e = cudaMemcpyAsync(b.dev, host.data(), host.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       cudaFree(b.dev);
+      cudaFree(b.qbuf);
       return FR3D_ERR_CUDA;
     }
   }
@@ -246,6 +316,7 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
   fr3d_batch* h = new (std::nothrow) fr3d_batch();
   if (!h) {
     cudaFree(b.dev);
+    cudaFree(b.qbuf);
     return FR3D_ERR_OOM;
   }
   h->b = std::move(b);
@@ -266,15 +337,31 @@ extern "C" int fr3d_batch_run(fr3d_batch* h, void* stream) {
     if (mode == 1) {
       if (g.var < 0 && cs == cudaStreamCaptureStatusNone) {
         // the first run outside a capture times the variants on this group (their launches leave
-        // the group's outputs complete: every variant writes the same bits)
+        // the group's outputs complete: every variant writes the same bits), the tile queue too
+        float fms = 0.f;
         FR3D_TRY(fused_tune_batched(g.n, fused_of(g, h->b.dev), map_of(g, h->b.dev), g.nclusters, h->b.output, st,
-                                    &g.var));
+                                    &g.var, &fms));
+        if (g.qn > 0) {
+          cudaEvent_t e0, e1;
+          FR3D_CUDA_TRY(cudaEventCreate(&e0));
+          FR3D_CUDA_TRY(cudaEventCreate(&e1));
+          int rc = run_inverse(g, h->b.dev, h->b.output, 5, st);
+          if (rc == FR3D_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = FR3D_ERR_CUDA;
+          for (int k = 0; k < 2 && rc == FR3D_OK; ++k) rc = run_inverse(g, h->b.dev, h->b.output, 5, st);
+          if (rc == FR3D_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = FR3D_ERR_CUDA;
+          if (rc == FR3D_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = FR3D_ERR_CUDA;
+          float qms = 0.f;
+          if (rc == FR3D_OK && cudaEventElapsedTime(&qms, e0, e1) != cudaSuccess) rc = FR3D_ERR_CUDA;
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          FR3D_TRY(rc);
+          if (qms / 2.f < fms) g.var = 5;
+        }
         continue;
       }
       v = g.var < 0 ? 0 : g.var;
     }
-    FR3D_TRY(inv_fused_batched_f32(g.n, fused_of(g, h->b.dev), map_of(g, h->b.dev), g.nclusters, h->b.output, v,
-                                   st));
+    FR3D_TRY(run_inverse(g, h->b.dev, h->b.output, v, st));
   }
   return FR3D_OK;
 }
@@ -285,6 +372,7 @@ extern "C" void fr3d_batch_destroy(fr3d_batch* h) {
   if (!h) return;
   cudaDeviceSynchronize();
   cudaFree(h->b.dev);
+  cudaFree(h->b.qbuf);
   delete h;
 }
 

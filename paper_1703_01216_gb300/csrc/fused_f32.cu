@@ -247,7 +247,7 @@ int fused_tune_mode_get() { return g_tune_mode.load(); }
 // Time every variant of a batched group's fused launch (1 warm-up + 2 timed launches each) and return
 // the fastest in *best.  Synchronises the stream.
 int fused_tune_batched(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, cudaStream_t st,
-                       int* best) {
+                       int* best, float* best_ms) {
   const bool xi = output == FR3D_OUT_XI;
   cudaEvent_t e0, e1;
   FR3D_CUDA_TRY(cudaEventCreate(&e0));
@@ -271,6 +271,7 @@ int fused_tune_batched(int n, const FusedArgs* inst, const int2* map, int nclust
   cudaEventDestroy(e1);
   FR3D_TRY(rc);
   *best = bv;
+  if (best_ms) *best_ms = bms / 2.f;   // per launch
   return FR3D_OK;
 }
 

@@ -30,6 +30,8 @@
 // always ends.
 // The arithmetic of every output (the solve weights, the radix passes and their twiddles, the split, the
 // order of the accumulation over q) is the fused kernel's, so all variants return the same bits.
+#include <string.h>
+
 #include <atomic>
 
 #include "fused.cuh"
@@ -67,13 +69,25 @@ template <int N> struct QGeom {
   static_assert(Plan<N>::np == 2 && Plan<N>::radix(0) == 16, "the column DFT: a radix-16 first pass, then the last pass");
 };
 
-struct QArgs {
+// One instance of a launch (a call, or one instance of a batch).
+struct QInst {
   FusedArgs f;
   float2* T;    // [nj][Q][n/16][n/2][16] intermediate
-  int* ctl;     // [0] ticket, [1] CTAs finished, [2] a wait gave up, [4 + 2j + h] column tiles of depth j done
-                // with the first (h = 0) or with every (h = 1) half of the source parameters
+  int* cnt;     // [2 nj]: column tiles of depth j done with the first (2j) or with every (2j + 1) half of the q
   int nj, lag;
-  int withhold;   // test hook: column tiles do not count themselves (the row tiles' waits run out)
+  int tick0;    // the instance's first ticket; its tickets follow each other
+};
+
+// The launch: the instances (one in the arguments, or a device table of several), the ticket counter and
+// the flags that every instance shares.
+struct QLaunch {
+  int* ctl;          // [0] ticket, [1] CTAs finished, [2] a wait gave up
+  int* cnt_all;      // every instance's counters, contiguous (reset with ctl by the last CTA)
+  int ncnt, total;   // counter ints; tickets of the launch
+  int withhold;      // test hook: column tiles do not count themselves (the row tiles' waits run out)
+  int ninst;
+  const QInst* tab;  // device table of ninst instances, or null: inst0
+  QInst inst0;
 };
 
 // Tile of ticket k (depth j counted from the call's first depth j0): kind 0 = column tile, 1 = row tile.  Groups s = 0 .. nj - 1 + lag: the column tiles
@@ -111,14 +125,20 @@ __device__ __forceinline__ void decode_ticket(int k, int nj, int lag, int& kind,
 // source parameters of the first half (the first dependency step of a row tile)
 __device__ __forceinline__ int half_q(int Q) { return Q > 1 ? Q / 2 : 1; }
 
-__device__ __forceinline__ void report_timeout(const QArgs& qa) {
-  atomicExch(qa.ctl + 2, 1);
+// tickets of one instance
+template <int N> __host__ __device__ inline int queue_tickets(int nj, int) {
+  using G = QGeom<N>;
+  return nj * (G::NCT + G::NRT);
+}
+
+__device__ __forceinline__ void report_timeout(const QLaunch& ql, const QInst& qa) {
+  atomicExch(ql.ctl + 2, 1);
   if (qa.f.info) atomicOr(qa.f.info, FR3D_INFO_TIMEOUT);
 }
 
 // Wait until *c >= target (acquire), or a wait elsewhere has given up; false if this one gave up.
-__device__ __forceinline__ bool wait_count(const QArgs& qa, const int* c, int target) {
-  const volatile int* gave_up = qa.ctl + 2;
+__device__ __forceinline__ bool wait_count(const QLaunch& ql, const QInst& qa, const int* c, int target) {
+  const volatile int* gave_up = ql.ctl + 2;
   for (long it = 0; it < kSpinLimit; ++it) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
@@ -126,12 +146,12 @@ __device__ __forceinline__ bool wait_count(const QArgs& qa, const int* c, int ta
     if (*gave_up) return true;   // the results are flagged already; do not wait again
     __nanosleep(128);
   }
-  report_timeout(qa);
+  report_timeout(ql, qa);
   return false;
 }
 
-__device__ __forceinline__ void stage_wait(const QArgs& qa, uint64_t* bar, uint32_t& parity) {
-  if (!tc::mbar_wait(bar, parity, kSpinLimit)) report_timeout(qa);
+__device__ __forceinline__ void stage_wait(const QLaunch& ql, const QInst& qa, uint64_t* bar, uint32_t& parity) {
+  if (!tc::mbar_wait(bar, parity, kSpinLimit)) report_timeout(ql, qa);
   parity ^= 1u;
 }
 
@@ -164,7 +184,7 @@ template <int N> __device__ __forceinline__ int pair_column(int t, int c) {
 }
 
 template <int N>
-__device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float2* stage, float2* colbuf,
+__device__ __forceinline__ void column_tile(const QLaunch& ql, const QInst& qa, int j, int t, float2* stage, float2* colbuf,
                                             float2* tab, uint64_t* bar, uint32_t* par, const int* s_aidx, int tid) {
   using G = QGeom<N>;
   constexpr int L = G::L, CT = G::CT, SSC = G::SSC, STG = G::STG;
@@ -223,7 +243,7 @@ __device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float
   float2* Tj = qa.T + (long)j * a.Q * N * L;
   for (int q = 0; q < a.Q; ++q) {
     const int sl = q & 1;
-    stage_wait(qa, &bar[sl], par[sl]);
+    stage_wait(ql, qa, &bar[sl], par[sl]);
     // first pass of the inverse column DFTs from the stage (butterfly jj of column c: bins jj + 16 r)
     const float2* sg = stage + sl * STG + c * N;
     float2 v[16];
@@ -272,15 +292,15 @@ __device__ __forceinline__ void column_tile(const QArgs& qa, int j, int t, float
     const bool release = q == half_q(a.Q) - 1 || q == a.Q - 1;
     if (release) __threadfence();
     __syncthreads();   // the column buffer is free again
-    if (tid == 0 && release && !qa.withhold) {
-      if (q == half_q(a.Q) - 1) atomicAdd(qa.ctl + 4 + 2 * j, 1);
-      if (q == a.Q - 1) atomicAdd(qa.ctl + 4 + 2 * j + 1, 1);
+    if (tid == 0 && release && !ql.withhold) {
+      if (q == half_q(a.Q) - 1) atomicAdd(qa.cnt + 2 * j, 1);
+      if (q == a.Q - 1) atomicAdd(qa.cnt + 2 * j + 1, 1);
     }
   }
 }
 
 template <int N>
-__device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* stage, float2* rowbuf,
+__device__ __forceinline__ void row_tile(const QLaunch& ql, const QInst& qa, int j, int b, float2* stage, float2* rowbuf,
                                          float2* tab, uint64_t* bar, uint32_t* par, uint64_t pol, int tid) {
   using G = QGeom<N>;
   constexpr int L = G::L, RB = G::RB, SSR = G::SSR, STG = G::STG, NCT = G::NCT;
@@ -293,7 +313,7 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
   // q's rows once every column tile of depth j has finished the half of the source parameters q is in
   auto issue = [&](int q, int sl) {
     if (q == 0 || q == half_q(a.Q)) {
-      wait_count(qa, qa.ctl + 4 + 2 * j + (q == 0 ? 0 : 1), NCT);
+      wait_count(ql, qa, qa.cnt + 2 * j + (q == 0 ? 0 : 1), NCT);
       fence_proxy_global();
     }
     fence_proxy_smem();
@@ -334,7 +354,7 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
   __syncthreads();   // tables
   for (int q = 0; q < a.Q; ++q) {
     const int sl = q & 1;
-    stage_wait(qa, &bar[sl], par[sl]);
+    stage_wait(ql, qa, &bar[sl], par[sl]);
     // the rows of T are in shared memory now: drop their lines from L2 (one 128-byte line per thread)
     static_assert(STG * sizeof(float2) == 128 * kQThreads, "one line per thread");
     l2_discard(Tj + ((long)q * (N / 16) + b) * L * 16 + tid * 16);
@@ -377,9 +397,8 @@ __device__ __forceinline__ void row_tile(const QArgs& qa, int j, int b, float2* 
 }
 
 template <int N>
-__global__ void __launch_bounds__(kQThreads, kQMinBlocks) k_inv_queue(QArgs qa) {
+__global__ void __launch_bounds__(kQThreads, kQMinBlocks) k_inv_queue(QLaunch ql) {
   using G = QGeom<N>;
-  const FusedArgs& a = qa.f;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   int* s_tick = reinterpret_cast<int*>(smem_raw + 16);
@@ -387,8 +406,9 @@ __global__ void __launch_bounds__(kQThreads, kQMinBlocks) k_inv_queue(QArgs qa) 
   float2* buf = stage + 2 * G::STG;
   float2* tab = buf + G::BUF;
   __shared__ int s_aidx[FR3D_MAX_BANDS];
+  __shared__ __align__(16) int s_inst_raw[sizeof(QInst) / 4];   // the current tile's instance descriptor
+  QInst& s_inst = *reinterpret_cast<QInst*>(s_inst_raw);
   const int tid = threadIdx.x;
-  const int total = qa.nj * (G::NCT + G::NRT);
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
     tc::mbar_init(&bar[1], 1);
@@ -396,29 +416,50 @@ __global__ void __launch_bounds__(kQThreads, kQMinBlocks) k_inv_queue(QArgs qa) 
   }
   uint32_t par[2] = {0u, 0u};   // parity of each stage barrier's next completion
   const uint64_t pol = evict_first_policy();
-  pdl_wait();   // the data spectra, the chosen alpha index and the queue counters of the previous call
-  if (tid < a.nb) s_aidx[tid] = min(max(a.aidx[tid], 0), a.na - 1);
+  pdl_wait();   // the data spectra, the chosen alpha indices and the queue counters of the previous call
+  int cur = -1;   // instance held in s_inst
   for (;;) {
-    if (tid == 0) *s_tick = atomicAdd(qa.ctl, 1);
+    if (tid == 0) *s_tick = atomicAdd(ql.ctl, 1);
     __syncthreads();   // the ticket; also orders the previous tile's last reads before this tile's writes
     const int tick = *s_tick;
-    if (tick >= total) break;
+    if (tick >= ql.total) break;
+    // the instance of the ticket (the table is ordered by first ticket)
+    int inst = 0;
+    if (ql.tab) {
+      int lo = 0, hi = ql.ninst - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&ql.tab[mid].tick0) <= tick) lo = mid;
+        else hi = mid - 1;
+      }
+      inst = lo;
+    }
+    if (inst != cur) {   // a uniform branch: every thread computed the same instance
+      constexpr int W = sizeof(QInst) / 4;
+      static_assert(sizeof(QInst) % 4 == 0 && W <= kQThreads, "the descriptor is copied one word per thread");
+      const int* src = reinterpret_cast<const int*>(ql.tab ? &ql.tab[inst] : &ql.inst0);
+      if (tid < W) s_inst_raw[tid] = src[tid];
+      __syncthreads();
+      if (tid < s_inst.f.nb) s_aidx[tid] = min(max(s_inst.f.aidx[tid], 0), s_inst.f.na - 1);
+      __syncthreads();
+      cur = inst;
+    }
     int kind, j, t;
-    decode_ticket<N>(tick, qa.nj, qa.lag, kind, j, t);
-    if (kind == 0) column_tile<N>(qa, j, t, stage, buf, tab, bar, par, s_aidx, tid);
-    else row_tile<N>(qa, j, t, stage, buf, tab, bar, par, pol, tid);
+    decode_ticket<N>(tick - s_inst.tick0, s_inst.nj, s_inst.lag, kind, j, t);
+    if (kind == 0) column_tile<N>(ql, s_inst, j, t, stage, buf, tab, bar, par, s_aidx, tid);
+    else row_tile<N>(ql, s_inst, j, t, stage, buf, tab, bar, par, pol, tid);
     __syncthreads();   // before thread 0 overwrites the ticket
   }
-  // the last CTA to finish resets the queue for the next call
+  // the last CTA to finish resets the queue for the next launch
   if (tid == 0) {
     __threadfence();
-    if (atomicAdd(qa.ctl + 1, 1) == (int)gridDim.x - 1) {
+    if (atomicAdd(ql.ctl + 1, 1) == (int)gridDim.x - 1) {
       __threadfence();
-      qa.ctl[0] = 0;
-      qa.ctl[2] = 0;
-      for (int e = 0; e < 2 * qa.nj; ++e) qa.ctl[4 + e] = 0;
+      ql.ctl[0] = 0;
+      ql.ctl[2] = 0;
+      for (int e = 0; e < ql.ncnt; ++e) ql.cnt_all[e] = 0;
       __threadfence();
-      qa.ctl[1] = 0;
+      ql.ctl[1] = 0;
     }
   }
 }
@@ -431,10 +472,9 @@ bool inv_queue_supported(int n, bool xi) { return n == 256 && xi; }
 
 size_t inv_queue_ctl_ints(int nj, int) { return 4 + 2 * (size_t)nj; }
 
-// T: the intermediate ([nj][Q][n][n/2] complex, inv2_scratch_bytes); ctl: inv_queue_ctl_ints(nj, Q) zeroed
-// ints (the kernel leaves them zeroed).
-int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cudaStream_t st) {
-  if (!inv_queue_supported(n, true) || f.Zs) return FR3D_ERR_UNSUPPORTED_SIZE;
+namespace {
+
+int queue_launch(const QLaunch& ql, cudaStream_t st) {
   using G = QGeom<256>;
   const void* kern = reinterpret_cast<const void*>(k_inv_queue<256>);
   FR3D_TRY(smem_optin(kern, G::smem));
@@ -443,16 +483,8 @@ int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cud
   int dev = 0, sms = 0;
   FR3D_CUDA_TRY(cudaGetDevice(&dev));
   FR3D_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  QArgs qa;
-  qa.f = f;
-  qa.T = T;
-  qa.ctl = ctl;
-  qa.nj = nj;
-  qa.lag = std::min(36, nj);
-  qa.withhold = g_withhold.load();
-  const int total = nj * (G::NCT + G::NRT);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(std::min(total, grid_per_sm * sms));
+  cfg.gridDim = dim3(std::min(ql.total, grid_per_sm * sms));
   cfg.blockDim = dim3(kQThreads);
   cfg.dynamicSmemBytes = G::smem;
   cfg.stream = st;
@@ -461,8 +493,57 @@ int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cud
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FR3D_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_inv_queue<256>, qa));
+  FR3D_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_inv_queue<256>, ql));
   return FR3D_OK;
+}
+
+QInst make_inst(const FusedArgs& f, float2* T, int* cnt, int nj, int tick0) {
+  QInst qi;
+  qi.f = f;
+  qi.T = T;
+  qi.cnt = cnt;
+  qi.nj = nj;
+  qi.lag = std::min(36, nj);
+  qi.tick0 = tick0;
+  return qi;
+}
+
+}  // namespace
+
+// T: the intermediate ([nj][Q][n][n/2] complex, inv2_scratch_bytes); ctl: inv_queue_ctl_ints(nj, Q) zeroed
+// ints (the kernel leaves them zeroed): [0..3] the launch's counters, then the depth counters.
+int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cudaStream_t st) {
+  if (!inv_queue_supported(n, true) || f.Zs) return FR3D_ERR_UNSUPPORTED_SIZE;
+  QLaunch ql = {};
+  ql.inst0 = make_inst(f, T, ctl + 4, nj, 0);
+  ql.ctl = ctl;
+  ql.cnt_all = ctl + 4;
+  ql.ncnt = 2 * nj;
+  ql.total = queue_tickets<256>(nj, ql.inst0.lag);
+  ql.withhold = g_withhold.load();
+  ql.ninst = 1;
+  ql.tab = nullptr;
+  return queue_launch(ql, st);
+}
+
+size_t inv_queue_inst_bytes() { return sizeof(QInst); }
+
+int inv_queue_make_inst(void* dst, const FusedArgs& f, float2* T, int* cnt, int nj, int tick0) {
+  const QInst qi = make_inst(f, T, cnt, nj, tick0);
+  memcpy(dst, &qi, sizeof(QInst));
+  return queue_tickets<256>(nj, qi.lag);
+}
+
+int inv_queue_launch_table(const void* tab, int ninst, int* ctl, int* cnt_all, int ncnt, int total, cudaStream_t st) {
+  QLaunch ql = {};
+  ql.ctl = ctl;
+  ql.cnt_all = cnt_all;
+  ql.ncnt = ncnt;
+  ql.total = total;
+  ql.withhold = g_withhold.load();
+  ql.ninst = ninst;
+  ql.tab = static_cast<const QInst*>(tab);
+  return queue_launch(ql, st);
 }
 
 }  // namespace fr3d

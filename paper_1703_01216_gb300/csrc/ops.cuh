@@ -58,6 +58,13 @@ int inv2_launch(int n, bool xi, const FusedArgs& f, int nj, float2* T, cudaStrea
 bool inv_queue_supported(int n, bool xi);
 size_t inv_queue_ctl_ints(int nj, int Q);
 int inv_queue_launch(int n, const FusedArgs& f, int nj, float2* T, int* ctl, cudaStream_t st);
+// The same queue over several instances of n = 256 in one launch: every instance's descriptor (written to
+// host memory by inv_queue_make_inst, which returns the instance's ticket count; tick0 = the tickets of the
+// instances before it) in a device table; ctl: 4 zeroed ints; cnt_all: ncnt zeroed ints holding every
+// instance's 2 nj counters (cnt); total = all tickets.  The launch leaves ctl and cnt_all zeroed.
+size_t inv_queue_inst_bytes();
+int inv_queue_make_inst(void* dst, const FusedArgs& f, float2* T, int* cnt, int nj, int tick0);
+int inv_queue_launch_table(const void* tab, int ninst, int* ctl, int* cnt_all, int ncnt, int total, cudaStream_t st);
 // W_q = V0_q / sum_q' V0_q'^2 on the R grid for the handle's cached sources
 int build_wtab(const Handle* H, float* W, int Q, const double* pts64, int L, double coef, cudaStream_t st);
 
