@@ -53,7 +53,7 @@ template <> struct FusedCfg<48> : FusedCfgBase { static constexpr int CL = 1, NT
 template <> struct FusedCfg<64> : FusedCfgBase { static constexpr int CL = 2, NT = 256, RB = 32, MINB = 2; };
 template <> struct FusedCfg<96> : FusedCfgBase { static constexpr int CL = 2, NT = 256, RB = 48, MINB = 2; };
 template <> struct FusedCfg<128> : FusedCfgBase { static constexpr int CL = 4, NT = 256, RB = 32, MINB = 2; };
-template <> struct FusedCfg<192> : FusedCfgBase { static constexpr int CL = 4, NT = 256, RB = 16, MINB = 2; };
+template <> struct FusedCfg<192> : FusedCfgBase { static constexpr int CL = 8, NT = 256, RB = 8, MINB = 2; };
 template <> struct FusedCfg<256> : FusedCfgBase { static constexpr int CL = 8, NT = 256, RB = 16, MINB = 2; };
 template <> struct FusedCfg<384> : FusedCfgBase { static constexpr int CL = 8, NT = 512, RB = 16, MINB = 1; };
 
