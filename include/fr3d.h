@@ -70,8 +70,9 @@ extern "C" {
 #define FR3D_INFO_LEARNED_OUT_OF_RANGE 8 /* LEARNED: a band's predicted log10 alpha lay more than half a
                                             decade outside the candidate grid (the nearest end was used;
                                             the discrepancy rule is the fallback to run) */
-#define FR3D_INFO_TIMEOUT 16             /* a bounded device wait (tensor-core copy or MMA completion)
-                                            gave up: the outputs of this call are incomplete */
+#define FR3D_INFO_TIMEOUT 16             /* a bounded device wait (a tensor-core copy or MMA completion,
+                                            or the tile-queue inverse's wait on a release) gave up: the
+                                            outputs of this call are incomplete */
 
 /* ---- enums ---- */
 #define FR3D_K_DZ_INV_R 0 /* K = d/dz (1/r), Eq. (4) (the equation the paper solves) */
