@@ -22,6 +22,7 @@ struct AlphaInst {
   const unsigned char* cband;
   double* partials;
   unsigned* counter;
+  unsigned* tickets;
   int* aidx;
   double* res;
   int* info;
@@ -29,14 +30,14 @@ struct AlphaInst {
   int nplanes, na, nb, bstart, nblk;
 };
 
-// Each instance owns a whole number of clusters of blocks (alpha_blocks), so no cluster spans two.
-__global__ void __cluster_dims__(kAlphaCluster, 1, 1) __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst, long ps, int n,
+// Each instance owns alpha_blocks(C) consecutive blocks of the grid and its own partial sums and tickets.
+__global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst, long ps, int n,
                                                        int Cn, double inv_n2) {
   int i = 0;
   while (i + 1 < ninst && inst[i + 1].bstart <= (int)blockIdx.x) ++i;
   const AlphaInst a = inst[i];
   alpha_choose_body<float2>(a.Uh, ps, a.nplanes, n, Cn, a.Ft, a.na, a.thr2, a.cband, a.nb, inv_n2, a.partials,
-                            a.counter, a.aidx, a.res, a.info, (int)blockIdx.x - a.bstart, a.nblk);
+                            a.counter, a.aidx, a.res, a.info, a.tickets, (int)blockIdx.x - a.bstart, a.nblk);
 }
 
 int inv_fused_batched_f32(int n, const FusedArgs* inst, const int2* map, int nclusters, int output, int variant,
@@ -195,6 +196,7 @@ void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vecto
         band_thresholds(H, I.opts, a.nb, a.thr2.t);
         a.partials = H->partials;
         a.counter = H->counter;
+        a.tickets = alpha_tickets(H);
         a.aidx = const_cast<int*>(ai[idx]);
         a.res = I.opts->residuals;
         a.info = I.opts->info;

@@ -235,7 +235,9 @@ __device__ __forceinline__ double sq_abs(double2 v) { return fma(v.x, v.x, v.y *
 
 constexpr int kAlphaCPB = 64;  // classes per block
 constexpr int kAlphaSplit = 4; // threads per class in the power gather
-constexpr int kAlphaCluster = 8; // blocks per cluster (the grid is padded to a multiple)
+constexpr int kAlphaGroup = 8;   // blocks per group of the two-level reduction
+static_assert(kAlphaCPB == 64 && kAlphaGroup == 8,
+              "ensure_partials sizes the partial-sum buffer for 64 classes per block and 8 blocks per group");
 static_assert(256 / kAlphaSplit >= kAlphaCPB, "every class of a block has its gather threads");
 
 // Per band b of frequency classes (one band: the whole spectrum),
@@ -243,19 +245,21 @@ static_assert(256 / kAlphaSplit >= kAlphaCPB, "every class of a block has its ga
 // with P[c] the data power of class c: every stored half-spectrum bin of the class, weighted 1 on
 // the kx = 0 and kx = n/2 columns and 2 elsewhere (their mirror bins are not stored), summed over
 // planes.  The discrepancy rule picks, per band, the largest alpha_k with r_b^2 <= thr2.t[b].
-// Deterministic: fixed-order partial sums per block, per cluster of kAlphaCluster blocks (through
-// distributed shared memory), and over clusters by the last block to finish.  FP64 runs at a small
-// fraction of the FP32 rate on this GPU, so the serial parts avoid FP64 chains: the choice is a warp
-// ballot per band rather than a loop over candidates.
+// Deterministic: fixed-order partial sums per block; per group of kAlphaGroup consecutive blocks, in
+// block order, by the group's last block to finish (an atomic ticket per group); over the groups, in
+// group order, by the last group to finish.  The tickets leave the blocks free to land on distinct
+// SMs (an 8-block cluster per group placed two blocks on some SMs and added two cluster barriers).
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the serial parts avoid FP64 chains:
+// the choice is a warp ballot per band rather than a loop over candidates.
 struct BandThr {
   double t[FR3D_MAX_BANDS];
 };
 
-// blocks of the alpha rule for Cn classes: one per kAlphaCPB classes, padded to whole clusters
-inline int alpha_blocks(int Cn) {
-  const int b = (Cn + kAlphaCPB - 1) / kAlphaCPB;
-  return (b + kAlphaCluster - 1) / kAlphaCluster * kAlphaCluster;
-}
+// blocks of the alpha rule for Cn classes: one per kAlphaCPB classes
+inline int alpha_blocks(int Cn) { return (Cn + kAlphaCPB - 1) / kAlphaCPB; }
+__host__ __device__ inline int alpha_groups(int nblk) { return (nblk + kAlphaGroup - 1) / kAlphaGroup; }
+// the group tickets of the alpha rule in the handle's partial-sum buffer (tables.cu)
+unsigned* alpha_tickets(const Handle* H);
 
 template <typename C>
 __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
@@ -263,11 +267,13 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
                                                   const unsigned char* __restrict__ cband, int nb, double inv_n2,
                                                   double* __restrict__ partials, unsigned* __restrict__ counter,
                                                   int* __restrict__ aidx, double* __restrict__ res_out,
-                                                  int* __restrict__ info, int blk, int nblk) {
+                                                  int* __restrict__ info, unsigned* __restrict__ gticket, int blk,
+                                                  int nblk) {
+  // partials: [nblk][O] block sums, then [groups][O] group sums; gticket: one ticket per group
+  // (alpha_tickets); counter: the ticket over the groups.  Every ticket is zero between launches.
   // Accumulation types: the class power P[c] is summed in the data's precision (at most 4 nplanes
   // positive terms); the residual sums F[c][k] P[c] over classes and blocks are FP64.
   using A = typename std::conditional<std::is_same<C, float2>::value, float, double>::type;
-  namespace cg = cooperative_groups;
   __shared__ double sP[kAlphaCPB];
   __shared__ unsigned char sB[kAlphaCPB];
   __shared__ int present[FR3D_MAX_BANDS];
@@ -356,39 +362,50 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
     }
     __syncthreads();
   }
-  // cluster of kAlphaCluster consecutive blocks: block r adds output o = r, r + CL, ... over the
-  // cluster's blocks (distributed shared memory, rank order) and stores the cluster's partial
-  cg::cluster_group cluster = cg::this_cluster();
-  cluster.sync();
-  {
-    const int r = (int)cluster.block_rank();
-    const int cid = blk / kAlphaCluster;
-    for (int o = r + tid * kAlphaCluster; o < O; o += 256 * kAlphaCluster) {
-      double s = 0.0;
-#pragma unroll
-      for (int q = 0; q < kAlphaCluster; ++q) s += *cluster.map_shared_rank(sPart + o, (unsigned)q);
-      partials[(long)cid * O + o] = s;
-    }
-  }
-  cluster.sync();                            // no block leaves while its shared memory is read
+  // level 1: this block's sums, then a ticket of its group; the group's last block adds the group's
+  // block sums in block order
+  const int ngr = alpha_groups(nblk);
+  double* gpart = partials + (long)nblk * O;
+  for (int o = tid; o < O; o += 256) partials[(long)blk * O + o] = sPart[o];
   __threadfence();
   __syncthreads();
-  if (tid == 0) last = atomicAdd(counter, 1u) == (unsigned)(nblk - 1);
+  const int g = blk / kAlphaGroup;
+  const int gsz = min(kAlphaGroup, nblk - g * kAlphaGroup);
+  if (tid == 0) last = atomicAdd(gticket + g, 1u) == (unsigned)(gsz - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int o = tid; o < O; o += 256) {
+    double v[kAlphaGroup];
+#pragma unroll
+    for (int q = 0; q < kAlphaGroup; ++q) v[q] = q < gsz ? __ldcg(partials + (long)(g * kAlphaGroup + q) * O + o) : 0.0;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kAlphaGroup; ++q)
+      if (q < gsz) s += v[q];
+    gpart[(long)g * O + o] = s;
+  }
+  // level 2: a ticket over the groups
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    gticket[g] = 0u;
+    last = atomicAdd(counter, 1u) == (unsigned)(ngr - 1);
+  }
   __syncthreads();
   if (!last) return;
   __threadfence();
   // every other block has finished: let a programmatically launched successor start its set-up
   pdl_release();
-  // the last block: r^2 per (band, candidate) over the cluster partials (8 loads in flight per round)
-  const int ncl = nblk / kAlphaCluster;
+  // the last group: r^2 per (band, candidate) over the group sums (24 loads in flight per round)
   for (int o = tid; o < O; o += 256) {
     double s = 0.0;
-    for (int g0 = 0; g0 < ncl; g0 += 8) {
-      double v[8];
+    for (int g0 = 0; g0 < ngr; g0 += 24) {
+      double v[24];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = g0 + i < ncl ? __ldcg(partials + (long)(g0 + i) * O + o) : 0.0;
+      for (int i = 0; i < 24; ++i) v[i] = g0 + i < ngr ? __ldcg(gpart + (long)(g0 + i) * O + o) : 0.0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) s += v[i];
+      for (int i = 0; i < 24; ++i) s += v[i];
     }
     s *= inv_n2;
     sPart[o] = s;
@@ -434,14 +451,14 @@ __device__ __forceinline__ void alpha_choose_body(const C* __restrict__ Uh, long
 }
 
 template <typename C>
-__global__ void __cluster_dims__(kAlphaCluster, 1, 1) __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
+__global__ void __launch_bounds__(256) k_alpha_choose(const C* __restrict__ Uh, long ps, int nplanes, int n, int Cn,
                                                       const double* __restrict__ Ft, int na, BandThr thr2,
                                                       const unsigned char* __restrict__ cband, int nb, double inv_n2,
                                                       double* __restrict__ partials, unsigned* __restrict__ counter,
                                                       int* __restrict__ aidx, double* __restrict__ res_out,
-                                                      int* __restrict__ info) {
+                                                      int* __restrict__ info, unsigned* __restrict__ gticket) {
   alpha_choose_body(Uh, ps, nplanes, n, Cn, Ft, na, thr2, cband, nb, inv_n2, partials, counter, aidx, res_out, info,
-                    (int)blockIdx.x, (int)gridDim.x);
+                    gticket, (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <typename T>
@@ -456,7 +473,7 @@ int Ops<T>::alpha_choose(Handle* H, const C* Uh, int nplanes, int n_alpha, const
   for (int b = 0; b < nb; ++b) t.t[b] = thr2[b];
   k_alpha_choose<C><<<blocks, 256, sm, st>>>(Uh, ps, nplanes, H->n, H->C, H->Ft, n_alpha, t, H->cband, nb,
                                             1.0 / ((double)H->n * H->n), H->partials, H->counter, aidx, residuals,
-                                            info);
+                                            info, alpha_tickets(H));
   return cudaGetLastError() == cudaSuccess ? FR3D_OK : FR3D_ERR_CUDA;
 }
 

@@ -99,18 +99,33 @@ int alpha_tables(Handle* H, const double* alphas, int n_alpha, int ra, cudaStrea
   return FR3D_OK;
 }
 
+// The handle's partial-sum buffer: data, then the alpha rule's group tickets at a fixed offset.
+// Data: the alpha rule's [blocks][O] block sums and [groups][O] group sums (blocks of 64 classes,
+// groups of 8 blocks, O <= FR3D_MAX_ALPHAS * FR3D_MAX_BANDS); the M > 1 rule's [blocks of 64
+// classes][bands][alphas]; the learned rule's at most 2 * 152 blocks of FR3D_MAX_BANDS sums.
+// Tickets: one unsigned per group, zero between launches (zeroed here, reset by the launch that
+// used them).
+static long partial_data_doubles(int C) {
+  const long blocks = (C + 63) / 64, groups = (blocks + 7) / 8;
+  return std::max((blocks + groups) * (long)FR3D_MAX_ALPHAS * FR3D_MAX_BANDS, 2L * 152 * FR3D_MAX_BANDS);
+}
+
 int ensure_partials(Handle* H) {
-  const int blocks = (H->C + 63) / 64;
-  // alpha rule: [blocks][bands][alphas]; learned rule: at most 2 * 152 blocks of FR3D_MAX_BANDS sums
-  const int need = std::max(blocks * FR3D_MAX_ALPHAS * FR3D_MAX_BANDS, 2 * 152 * FR3D_MAX_BANDS);
+  const long data = partial_data_doubles(H->C);
+  const long groups = ((H->C + 63) / 64 + 7) / 8;
+  const long need = data + (groups + 1) / 2;
   if (H->partial_cap >= need) return FR3D_OK;
   if (H->partials) cudaFree(H->partials);
   H->partials = nullptr;
   H->partial_cap = 0;
   FR3D_CUDA_TRY(cudaMalloc(&H->partials, sizeof(double) * need));
-  H->partial_cap = need;
+  FR3D_CUDA_TRY(cudaMemset(H->partials + data, 0, sizeof(double) * (need - data)));
+  FR3D_CUDA_TRY(cudaDeviceSynchronize());
+  H->partial_cap = (int)need;
   return FR3D_OK;
 }
+
+unsigned* alpha_tickets(const Handle* H) { return reinterpret_cast<unsigned*>(H->partials + partial_data_doubles(H->C)); }
 
 // Radial band of frequency class (p, q): floor(nb |k| / |k|max) with |k| = sqrt(p^2 + q^2) and
 // |k|max = sqrt(2) n/2 (clamped to nb - 1).  count[b] = number of grid frequencies in band b (each
