@@ -225,8 +225,9 @@ int fr3d_invert_host(fr3d_handle* h, const void* U_host, int Q, const fr3d_inver
  * Each instance is one call of fr3d_invert (FP32, M = 1) with its own handle (geometry), data,
  * options and output; all instances of a batch use the same output kind.  Instances must have
  * distinct handles (a handle's workspace holds one instance's spectra).  A plan groups the
- * instances by grid size n and runs Algorithm 1 for each group with four launches covering all of
- * its instances (data row pass, data column pass, alpha rule, fused inverse).  fr3d_batch_create
+ * instances by grid size n and runs Algorithm 1 with three launches per group covering all of its
+ * instances (data row pass, data column pass, inverse) and one alpha-rule launch covering the
+ * instances of every group (fr3d_batch_launch_count: 3 per group + 1).  fr3d_batch_create
  * builds every table and workspace and uploads the descriptors (it synchronises `stream`); the
  * device pointers and options of the instances are fixed at creation.  fr3d_batch_run only
  * launches kernels (it can be captured in a CUDA graph); with the autotuner on (mode 1, below) its

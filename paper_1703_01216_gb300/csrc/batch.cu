@@ -1,7 +1,8 @@
 // Batched inversion of many independent instances of uneven size (grid n, depths M', sources Q):
-// a batch plan groups the instances by n and runs Algorithm 1 for every group with four launches
-// (data row pass, data column pass, alpha rule, fused inverse), each covering all instances of the
-// group through device tables of per-plane, per-instance and per-cluster descriptors.  The plan
+// a batch plan groups the instances by n and runs Algorithm 1 with three launches per group (data
+// row pass, data column pass, inverse), each covering all instances of the group through device
+// tables of per-plane, per-instance and per-cluster descriptors, and one alpha-rule launch over the
+// instances of every group (the rule's kernel takes the grid size per instance).  The plan
 // is built once (tables, workspaces, descriptors); running it only launches kernels, so it can be
 // captured in a CUDA graph.
 #include <string.h>
@@ -27,16 +28,24 @@ struct AlphaInst {
   double* res;
   int* info;
   BandThr thr2;
+  double inv_n2;   // 1 / n^2
+  long ps;         // plane stride of the data spectra, (n/2 + 1) n
+  int n, Cn;       // grid size and its frequency classes
   int nplanes, na, nb, bstart, nblk;
 };
 
-// Each instance owns alpha_blocks(C) consecutive blocks of the grid and its own partial sums and tickets.
-__global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst, long ps, int n,
-                                                       int Cn, double inv_n2) {
-  int i = 0;
-  while (i + 1 < ninst && inst[i + 1].bstart <= (int)blockIdx.x) ++i;
-  const AlphaInst a = inst[i];
-  alpha_choose_body<float2>(a.Uh, ps, a.nplanes, n, Cn, a.Ft, a.na, a.thr2, a.cband, a.nb, inv_n2, a.partials,
+// The alpha rule of every instance of a plan, all grid sizes, in one launch.  Each instance owns
+// alpha_blocks(Cn) consecutive blocks of the grid (the table is ordered by first block) and its own
+// partial sums and tickets.
+__global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (inst[mid].bstart <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const AlphaInst a = inst[lo];
+  alpha_choose_body<float2>(a.Uh, a.ps, a.nplanes, a.n, a.Cn, a.Ft, a.na, a.thr2, a.cband, a.nb, a.inv_n2, a.partials,
                             a.counter, a.aidx, a.res, a.info, a.tickets, (int)blockIdx.x - a.bstart, a.nblk);
 }
 
@@ -55,9 +64,9 @@ namespace {
 struct Group {
   int n = 0;
   const Handle* H0 = nullptr;
-  int nplanes = 0, nalpha_inst = 0, nalpha_blk = 0, nclusters = 0, max_na = 0;
+  int nplanes = 0, nclusters = 0;
   int var = -1;   // inverse variant (-1: not chosen yet; 5: the tile queue)
-  size_t off_planes = 0, off_alpha = 0, off_fused = 0, off_map = 0;
+  size_t off_planes = 0, off_fused = 0, off_map = 0;
   // the tile queue over the group's instances (n = 256, xi output, plan form): its descriptor table in
   // the plan's tables, its counters and intermediates in the plan's queue buffer
   int qn = 0, qtotal = 0, qncnt = 0;
@@ -70,21 +79,13 @@ struct Group {
 // intermediates), laid out by queue_layout.
 bool queue_group(int n, int output) { return output == FR3D_OUT_XI && inv_queue_supported(n, true); }
 
-// the launches of a group before the fused inverse: data row and column passes, alpha rule
+// the data transform of a group: row and column passes over all its instances' planes
 template <int N>
 int run_group_pre_n(const Group& g, const unsigned char* dev, cudaStream_t st) {
   const PlanePtr* planes = reinterpret_cast<const PlanePtr*>(dev + g.off_planes);
   constexpr int TY = SmallTile<N>::row, TC = SmallTile<N>::col;
   FR3D_TRY((row_r2c_t<float, N, TY, TablePlanes>(g.H0, TablePlanes{planes}, g.nplanes, st)));
   FR3D_TRY((col_t<float, N, false, ColTable, TC>(g.H0, ColTable{planes}, g.nplanes, st)));
-  if (g.nalpha_inst > 0) {
-    const size_t sm = sizeof(double) * kAlphaCPB * g.max_na;
-    FR3D_TRY(smem_optin(reinterpret_cast<const void*>(k_alpha_batched), sm));
-    k_alpha_batched<<<g.nalpha_blk, 256, sm, st>>>(reinterpret_cast<const AlphaInst*>(dev + g.off_alpha),
-                                                   g.nalpha_inst, (long)(N / 2 + 1) * N, N, num_classes(N),
-                                                   1.0 / ((double)N * N));
-    FR3D_CUDA_TRY(cudaGetLastError());
-  }
   return FR3D_OK;
 }
 
@@ -105,10 +106,26 @@ const int2* map_of(const Group& g, const unsigned char* dev) { return reinterpre
 
 size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// The alpha rule over all groups: one table of every discrepancy-rule instance, in group order.
+struct AlphaPlan {
+  size_t off = 0;   // the table's offset in the plan's device tables
+  int ninst = 0, nblk = 0, max_na = 0;
+};
+
+int run_alpha(const AlphaPlan& a, const unsigned char* dev, cudaStream_t st) {
+  if (a.ninst == 0) return FR3D_OK;
+  const size_t sm = sizeof(double) * kAlphaCPB * a.max_na;
+  FR3D_TRY(smem_optin(reinterpret_cast<const void*>(k_alpha_batched), sm));
+  k_alpha_batched<<<a.nblk, 256, sm, st>>>(reinterpret_cast<const AlphaInst*>(dev + a.off), a.ninst);
+  FR3D_CUDA_TRY(cudaGetLastError());
+  return FR3D_OK;
+}
+
 }  // namespace
 
 struct Batch {
   std::vector<Group> groups;
+  AlphaPlan alpha;
   unsigned char* dev = nullptr;
   unsigned char* qbuf = nullptr;   // the tile queue's counters and intermediates (zeroed once)
   int output = FR3D_OUT_XI;
@@ -167,7 +184,8 @@ namespace {
 void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vector<int>>& by_n,
                        const std::vector<float2*>& uh, const std::vector<const float*>& dd,
                        const std::vector<const int*>& ai, std::vector<unsigned char>& host, std::vector<Group>& groups,
-                       unsigned char* qbuf = nullptr) {
+                       AlphaPlan& ap, unsigned char* qbuf = nullptr) {
+  std::vector<AlphaInst> alph;
   auto put = [&](const void* p, size_t bytes) {
     const size_t off = al(host.size());
     host.resize(off + bytes);
@@ -179,7 +197,6 @@ void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vecto
     g.n = kv.first;
     g.H0 = &inst[kv.second[0]].handle->h;
     std::vector<PlanePtr> planes;
-    std::vector<AlphaInst> alph;
     std::vector<FusedArgs> fa;
     std::vector<int2> map;
     const long ps = (long)(g.n / 2 + 1) * g.n;
@@ -200,12 +217,16 @@ void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vecto
         a.aidx = const_cast<int*>(ai[idx]);
         a.res = I.opts->residuals;
         a.info = I.opts->info;
+        a.inv_n2 = 1.0 / ((double)g.n * g.n);
+        a.ps = ps;
+        a.n = g.n;
+        a.Cn = H->C;
         a.nplanes = I.Q;
         a.na = I.opts->n_alpha;
-        a.bstart = g.nalpha_blk;
+        a.bstart = ap.nblk;
         a.nblk = alpha_blocks(H->C);
-        g.nalpha_blk += a.nblk;
-        g.max_na = std::max(g.max_na, a.na);
+        ap.nblk += a.nblk;
+        ap.max_na = std::max(ap.max_na, a.na);
         alph.push_back(a);
       }
       FusedArgs f;
@@ -214,7 +235,6 @@ void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vecto
       fa.push_back(f);
     }
     g.nplanes = (int)planes.size();
-    g.nalpha_inst = (int)alph.size();
     g.nclusters = (int)map.size();
     if (qbuf && queue_group(g.n, inst[kv.second[0]].opts->output)) {
       // [4 launch counters][2 M' depth counters per instance][intermediates, 256-byte aligned]
@@ -240,11 +260,12 @@ void build_descriptors(const fr3d_instance* inst, const std::map<int, std::vecto
       g.off_queue = put(qt.data(), qt.size());
     }
     g.off_planes = put(planes.data(), planes.size() * sizeof(PlanePtr));
-    g.off_alpha = alph.empty() ? 0 : put(alph.data(), alph.size() * sizeof(AlphaInst));
     g.off_fused = put(fa.data(), fa.size() * sizeof(FusedArgs));
     g.off_map = put(map.data(), map.size() * sizeof(int2));
     groups.push_back(g);
   }
+  ap.ninst = (int)alph.size();
+  ap.off = alph.empty() ? 0 : put(alph.data(), alph.size() * sizeof(AlphaInst));
 }
 
 // bytes of the plan's queue buffer (the tile queue of its n = 256 group, xi output), 0 if none
@@ -267,10 +288,9 @@ int run_inverse(const Group& g, const unsigned char* dev, int output, int v, cud
   return inv_fused_batched_f32(g.n, fused_of(g, dev), map_of(g, dev), g.nclusters, output, std::min(v, 3), st);
 }
 
-int batch_launches(const std::vector<Group>& groups) {
-  int k = 0;
-  for (const auto& g : groups) k += 3 + (g.nalpha_inst > 0 ? 1 : 0);
-  return k;
+// per group: row pass, column pass, inverse; one alpha launch over all groups
+int batch_launches(const std::vector<Group>& groups, const AlphaPlan& ap) {
+  return 3 * (int)groups.size() + (ap.ninst > 0 ? 1 : 0);
 }
 
 }  // namespace
@@ -300,7 +320,7 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
     }
   }
   std::vector<unsigned char> host;
-  build_descriptors(inst, by_n, uh, dd, ai, host, b.groups, b.qbuf);
+  build_descriptors(inst, by_n, uh, dd, ai, host, b.groups, b.alpha, b.qbuf);
   if (cudaMalloc(&b.dev, al(host.size())) != cudaSuccess) {
     cudaFree(b.qbuf);
     return FR3D_ERR_OOM;
@@ -314,7 +334,7 @@ extern "C" int fr3d_batch_create(const fr3d_instance* inst, int n, fr3d_batch** 
       return FR3D_ERR_CUDA;
     }
   }
-  b.launches = batch_launches(b.groups);
+  b.launches = batch_launches(b.groups, b.alpha);
   fr3d_batch* h = new (std::nothrow) fr3d_batch();
   if (!h) {
     cudaFree(b.dev);
@@ -333,8 +353,9 @@ extern "C" int fr3d_batch_run(fr3d_batch* h, void* stream) {
   const int mode = fused_tune_mode_get();
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   FR3D_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  for (auto& g : h->b.groups) FR3D_TRY(run_group_pre(g, h->b.dev, st));
+  FR3D_TRY(run_alpha(h->b.alpha, h->b.dev, st));
   for (auto& g : h->b.groups) {
-    FR3D_TRY(run_group_pre(g, h->b.dev, st));
     int v = mode >= 2 ? mode - 2 : 0;
     if (mode == 1) {
       if (g.var < 0 && cs == cudaStreamCaptureStatusNone) {
@@ -393,7 +414,8 @@ extern "C" int fr3d_invert_batched_workspace(const fr3d_instance* inst, int n, s
   FR3D_TRY(batch_prepare(inst, n, true, uh, dd, ai, by_n, &spectra, (cudaStream_t)stream));
   std::vector<unsigned char> host;
   std::vector<Group> groups;
-  build_descriptors(inst, by_n, uh, dd, ai, host, groups);
+  AlphaPlan ap;
+  build_descriptors(inst, by_n, uh, dd, ai, host, groups, ap);
   *bytes = al(spectra) + al(host.size());
   return FR3D_OK;
 }
@@ -412,7 +434,8 @@ extern "C" int fr3d_invert_batched(const fr3d_instance* inst, int n, void* works
   for (int i = 0; i < n; ++i) uh[i] = reinterpret_cast<float2*>(base + reinterpret_cast<size_t>(uh[i]));
   std::vector<unsigned char> host;
   std::vector<Group> groups;
-  build_descriptors(inst, by_n, uh, dd, ai, host, groups);
+  AlphaPlan ap;
+  build_descriptors(inst, by_n, uh, dd, ai, host, groups, ap);
   const size_t need = al(spectra) + al(host.size());
   if (ws_bytes < need) return FR3D_ERR_INVALID_ARG;
   unsigned char* tables = base + al(spectra);
@@ -420,10 +443,10 @@ extern "C" int fr3d_invert_batched(const fr3d_instance* inst, int n, void* works
   FR3D_CUDA_TRY(cudaMemcpyAsync(tables, host.data(), host.size(), cudaMemcpyHostToDevice, st));
   const int mode = fused_tune_mode_get();
   const int v = mode >= 2 ? mode - 2 : 3;   // the forced tile, else the register-accumulator tile
-  for (auto& g : groups) {
-    FR3D_TRY(run_group_pre(g, tables, st));
+  for (auto& g : groups) FR3D_TRY(run_group_pre(g, tables, st));
+  FR3D_TRY(run_alpha(ap, tables, st));
+  for (auto& g : groups)
     FR3D_TRY(inv_fused_batched_f32(g.n, fused_of(g, tables), map_of(g, tables), g.nclusters, inst[0].opts->output, v,
                                    st));
-  }
   return FR3D_OK;
 }

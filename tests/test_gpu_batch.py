@@ -1,5 +1,5 @@
-"""Batched uneven instances (one plan, four launches per grid size) against per-instance calls and
-the FP64 oracle."""
+"""Batched uneven instances (one plan: three launches per grid size and one alpha-rule launch over all
+sizes) against per-instance calls and the FP64 oracle."""
 
 import numpy as np
 import pytest
@@ -49,7 +49,7 @@ def test_batch_matches_single_calls_and_oracle(F):
         F.invert(H, Ud, Q, o, opts)
         singles.append((o.clone(), int(idx.item())))
     B = F.Batch(items)
-    assert B.launches == 4 * 5            # 5 grid sizes, 4 launches each
+    assert B.launches == 3 * 5 + 1        # 5 grid sizes, 3 launches each, one alpha launch
     for (H, Ud, Q, opts, out) in items:
         out.fill_(float("nan"))
     B.run()
