@@ -254,28 +254,41 @@ __global__ void __launch_bounds__(128) k_wgrad3(WgradArgs a) {
   tc::fence_after_sync();
   const uint32_t tmem = tbase;
   const uint32_t idesc = idesc_mn(128, N);
-  if (tid == 0) {
-    for (int it = 0; it < nst && !flag(&sabort); ++it) {
+  if (warp == 0) {
+    // producer warp: lane 0 waits for the stage and posts its byte count, then the lanes issue the
+    // stage's copies (rows_loaded gradient chunks, N / 8 input chunks), one copy per lane
+    const int lane = tid & 31;
+    const int ncopy = rows_loaded + N / 8;
+    for (int it = 0; it < nst; ++it) {
       const int s = it % kWgStages;
       const int use = it / kWgStages;
-      if (use > 0 && !tc::mbar_wait_sleep(&empty[s], (uint32_t)((use - 1) & 1), kPolls, kSleepNs)) {
-        sabort = 1;
-        break;
+      int stop = 0;
+      if (lane == 0) {
+        stop = flag(&sabort);
+        if (!stop && use > 0 && !tc::mbar_wait_sleep(&empty[s], (uint32_t)((use - 1) & 1), kPolls, kSleepNs)) {
+          sabort = 1;
+          stop = 1;
+        }
+        if (!stop) tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(ncopy * kWgPlane));
       }
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      __syncwarp();   // the byte count is posted before any copy of the stage is issued
+      if (stop) break;
       const long v = v0 + (long)it * kWgVox;
       unsigned char* st = sm + (size_t)s * stage;
-      tc::mbar_arrive_expect_tx(&full[s], (uint32_t)((rows_loaded + N / 8) * kWgPlane));
-      // A: row group (fi, c) = output gradient chunk c at positions v - (fi - 1) (ndw = 3), or c at v
-      for (int rg = 0; rg < rows_loaded; ++rg) {
-        const int fi = rg / gc, c = rg - fi * gc;
-        const long pos = v - (a.ndw == 3 ? fi - 1 : 0);
-        const long chunk = (long)b * a.g_chunks + a.g_off + c;
-        tc::bulk_g2s(st + rg * kWgPlane, a.g + (chunk * a.Vs + pos) * 16, kWgPlane, &full[s]);
-      }
-      // B: input chunk c at positions v + the (a, e[, f]) shift
-      for (int c = 0; c < N / 8; ++c) {
-        const long chunk = (long)b * a.x_chunks + a.x_off + c;
-        tc::bulk_g2s(st + aBytes + c * kWgPlane, a.x + (chunk * a.Vs + v + xoff) * 16, kWgPlane, &full[s]);
+      for (int k = lane; k < ncopy; k += 32) {
+        if (k < rows_loaded) {
+          // A: row group (fi, c) = output gradient chunk c at positions v - (fi - 1) (ndw = 3), or c at v
+          const int fi = k / gc, c = k - fi * gc;
+          const long pos = v - (a.ndw == 3 ? fi - 1 : 0);
+          const long chunk = (long)b * a.g_chunks + a.g_off + c;
+          tc::bulk_g2s(st + k * kWgPlane, a.g + (chunk * a.Vs + pos) * 16, kWgPlane, &full[s]);
+        } else {
+          // B: input chunk c at positions v + the (a, e[, f]) shift
+          const int c = k - rows_loaded;
+          const long chunk = (long)b * a.x_chunks + a.x_off + c;
+          tc::bulk_g2s(st + aBytes + c * kWgPlane, a.x + (chunk * a.Vs + v + xoff) * 16, kWgPlane, &full[s]);
+        }
       }
     }
   } else if (tid == 32) {
