@@ -111,3 +111,45 @@ def test_withheld_releases_end_in_a_timeout_report_and_the_next_call_is_exact(F)
     torch.cuda.synchronize()
     assert not int(info.item()) & F.INFO_TIMEOUT
     assert torch.equal(got, ref)
+
+
+def test_many_repeats_and_random_counts_match_the_register_tile(F):
+    """The queue's ordering is timing-dependent (tickets, per-depth counters, bulk copies): repeat the
+    full-size call, directly and as graph replays, and draw source, depth and band counts at random."""
+    import random
+    w = I.config_workload(3)
+    H, U, delta = _data(F, w)
+    ref, _ = _run(F, H, U, w.Q, w, delta, 3)
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    F.autotune_mode(2 + 5)
+    out = torch.empty_like(ref)
+    opts = F.Opts(alphas=w.alphas, delta=delta, tau=1.1, points=w.sources, info=info)
+    for _ in range(40):
+        out.fill_(float("nan"))
+        F.invert(H, U, w.Q, out, opts)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        assert not int(info.item()) & F.INFO_TIMEOUT
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            F.invert(H, U, w.Q, out, opts)
+    torch.cuda.current_stream().wait_stream(st)
+    for _ in range(40):
+        out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    rnd = random.Random(11)
+    for case in range(8):
+        q, mp, nb = rnd.randint(1, 8), rnd.choice([1, 3, 7, 16, 33, 64]), rnd.choice([1, 4])
+        w2 = I.make_workload(256, mp, q=q, n_incl=2, noise_level=0.02, n_alpha=12, seed=3100 + case)
+        H2, U2, d2 = _data(F, w2)
+        r, ri = _run(F, H2, U2, q, w2, d2, 3, n_bands=nb)
+        for _ in range(3):
+            got, gi = _run(F, H2, U2, q, w2, d2, 5, n_bands=nb)
+            assert torch.equal(gi, ri), (q, mp, nb)
+            assert torch.equal(got, r), (q, mp, nb)
+        H2.close()
