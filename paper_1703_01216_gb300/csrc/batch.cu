@@ -36,8 +36,9 @@ struct AlphaInst {
 
 // The alpha rule of every instance of a plan, all grid sizes, in one launch.  Each instance owns
 // alpha_blocks(Cn) consecutive blocks of the grid (the table is ordered by first block) and its own
-// partial sums and tickets.
-__global__ void __launch_bounds__(256) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst) {
+// partial sums and tickets.  A plan's grid is many waves of blocks, each a chain of dependent
+// steps, so four blocks per SM (64 registers, a 64-byte spill) run faster than two at 98 registers.
+__global__ void __launch_bounds__(256, 4) k_alpha_batched(const AlphaInst* __restrict__ inst, int ninst) {
   int lo = 0, hi = ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
